@@ -1,0 +1,197 @@
+"""Seeded synthetic inputs for the checkerboard hard-particle MC sweep.
+
+This module is shared by the tests, the benchmark, the oracle checks and the
+CUDA path.  It holds none of the method's arithmetic: no overlap test, no
+cell list, no random stream of the sweep.  It only builds shapes, boxes and
+overlap-free starting configurations by construction:
+
+* 2D, random orientations: a (slightly stretched) triangular lattice whose
+  nearest-site distance is at least the circumdiameter 2R, so no two shapes
+  can touch whatever their orientations.
+* 2D, aligned: the same lattice with every shape at the same orientation and a
+  nearest-site distance of at least the shape's diameter (largest vertex
+  distance).  Translates K and K+t overlap only if t lies in the difference
+  body K-K, which sits inside the disk of that radius.
+* 3D, aligned: a simple cubic lattice with spacing at least the largest
+  axis-aligned extent of the shape; two aligned translates whose centres
+  differ by at least that much along some axis have disjoint bounding boxes.
+
+Numbers follow the benchmark systems (Sec. 3: pentagon fluids) and the
+workload list this library is measured on (regular pentagons of circumradius
+0.5; unit cubes; replicas with N in [256, 8192] and packing fraction in
+[0.40, 0.70]).
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+
+import numpy as np
+
+
+def regular_polygon(n: int, R: float = 0.5) -> np.ndarray:
+    """Counter-clockwise regular n-gon of circumradius R, first vertex at +y."""
+    k = np.arange(n)
+    th = 0.5 * math.pi + 2.0 * math.pi * k / n
+    return np.stack([R * np.cos(th), R * np.sin(th)], axis=1)
+
+
+def cube(edge: float = 1.0) -> np.ndarray:
+    h = 0.5 * edge
+    return np.array([[sx * h, sy * h, sz * h]
+                     for sz in (-1, 1) for sy in (-1, 1) for sx in (-1, 1)], dtype=np.float64)
+
+
+def polygon_area(v: np.ndarray) -> float:
+    x, y = v[:, 0], v[:, 1]
+    return 0.5 * float(np.sum(x * np.roll(y, -1) - np.roll(x, -1) * y))
+
+
+def cube_volume(edge: float) -> float:
+    return edge ** 3
+
+
+def diameter(v: np.ndarray) -> float:
+    d = v[:, None, :] - v[None, :, :]
+    return float(np.sqrt((d * d).sum(-1)).max())
+
+
+def circumradius(v: np.ndarray) -> float:
+    return float(np.sqrt((v * v).sum(1)).max())
+
+
+def box_length(N: int, particle_measure: float, phi: float, dim: int) -> float:
+    """Side of a square/cubic box holding N shapes at packing fraction phi."""
+    return (N * particle_measure / phi) ** (1.0 / dim)
+
+
+def _tri_lattice_dims(N: int, L: float):
+    """Columns/rows (rows even) of a triangular lattice in an L x L box with at
+    least N sites and the largest nearest-site distance."""
+    best = None
+    ny0 = max(2, int(round(math.sqrt(N * 2.0 / math.sqrt(3.0)))))
+    for ny in range(max(2, ny0 - 12), ny0 + 13):
+        if ny % 2:
+            continue
+        nx = -(-N // ny)
+        ax, ay = L / nx, L / ny
+        dmin = min(ax, math.hypot(0.5 * ax, ay))
+        if best is None or dmin > best[0]:
+            best = (dmin, nx, ny)
+    return best
+
+
+def triangular_lattice(N: int, L: float, rng: np.random.Generator, aligned: bool = False):
+    """N sites of a periodic triangular lattice in [0,L)^2 (vacancies random).
+
+    Returns (pos[N,2], orient[N,2], nearest_site_distance)."""
+    dmin, nx, ny = _tri_lattice_dims(N, L)
+    ax, ay = L / nx, L / ny
+    sites = []
+    for j in range(ny):
+        for i in range(nx):
+            sites.append(((i + 0.5 * (j % 2)) * ax, j * ay))
+    sites = np.array(sites, dtype=np.float64)
+    keep = np.sort(rng.permutation(sites.shape[0])[:N])
+    pos = sites[keep]
+    pos += rng.uniform(0.0, L, size=2)[None, :]          # random global offset
+    pos = np.mod(pos, L)
+    pos[pos >= L] = 0.0
+    if aligned:
+        ori = np.tile(np.array([1.0, 0.0]), (N, 1))
+    else:
+        th = rng.uniform(0.0, 2.0 * math.pi, size=N)
+        ori = np.stack([np.cos(th), np.sin(th)], axis=1)
+    return pos, ori, dmin
+
+
+def cubic_lattice(N: int, L: float, rng: np.random.Generator):
+    """N sites of a periodic simple cubic lattice in [0,L)^3, identity
+    orientations.  Returns (pos[N,3], quat[N,4], spacing)."""
+    n = -(-int(round(N ** (1.0 / 3.0))) // 1)
+    while n ** 3 < N:
+        n += 1
+    a = L / n
+    g = np.arange(n) * a
+    sites = np.stack(np.meshgrid(g, g, g, indexing="ij"), axis=-1).reshape(-1, 3)
+    keep = np.sort(rng.permutation(sites.shape[0])[:N])
+    pos = np.mod(sites[keep] + rng.uniform(0.0, L, size=3)[None, :], L)
+    pos[pos >= L] = 0.0
+    q = np.tile(np.array([1.0, 0.0, 0.0, 0.0]), (N, 1))
+    return pos, q, a
+
+
+@dataclass
+class System:
+    """One replica: shape, box and a starting configuration."""
+    name: str
+    dim: int
+    verts: np.ndarray
+    L: np.ndarray
+    pos: np.ndarray
+    orient: np.ndarray
+    phi: float
+    seed: int
+    d: float = 0.1
+    a: float = 0.1
+    nselect: int = 4
+    w_min: float = 0.0
+    notes: dict = field(default_factory=dict)
+
+    @property
+    def N(self):
+        return self.pos.shape[0]
+
+
+def pentagon_system(N: int, phi: float, seed: int, name: str = "pentagons",
+                    d: float = 0.1, a: float = 0.1, nselect: int = 4, w_min: float = 0.0,
+                    gen_seed: int | None = None) -> System:
+    """Regular pentagons (circumradius 0.5) on an overlap-free lattice.
+
+    Random orientations while the lattice spacing allows 2R; aligned shapes up
+    to the diameter bound otherwise; raises if phi is beyond both."""
+    v = regular_polygon(5, 0.5)
+    A = polygon_area(v)
+    L = box_length(N, A, phi, 2)
+    rng = np.random.default_rng(seed if gen_seed is None else gen_seed)
+    dmin, _, _ = _tri_lattice_dims(N, L)
+    R = circumradius(v)
+    if dmin >= 2.0 * R:
+        pos, ori, dmin = triangular_lattice(N, L, rng, aligned=False)
+        kind = "triangular lattice, random orientations (site distance >= 2R)"
+    elif dmin >= diameter(v):
+        pos, ori, dmin = triangular_lattice(N, L, rng, aligned=True)
+        kind = "triangular lattice, aligned (site distance >= shape diameter)"
+    else:
+        raise ValueError(f"phi={phi} too dense for an overlap-free lattice start")
+    return System(name=name, dim=2, verts=v, L=np.array([L, L]), pos=pos, orient=ori,
+                  phi=phi, seed=seed, d=d, a=a, nselect=nselect, w_min=w_min,
+                  notes={"init": kind, "site_distance": dmin})
+
+
+def cube_system(N: int, phi: float, seed: int, name: str = "cubes", d: float = 0.1,
+                a: float = 0.1, nselect: int = 4) -> System:
+    v = cube(1.0)
+    L = box_length(N, 1.0, phi, 3)
+    rng = np.random.default_rng(seed)
+    pos, q, a_sp = cubic_lattice(N, L, rng)
+    if a_sp < 1.0:
+        raise ValueError("cubic lattice spacing below the cube edge")
+    return System(name=name, dim=3, verts=v, L=np.array([L, L, L]), pos=pos, orient=q,
+                  phi=phi, seed=seed, d=d, a=a, nselect=nselect,
+                  notes={"init": "simple cubic lattice, aligned (spacing >= edge)",
+                         "spacing": a_sp})
+
+
+def replica_params(n_replicas: int = 512, gen_seed: int = 2024, n_lo: int = 256,
+                   n_hi: int = 8192, phi_lo: float = 0.40, phi_hi: float = 0.70):
+    """(N_r, phi_r, seed_r = 42 + r) for a batch of independent replicas."""
+    rng = np.random.default_rng(gen_seed)
+    Ns = rng.integers(n_lo, n_hi + 1, size=n_replicas)
+    phis = rng.uniform(phi_lo, phi_hi, size=n_replicas)
+    return [(int(Ns[r]), float(phis[r]), 42 + r) for r in range(n_replicas)]
+
+
+def replica_systems(n_replicas: int = 512, gen_seed: int = 2024, **kw):
+    return [pentagon_system(N, phi, seed, name=f"replica{r}", gen_seed=gen_seed * 100003 + r)
+            for r, (N, phi, seed) in enumerate(replica_params(n_replicas, gen_seed, **kw))]
