@@ -1,0 +1,192 @@
+/*
+ * hpmc.h -- C ABI of the GB300 (sm_103a) checkerboard hard-particle Monte
+ * Carlo library libhpmc.so.
+ *
+ * The library implements the data-parallel hot path of hard-particle
+ * Metropolis Monte Carlo (Anderson, Irrgang & Glotzer, "Scalable Metropolis
+ * Monte Carlo for simulation of hard shapes"): per sweep a random shift of
+ * the cell grid, a cell-list rebuild, and 2^d checkerboard sets in which
+ * every active cell makes `nselect` sequential trial moves (translation and
+ * rotation), each rejected when it leaves its cell or overlaps a neighbour.
+ *
+ * Conventions for every function below:
+ *   - Return value: 0 on success or a negative HPMC_ERR_* code.  The library
+ *     never exits, aborts or traps; errors raised by device code (capacity
+ *     overflow, bounded waits) are recorded in the handle and returned by the
+ *     next call that synchronises (hpmc_counters, hpmc_get_state,
+ *     hpmc_check_overlaps, hpmc_sync).  hpmc_strerror() names a code.
+ *   - Host pointers are owned by the caller and only read/written during the
+ *     call.  The library owns all device memory; it allocates in *_create and
+ *     frees in *_destroy.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream).  Functions that take a stream only enqueue work on it.
+ *   - dim is 2 (convex polygons, orientation (cos, sin)) or 3 (convex
+ *     polyhedra, unit quaternion (w, x, y, z)).  Positions lie in [0, L).
+ *   - A "batch" holds R independent replicas of one shape type; a single
+ *     system is a batch with R = 1.  Replica index r selects one replica.
+ */
+#ifndef HPMC_H
+#define HPMC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define HPMC_OK                0
+#define HPMC_ERR_INVALID_ARG  -1   /* NaN, N = 0, dim not 2/3, bad vertices, sizes */
+#define HPMC_ERR_BOX_TOO_SMALL -2  /* fewer than 4 cells on an axis */
+#define HPMC_ERR_OVERLAP      -3   /* (reserved) overlapping input where forbidden */
+#define HPMC_ERR_OOM          -4   /* device allocation failed */
+#define HPMC_ERR_CUDA         -5   /* a CUDA runtime call failed */
+#define HPMC_ERR_TIMEOUT      -6   /* a bounded device wait gave up */
+#define HPMC_ERR_CAPACITY     -7   /* a cell or stencil exceeded the staging capacity */
+#define HPMC_ERR_NOT_READY    -8   /* call order violated (e.g. no moves set) */
+
+#define HPMC_FP64          0       /* plain form: every decision in FP64 */
+#define HPMC_FP32_FILTERED 1       /* FP32 with certified bounds, FP64 re-check */
+
+/* Counters accumulated since the last reset, summed over replicas. */
+typedef struct {
+    uint64_t moves;            /* trial moves proposed = accept + both rejects */
+    uint64_t accept;
+    uint64_t reject_overlap;
+    uint64_t reject_boundary;  /* trial left its active cell (checkerboard rule) */
+    uint64_t cull_pairs;       /* stencil neighbours tested by circumsphere */
+    uint64_t overlap_checks;   /* full SAT / GJK evaluations */
+    uint64_t fp64_rechecks;    /* FP32 verdicts that were not certified */
+    uint64_t gjk_cap;          /* 3D: GJK iteration cap reached (counted as overlap) */
+} hpmc_counters_t;
+
+typedef struct hpmc_batch* hpmc_t;
+
+/* One replica of a batch.  pos[N*dim] and orient[N*(2|4)] are its starting
+ * configuration in tag order (caller-owned host arrays, read during create). */
+typedef struct {
+    uint32_t N;
+    double box[3];             /* L per axis (box[2] ignored in 2D) */
+    const double* pos;
+    const double* orient;
+    uint64_t seed;             /* Philox key of this replica */
+    double d;                  /* translation half-width */
+    double a;                  /* rotation half-angle parameter (radians) */
+    uint32_t nselect;          /* sequential trial moves per active cell */
+} hpmc_replica_desc_t;
+
+/*
+ * hpmc_batch_create -- allocate a batch of R replicas of one convex shape.
+ *   dim       2 or 3.
+ *   verts     nv*dim doubles, the shape in its local frame (2D: convex and
+ *             counter-clockwise; 3D: the vertices of a convex polyhedron).
+ *   nv        3..16 (2D) or 4..32 (3D).
+ *   w_min     floor on the cell width (0 = the circumdiameter, the paper's
+ *             minimum, Sec. 2.2.1).
+ *   reps      R replica descriptors (see above).
+ *   out       receives the handle.
+ * Cell geometry per axis: nc = floor(L / max(2R, w_min)), made even, >= 4.
+ * Errors: INVALID_ARG, BOX_TOO_SMALL, OOM, CUDA.  Synchronous.
+ */
+int hpmc_batch_create(int dim, const double* verts, uint32_t nv, double w_min,
+                      uint32_t R, const hpmc_replica_desc_t* reps, hpmc_t* out);
+
+/*
+ * hpmc_create -- single-system form of hpmc_batch_create (R = 1) taking the
+ * box, shape, configuration and Philox seed; moves default to d = a = 0.1,
+ * nselect = 4 until hpmc_set_moves is called.
+ */
+int hpmc_create(const double* box, int dim, uint32_t N, const double* verts, uint32_t nv,
+                const double* pos, const double* orient, uint64_t seed, double w_min,
+                hpmc_t* out);
+
+/* Release every device and host resource of the handle (synchronises it). */
+int hpmc_destroy(hpmc_t h);
+
+/*
+ * hpmc_set_moves -- trial-move sizes of replica r (r = -1: all replicas).
+ *   d >= 0 translation half-width; a in [0, pi) rotation parameter; nselect
+ *   1..65535.  Sec. 2.1: r' = r + dr, q' = q * dq.
+ */
+int hpmc_set_moves(hpmc_t h, int32_t r, double d, double a, uint32_t nselect);
+
+/* hpmc_set_precision -- HPMC_FP64 or HPMC_FP32_FILTERED (default).  Both give
+ * identical trajectories; the filtered form is faster. */
+int hpmc_set_precision(hpmc_t h, int mode);
+
+/*
+ * hpmc_set_group_size -- lanes per active cell in the set kernel (1, 2, 4, 8,
+ * 16 or 32) and warps per block (1..16).  Does not change the trajectory.
+ * hpmc_autotune picks them by timing.
+ */
+int hpmc_set_group_size(hpmc_t h, int lanes_per_cell, int warps_per_block);
+
+/*
+ * hpmc_sweep -- enqueue n sweeps on `stream`: per sweep the grid shift,
+ * the cell-list rebuild and the 2^d checkerboard sets (Sec. 2.5.2), for
+ * every replica.  Asynchronous; the sweep counter advances on the device.
+ * With use_graph != 0 the per-sweep launch sequence is captured once into a
+ * CUDA graph and replayed.
+ */
+int hpmc_sweep(hpmc_t h, uint32_t n, void* stream);
+int hpmc_sweep_graph(hpmc_t h, uint32_t n, void* stream);
+
+/* Wait for the handle's last stream; returns a recorded device error. */
+int hpmc_sync(hpmc_t h);
+
+/*
+ * hpmc_counters -- synchronise, then copy the counters of replica r (r = -1:
+ * the sum over replicas) into *out.  hpmc_reset_counters zeroes them.
+ */
+int hpmc_counters(hpmc_t h, int32_t r, hpmc_counters_t* out);
+int hpmc_reset_counters(hpmc_t h);
+
+/*
+ * hpmc_check_overlaps -- synchronise, rebuild the cell list and count the
+ * overlapping pairs of replica r (r = -1: all) with the FP64 contract
+ * predicate (circumsphere cull, then SAT / GJK).  *n_pairs receives the count.
+ */
+int hpmc_check_overlaps(hpmc_t h, int32_t r, uint64_t* n_pairs);
+
+/*
+ * hpmc_get_state / hpmc_set_state -- copy replica r's configuration in tag
+ * order to / from caller-owned host arrays pos[N*dim], orient[N*(2|4)], and
+ * its sweep counter.  Both synchronise.  set_state checks that positions are
+ * finite and inside [0, L) and orientations finite (INVALID_ARG otherwise);
+ * it does not check overlaps (see hpmc_check_overlaps).
+ */
+int hpmc_get_state(hpmc_t h, int32_t r, double* pos, double* orient, uint64_t* sweep);
+int hpmc_set_state(hpmc_t h, int32_t r, const double* pos, const double* orient, uint64_t sweep);
+
+/*
+ * hpmc_run_host -- end-to-end call for callers holding host buffers: upload
+ * every replica's configuration from pos/orient (all replicas concatenated in
+ * replica order, tag order inside), run n sweeps, download the result into
+ * pos_out/orient_out and the summed counters into *out.  Synchronous.
+ */
+int hpmc_run_host(hpmc_t h, const double* pos, const double* orient, uint32_t n,
+                  double* pos_out, double* orient_out, hpmc_counters_t* out, void* stream);
+
+/*
+ * hpmc_autotune -- time each (lanes per cell, warps per block) choice on
+ * n_trial sweeps from a saved copy of the state, restore the state and
+ * sweep counters, and keep the fastest choice.  The trajectory does not
+ * depend on the choice.  *best_lanes / *best_warps receive it.  Synchronous.
+ */
+int hpmc_autotune(hpmc_t h, uint32_t n_trial, int* best_lanes, int* best_warps);
+
+/* Geometry of replica r: cells per axis, cell width, circumradius. */
+int hpmc_geometry(hpmc_t h, int32_t r, int32_t* nc, double* w, double* R);
+
+/* Number of kernel launches one sweep enqueues (for launch accounting). */
+int hpmc_launches_per_sweep(hpmc_t h, uint32_t* n);
+
+/* FP32 filter margins of replica r (in-cell, cull, overlap), for reporting. */
+int hpmc_filter_margins(hpmc_t h, int32_t r, double* e_in, double* e_cull, double* e_overlap);
+
+const char* hpmc_strerror(int code);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HPMC_H */

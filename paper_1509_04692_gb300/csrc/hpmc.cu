@@ -1,0 +1,971 @@
+// hpmc.cu -- C ABI of libhpmc.so: batch state, launch sequence of a sweep,
+// CUDA-graph replay, counters, overlap check, state I/O and the autotuner.
+//
+// Sec. 2.5.2 (GPU checkerboard kernel): the host only enqueues; every step of
+// a sweep (shift, cell-list rebuild, 2^d sets) runs in the kernels of this
+// library on the caller's stream.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "../../include/hpmc.h"
+#include "hpmc_bounds.h"
+#include "hpmc_launch.h"
+#include "hpmc_rebuild.cuh"
+
+using namespace hpmc;
+
+int hpmc_check3d_launch(const hpmc::Dev& dv, const hpmc::Shape3& sh, int b, int32_t r,
+                        unsigned long long* out, uint32_t ntot);
+
+namespace {
+
+constexpr int kGroupSizes[6] = { 1, 2, 4, 8, 16, 32 };
+
+int gidx_of(int G)
+{
+    for (int i = 0; i < 6; ++i)
+        if (kGroupSizes[i] == G) return i;
+    return -1;
+}
+
+struct HostRep {
+    uint32_t N;
+    double L[3];
+    uint64_t seed;
+    double d, a;
+    uint32_t nselect;
+};
+
+}  // namespace
+
+struct hpmc_batch {
+    int dim = 2;
+    int nv = 0;
+    double verts[kMaxV3 * 3] = {};
+    double w_min = 0.0;
+    double Rc = 0.0, rc2 = 0.0;
+    uint32_t R = 0, ntot = 0, ctot = 0, ntiles = 0;
+    std::vector<HostRep> hr;
+    std::vector<Rep> reps;
+    Shape2 sh2{};
+    Shape3 sh3{};
+    Dev dv{};
+    int cur = 0;
+    int precision = HPMC_FP32_FILTERED;
+    int G = 4, wpb = 4;
+    int num_sms = 0;
+    uint32_t* item_base_dev = nullptr;   // [6][R + 1]
+    std::vector<uint32_t> items_per_set; // [6] totals
+    std::vector<void*> allocs;
+    cudaStream_t last_stream = nullptr;
+    int pending_error = 0;
+    // graph of two sweeps per starting buffer parity (two sweeps return to it)
+    cudaGraphExec_t graph[2] = { nullptr, nullptr };
+    cudaStream_t graph_stream = nullptr;
+    // set-kernel launch configuration (recomputed when G, wpb or precision change)
+    bool cfg_valid = false;
+    const void* cfg_fn = nullptr;
+    size_t cfg_smem = 0;
+    uint32_t cfg_grid = 0;
+    unsigned long long* check_out = nullptr;
+};
+
+namespace {
+
+int cuda_fail(cudaError_t e)
+{
+    (void)cudaGetLastError();
+    return e == cudaErrorMemoryAllocation ? HPMC_ERR_OOM : HPMC_ERR_CUDA;
+}
+
+#define CK(x)                                  \
+    do {                                       \
+        cudaError_t e_ = (x);                  \
+        if (e_ != cudaSuccess) return cuda_fail(e_); \
+    } while (0)
+
+template <typename T>
+int dalloc(hpmc_batch* h, T** p, size_t n)
+{
+    void* q = nullptr;
+    cudaError_t e = cudaMalloc(&q, std::max<size_t>(n, 1) * sizeof(T));
+    if (e != cudaSuccess) return cuda_fail(e);
+    h->allocs.push_back(q);
+    *p = (T*)q;
+    return 0;
+}
+
+float f32_down(double x)
+{
+    float f = (float)x;
+    if ((double)f > x) f = std::nextafter(f, -INFINITY);
+    return f;
+}
+
+float f32_up(double x)
+{
+    float f = (float)x;
+    if ((double)f < x) f = std::nextafter(f, INFINITY);
+    return f;
+}
+
+bool is_finite(double x) { return std::isfinite(x); }
+
+// geometry shared by every replica: circumradius and the overlap constants
+int shape_setup(hpmc_batch* h, int dim, const double* verts, uint32_t nv)
+{
+    if (dim != 2 && dim != 3) return HPMC_ERR_INVALID_ARG;
+    if (dim == 2 && (nv < 3 || nv > (uint32_t)kMaxV2)) return HPMC_ERR_INVALID_ARG;
+    if (dim == 3 && (nv < 4 || nv > (uint32_t)kMaxV3)) return HPMC_ERR_INVALID_ARG;
+    if (!verts) return HPMC_ERR_INVALID_ARG;
+    for (uint32_t i = 0; i < nv * (uint32_t)dim; ++i)
+        if (!is_finite(verts[i])) return HPMC_ERR_INVALID_ARG;
+    h->dim = dim;
+    h->nv = (int)nv;
+    std::memcpy(h->verts, verts, sizeof(double) * nv * dim);
+    double r2 = 0.0;
+    for (uint32_t i = 0; i < nv; ++i) {
+        const double* v = verts + (size_t)i * dim;
+        double q = v[0] * v[0] + v[1] * v[1];
+        if (dim == 3) q = q + v[2] * v[2];
+        if (q > r2) r2 = q;
+    }
+    h->Rc = std::sqrt(r2);
+    if (!(h->Rc > 0.0)) return HPMC_ERR_INVALID_ARG;
+    const double dcut = h->Rc + h->Rc;
+    h->rc2 = dcut * dcut;
+    if (dim == 2) {
+        // convex and counter-clockwise: strictly left turns everywhere
+        for (uint32_t i = 0; i < nv; ++i) {
+            const double* p0 = verts + 2 * i;
+            const double* p1 = verts + 2 * ((i + 1) % nv);
+            const double* p2 = verts + 2 * ((i + 2) % nv);
+            const double cr = (p1[0] - p0[0]) * (p2[1] - p1[1]) - (p1[1] - p0[1]) * (p2[0] - p1[0]);
+            if (!(cr > 0.0)) return HPMC_ERR_INVALID_ARG;
+        }
+        Shape2& s = h->sh2;
+        s = Shape2{};
+        s.nv = (int)nv;
+        for (uint32_t k = 0; k < nv; ++k) {
+            s.vx[k] = verts[2 * k];
+            s.vy[k] = verts[2 * k + 1];
+        }
+        for (uint32_t k = 0; k < nv; ++k) {
+            const uint32_t k1 = (k + 1) % nv;
+            s.nx[k] = s.vy[k1] - s.vy[k];
+            s.ny[k] = s.vx[k] - s.vx[k1];
+            double lo = 0.0, hi = 0.0;
+            for (uint32_t i = 0; i < nv; ++i) {
+                const double t = s.nx[k] * s.vx[i] + s.ny[k] * s.vy[i];
+                if (i == 0 || t < lo) lo = t;
+                if (i == 0 || t > hi) hi = t;
+            }
+            s.alo[k] = lo;
+            s.ahi[k] = hi;
+        }
+        for (uint32_t k = 0; k < nv; ++k) {
+            s.fvx[k] = (float)s.vx[k]; s.fvy[k] = (float)s.vy[k];
+            s.fnx[k] = (float)s.nx[k]; s.fny[k] = (float)s.ny[k];
+            s.falo[k] = (float)s.alo[k]; s.fahi[k] = (float)s.ahi[k];
+        }
+        s.rc2 = h->rc2;
+        s.frc2 = (float)h->rc2;
+    } else {
+        Shape3& s = h->sh3;
+        s = Shape3{};
+        s.nv = (int)nv;
+        for (uint32_t k = 0; k < nv; ++k)
+            for (int a = 0; a < 3; ++a) {
+                s.v[k][a] = verts[3 * k + a];
+                s.fv[k][a] = (float)verts[3 * k + a];
+            }
+        s.rc2 = h->rc2;
+        s.frc2 = (float)h->rc2;
+    }
+    return 0;
+}
+
+int rep_geometry(const hpmc_batch* h, const HostRep& hr, Rep& rp)
+{
+    const double dcut = h->Rc + h->Rc;
+    const double wmin = dcut > h->w_min ? dcut : h->w_min;
+    for (int a = 0; a < 3; ++a) {
+        if (a < h->dim) {
+            const double L = hr.L[a];
+            if (!(L > 0.0) || !is_finite(L)) return HPMC_ERR_INVALID_ARG;
+            int n = (int)std::floor(L / wmin);
+            if (n % 2) n -= 1;
+            if (n < 4) return HPMC_ERR_BOX_TOO_SMALL;
+            if (n > 65536) return HPMC_ERR_INVALID_ARG;
+            rp.L[a] = L;
+            rp.halfL[a] = 0.5 * L;
+            rp.nc[a] = n;
+            rp.w[a] = L / (double)n;
+            rp.inv_w[a] = (double)n / L;
+            rp.w32[a] = (float)rp.w[a];
+        } else {
+            rp.L[a] = 1.0; rp.halfL[a] = 0.5; rp.nc[a] = 1; rp.w[a] = 1.0; rp.inv_w[a] = 1.0;
+            rp.w32[a] = 1.0f;
+        }
+    }
+    rp.n = hr.N;
+    rp.seed = hr.seed;
+    rp.d = hr.d;
+    rp.tau = std::tan(0.5 * hr.a);
+    rp.d32 = (float)rp.d;
+    rp.tau32 = (float)rp.tau;
+    rp.nselect = hr.nselect;
+    rp.ncell = (uint32_t)rp.nc[0] * (uint32_t)rp.nc[1] * (uint32_t)(h->dim == 3 ? rp.nc[2] : 1);
+    // certified FP32 thresholds
+    double wmax = 0.0, Lmax = 0.0;
+    for (int a = 0; a < h->dim; ++a) { wmax = std::max(wmax, rp.w[a]); Lmax = std::max(Lmax, rp.L[a]); }
+    Margins g = base_margins(h->dim, wmax, Lmax, rp.d, rp.tau, h->rc2);
+    double vm = 0.0, nm = 0.0, am = 0.0;
+    if (h->dim == 2) {
+        for (int k = 0; k < h->sh2.nv; ++k) {
+            vm = std::max({ vm, std::fabs(h->sh2.vx[k]), std::fabs(h->sh2.vy[k]) });
+            nm = std::max({ nm, std::fabs(h->sh2.nx[k]), std::fabs(h->sh2.ny[k]) });
+            am = std::max({ am, std::fabs(h->sh2.alo[k]), std::fabs(h->sh2.ahi[k]) });
+        }
+        g.e_sat = sat2_margin(g, h->Rc, vm, nm, am);
+    } else {
+        g.e_sat = 0.0;   // 3D filter margins are set by the 3D path
+    }
+    rp.in_lo = f32_up(g.e_in);
+    rp.out_lo = f32_down(-g.e_in);
+    for (int a = 0; a < 3; ++a) {
+        rp.in_hi[a] = f32_down(rp.w[a] - g.e_in);
+        rp.out_hi[a] = f32_up(rp.w[a] + g.e_in);
+    }
+    rp.cull_keep = f32_down(h->rc2 - g.e_cull);
+    rp.cull_skip = f32_up(h->rc2 + g.e_cull);
+    rp.sat_e = f32_up(g.e_sat);
+    rp.e_in = g.e_in;
+    rp.e_cull = g.e_cull;
+    rp.e_sat = g.e_sat;
+    return 0;
+}
+
+int check_moves(double d, double a, uint32_t nselect)
+{
+    if (!is_finite(d) || d < 0.0) return HPMC_ERR_INVALID_ARG;
+    if (!is_finite(a) || a < 0.0 || a >= 3.14159) return HPMC_ERR_INVALID_ARG;
+    if (nselect == 0 || nselect > 65535) return HPMC_ERR_INVALID_ARG;
+    return 0;
+}
+
+int check_config(int dim, const HostRep& hr, const double* pos, const double* orient)
+{
+    if (!pos || !orient) return HPMC_ERR_INVALID_ARG;
+    const int qd = dim == 2 ? 2 : 4;
+    for (uint32_t i = 0; i < hr.N; ++i) {
+        for (int a = 0; a < dim; ++a) {
+            const double x = pos[(size_t)i * dim + a];
+            if (!is_finite(x) || x < 0.0 || x >= hr.L[a]) return HPMC_ERR_INVALID_ARG;
+        }
+        double n2 = 0.0;
+        for (int a = 0; a < qd; ++a) {
+            const double q = orient[(size_t)i * qd + a];
+            if (!is_finite(q)) return HPMC_ERR_INVALID_ARG;
+            n2 += q * q;
+        }
+        if (std::fabs(n2 - 1.0) > 1e-6) return HPMC_ERR_INVALID_ARG;
+    }
+    return 0;
+}
+
+// the half-width of the rotation and the translation need the filter margins
+// recomputed; items per set depend only on the cell grid
+void build_item_tables(hpmc_batch* h, std::vector<uint32_t>& tab)
+{
+    tab.assign(6 * (h->R + 1), 0);
+    h->items_per_set.assign(6, 0);
+    for (int gi = 0; gi < 6; ++gi) {
+        const int S = 32 / kGroupSizes[gi];
+        uint32_t acc = 0;
+        for (uint32_t r = 0; r < h->R; ++r) {
+            tab[gi * (h->R + 1) + r] = acc;
+            const Rep& rp = h->reps[r];
+            const uint32_t nax = (uint32_t)rp.nc[0] / 2;
+            const uint32_t spr = (nax + S - 1) / S;
+            uint32_t rows = (uint32_t)rp.nc[1] / 2;
+            if (h->dim == 3) rows *= (uint32_t)rp.nc[2] / 2;
+            acc += rows * spr;
+        }
+        tab[gi * (h->R + 1) + h->R] = acc;
+        h->items_per_set[gi] = acc;
+    }
+}
+
+void invalidate_graph(hpmc_batch* h)
+{
+    h->cfg_valid = false;
+    for (int p = 0; p < 2; ++p) {
+        if (h->graph[p]) {
+            cudaGraphExecDestroy(h->graph[p]);
+            h->graph[p] = nullptr;
+        }
+    }
+}
+
+int upload_reps(hpmc_batch* h, cudaStream_t st)
+{
+    CK(cudaMemcpyAsync((void*)h->dv.reps, h->reps.data(), sizeof(Rep) * h->R, cudaMemcpyHostToDevice, st));
+    return 0;
+}
+
+SetKernel pick_kernel(const hpmc_batch* h)
+{
+    const bool f32 = h->precision == HPMC_FP32_FILTERED;
+    if (h->dim == 2) {
+        const bool fixed = h->nv == 5;
+        return f32 ? set2d_f32_kernel(h->G, fixed) : set2d_f64_kernel(h->G, fixed);
+    }
+    const bool fixed = h->nv == 8;
+    return f32 ? set3d_f32_kernel(h->G, fixed) : set3d_f64_kernel(h->G, fixed);
+}
+
+// enqueue the rebuild of the cell list from buffer `cur` into cur ^ 1
+int enqueue_rebuild(hpmc_batch* h, cudaStream_t st, bool with_shift)
+{
+    const int T = 256;
+    if (with_shift) k_shift<<<(h->R + 127) / 128, 128, 0, st>>>(h->dv);
+    k_count<<<(h->ntot + T - 1) / T, T, 0, st>>>(h->dv, h->cur);
+    k_scan_tiles<<<h->ntiles, kScanThreads, 0, st>>>(h->dv);
+    if (h->ntiles > 1) {
+        k_scan_sums<<<1, kScanThreads, 0, st>>>(h->dv, h->ntiles);
+        k_scan_add<<<(h->ctot + T - 1) / T, T, 0, st>>>(h->dv);
+    }
+    k_scatter_tags<<<(h->ntot + T - 1) / T, T, 0, st>>>(h->dv, h->cur);
+    k_place<<<(h->ntot + T - 1) / T, T, 0, st>>>(h->dv, h->cur);
+    CK(cudaGetLastError());
+    return 0;
+}
+
+int prepare_set(hpmc_batch* h)
+{
+    if (h->cfg_valid) return 0;
+    const SetKernel K = pick_kernel(h);
+    if (!K.fn) return HPMC_ERR_INVALID_ARG;
+    const int gi = gidx_of(h->G);
+    const uint32_t items = h->items_per_set[gi];
+    const size_t smem = K.smem_per_warp * (size_t)h->wpb;
+    const uint32_t blocks_needed = (items + h->wpb - 1) / h->wpb;
+    int per_sm = 0;
+    CK(cudaFuncSetAttribute(K.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, K.fn, 32 * h->wpb, smem));
+    if (per_sm < 1) return HPMC_ERR_INVALID_ARG;
+    h->cfg_fn = K.fn;
+    h->cfg_smem = smem;
+    h->cfg_grid = std::max<uint32_t>(1, std::min<uint32_t>(blocks_needed, (uint32_t)(per_sm * h->num_sms)));
+    h->cfg_valid = true;
+    return 0;
+}
+
+int enqueue_sweep(hpmc_batch* h, cudaStream_t st)
+{
+    int rc = prepare_set(h);
+    if (rc) return rc;
+    rc = enqueue_rebuild(h, st, true);
+    if (rc) return rc;
+    const int nxt = h->cur ^ 1;
+    const int gi = gidx_of(h->G);
+    const uint32_t* ib = h->item_base_dev + (size_t)gi * (h->R + 1);
+    const int nsets = 1 << h->dim;
+    for (int sigma = 0; sigma < nsets; ++sigma) {
+        void* args[5];
+        int nx = nxt, sg = sigma;
+        args[0] = &h->dv;
+        args[1] = h->dim == 2 ? (void*)&h->sh2 : (void*)&h->sh3;
+        args[2] = &nx;
+        args[3] = &sg;
+        args[4] = (void*)&ib;
+        CK(cudaLaunchKernel(h->cfg_fn, dim3(h->cfg_grid), dim3(32 * h->wpb), args, h->cfg_smem, st));
+    }
+    h->cur = nxt;
+    return 0;
+}
+
+// unsorted copy of the state (tag order) into buffer cur ^ 1
+__global__ void k_unsort(Dev dv, int cur)
+{
+    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= dv.ntot) return;
+    const Bufs& S = dv.buf[cur];
+    const Bufs& D = dv.buf[cur ^ 1];
+    const uint32_t r = dv.rep_of[i];
+    const uint32_t o = dv.reps[r].pbase + S.tag[i];
+    D.px[o] = S.px[i];
+    D.py[o] = S.py[i];
+    D.q0[o] = S.q0[i];
+    D.q1[o] = S.q1[i];
+    D.tag[o] = S.tag[i];
+    if (dv.dim == 3) {
+        D.pz[o] = S.pz[i];
+        D.q2[o] = S.q2[i];
+        D.q3[o] = S.q3[i];
+    }
+}
+
+__global__ void k_identity_tags(Dev dv, int cur)
+{
+    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= dv.ntot) return;
+    dv.buf[cur].tag[i] = i - dv.reps[dv.rep_of[i]].pbase;
+}
+
+int read_error(hpmc_batch* h)
+{
+    int e = 0;
+    CK(cudaMemcpy(&e, h->dv.error, sizeof(int), cudaMemcpyDeviceToHost));
+    if (e) {
+        CK(cudaMemset(h->dv.error, 0, sizeof(int)));
+        if (e & ERR_TIMEOUT) return HPMC_ERR_TIMEOUT;
+        return HPMC_ERR_CAPACITY;
+    }
+    int p = h->pending_error;
+    h->pending_error = 0;
+    return p;
+}
+
+// copy a state in tag order into buffer cur (all replicas, concatenated)
+int upload_all(hpmc_batch* h, const double* pos, const double* orient, cudaStream_t st)
+{
+    const int dim = h->dim, qd = dim == 2 ? 2 : 4;
+    const size_t n = h->ntot;
+    std::vector<double> col(n);
+    Bufs& B = h->dv.buf[h->cur];
+    double* dst_p[3] = { B.px, B.py, B.pz };
+    double* dst_q[4] = { B.q0, B.q1, B.q2, B.q3 };
+    for (int a = 0; a < dim; ++a) {
+        for (size_t i = 0; i < n; ++i) col[i] = pos[i * dim + a];
+        CK(cudaMemcpyAsync(dst_p[a], col.data(), n * sizeof(double), cudaMemcpyHostToDevice, st));
+        CK(cudaStreamSynchronize(st));
+    }
+    for (int a = 0; a < qd; ++a) {
+        for (size_t i = 0; i < n; ++i) col[i] = orient[i * qd + a];
+        CK(cudaMemcpyAsync(dst_q[a], col.data(), n * sizeof(double), cudaMemcpyHostToDevice, st));
+        CK(cudaStreamSynchronize(st));
+    }
+    k_identity_tags<<<(h->ntot + 255) / 256, 256, 0, st>>>(h->dv, h->cur);
+    CK(cudaGetLastError());
+    return 0;
+}
+
+}  // namespace
+
+// ======================================================================= ABI
+extern "C" {
+
+const char* hpmc_strerror(int code)
+{
+    switch (code) {
+    case HPMC_OK: return "ok";
+    case HPMC_ERR_INVALID_ARG: return "invalid argument";
+    case HPMC_ERR_BOX_TOO_SMALL: return "box too small: fewer than 4 cells on an axis";
+    case HPMC_ERR_OVERLAP: return "overlapping configuration";
+    case HPMC_ERR_OOM: return "device allocation failed";
+    case HPMC_ERR_CUDA: return "CUDA runtime error";
+    case HPMC_ERR_TIMEOUT: return "bounded device wait gave up";
+    case HPMC_ERR_CAPACITY: return "a cell stencil exceeded the staging capacity";
+    case HPMC_ERR_NOT_READY: return "call order violated";
+    default: return "unknown error";
+    }
+}
+
+int hpmc_batch_create(int dim, const double* verts, uint32_t nv, double w_min, uint32_t R,
+                      const hpmc_replica_desc_t* reps, hpmc_t* out)
+{
+    if (!out || !reps || R == 0) return HPMC_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (!is_finite(w_min) || w_min < 0.0) return HPMC_ERR_INVALID_ARG;
+    hpmc_batch* h = new (std::nothrow) hpmc_batch();
+    if (!h) return HPMC_ERR_OOM;
+    int rc = shape_setup(h, dim, verts, nv);
+    if (rc) { delete h; return rc; }
+    h->w_min = w_min;
+    h->R = R;
+    h->hr.resize(R);
+    h->reps.resize(R);
+    uint64_t ntot = 0, ctot = 0;
+    for (uint32_t r = 0; r < R; ++r) {
+        const hpmc_replica_desc_t& d = reps[r];
+        HostRep& hr = h->hr[r];
+        if (d.N == 0) { delete h; return HPMC_ERR_INVALID_ARG; }
+        hr.N = d.N;
+        for (int a = 0; a < 3; ++a) hr.L[a] = d.box[a];
+        hr.seed = d.seed;
+        hr.d = d.d;
+        hr.a = d.a;
+        hr.nselect = d.nselect;
+        rc = check_moves(d.d, d.a, d.nselect);
+        if (!rc) rc = rep_geometry(h, hr, h->reps[r]);
+        if (!rc) rc = check_config(dim, hr, d.pos, d.orient);
+        if (rc) { delete h; return rc; }
+        h->reps[r].pbase = (uint32_t)ntot;
+        h->reps[r].cbase = (uint32_t)ctot;
+        ntot += d.N;
+        ctot += h->reps[r].ncell;
+        if (ntot > 0x7fffffffull || ctot > 0x7fffffffull) { delete h; return HPMC_ERR_INVALID_ARG; }
+    }
+    h->ntot = (uint32_t)ntot;
+    h->ctot = (uint32_t)ctot;
+    h->ntiles = (h->ctot + kScanTile - 1) / kScanTile;
+    int dev = 0;
+    cudaError_t ce = cudaGetDevice(&dev);
+    if (ce == cudaSuccess) ce = cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, dev);
+    if (ce != cudaSuccess) { delete h; return cuda_fail(ce); }
+
+    Dev& dv = h->dv;
+    dv.dim = dim;
+    dv.R = R;
+    dv.ntot = h->ntot;
+    dv.ctot = h->ctot;
+    auto fail = [&](int code) { hpmc_destroy(h); return code; };
+    Rep* reps_dev = nullptr;
+    uint32_t* rep_of = nullptr;
+    if ((rc = dalloc(h, &reps_dev, R))) return fail(rc);
+    dv.reps = reps_dev;
+    if ((rc = dalloc(h, &rep_of, h->ntot))) return fail(rc);
+    dv.rep_of = rep_of;
+    for (int b = 0; b < 2; ++b) {
+        Bufs& B = dv.buf[b];
+        if ((rc = dalloc(h, &B.px, h->ntot)) || (rc = dalloc(h, &B.py, h->ntot)) ||
+            (rc = dalloc(h, &B.q0, h->ntot)) || (rc = dalloc(h, &B.q1, h->ntot)) ||
+            (rc = dalloc(h, &B.f4a, h->ntot)) || (rc = dalloc(h, &B.tag, h->ntot)))
+            return fail(rc);
+        if (dim == 3) {
+            if ((rc = dalloc(h, &B.pz, h->ntot)) || (rc = dalloc(h, &B.q2, h->ntot)) ||
+                (rc = dalloc(h, &B.q3, h->ntot)) || (rc = dalloc(h, &B.f4b, h->ntot)))
+                return fail(rc);
+        }
+    }
+    if ((rc = dalloc(h, &dv.count, h->ctot)) || (rc = dalloc(h, &dv.start, (size_t)h->ctot + 1)) ||
+        (rc = dalloc(h, &dv.tile_sums, h->ntiles)) || (rc = dalloc(h, &dv.cellid, h->ntot)) ||
+        (rc = dalloc(h, &dv.slot, h->ntot)) || (rc = dalloc(h, &dv.tmp_tag, h->ntot)) ||
+        (rc = dalloc(h, &dv.shift, 3 * (size_t)R)) || (rc = dalloc(h, &dv.sweep, R)) ||
+        (rc = dalloc(h, &dv.counters, (size_t)R * kNumCounters)) || (rc = dalloc(h, &dv.error, 1)) ||
+        (rc = dalloc(h, &h->item_base_dev, 6 * ((size_t)R + 1))) || (rc = dalloc(h, &h->check_out, 1)))
+        return fail(rc);
+
+    std::vector<uint32_t> tab;
+    build_item_tables(h, tab);
+    std::vector<uint32_t> ro(h->ntot);
+    for (uint32_t r = 0; r < R; ++r)
+        for (uint32_t i = 0; i < h->hr[r].N; ++i) ro[h->reps[r].pbase + i] = r;
+    const uint32_t nt = h->ntot;
+    cudaError_t e = cudaSuccess;
+    if (e == cudaSuccess) e = cudaMemcpy(rep_of, ro.data(), sizeof(uint32_t) * nt, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(h->item_base_dev, tab.data(), sizeof(uint32_t) * tab.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(reps_dev, h->reps.data(), sizeof(Rep) * R, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemset(dv.count, 0, sizeof(uint32_t) * h->ctot);
+    if (e == cudaSuccess) e = cudaMemcpy(dv.start + h->ctot, &nt, sizeof(uint32_t), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemset(dv.sweep, 0, sizeof(uint64_t) * R);
+    if (e == cudaSuccess) e = cudaMemset(dv.counters, 0, sizeof(unsigned long long) * R * kNumCounters);
+    if (e == cudaSuccess) e = cudaMemset(dv.error, 0, sizeof(int));
+    if (e != cudaSuccess) return fail(cuda_fail(e));
+    // initial configuration (tag order) into buffer 0
+    std::vector<double> P((size_t)h->ntot * dim), Q((size_t)h->ntot * (dim == 2 ? 2 : 4));
+    const int qd = dim == 2 ? 2 : 4;
+    for (uint32_t r = 0; r < R; ++r) {
+        std::memcpy(P.data() + (size_t)h->reps[r].pbase * dim, reps[r].pos, sizeof(double) * reps[r].N * dim);
+        std::memcpy(Q.data() + (size_t)h->reps[r].pbase * qd, reps[r].orient, sizeof(double) * reps[r].N * qd);
+    }
+    h->cur = 0;
+    if ((rc = upload_all(h, P.data(), Q.data(), 0))) return fail(rc);
+    e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) return fail(cuda_fail(e));
+    *out = h;
+    return 0;
+}
+
+int hpmc_create(const double* box, int dim, uint32_t N, const double* verts, uint32_t nv,
+                const double* pos, const double* orient, uint64_t seed, double w_min, hpmc_t* out)
+{
+    if (!box) return HPMC_ERR_INVALID_ARG;
+    hpmc_replica_desc_t d{};
+    d.N = N;
+    for (int a = 0; a < 3; ++a) d.box[a] = (a < dim) ? box[a] : 1.0;
+    d.pos = pos;
+    d.orient = orient;
+    d.seed = seed;
+    d.d = 0.1;
+    d.a = 0.1;
+    d.nselect = 4;
+    return hpmc_batch_create(dim, verts, nv, w_min, 1, &d, out);
+}
+
+int hpmc_destroy(hpmc_t h)
+{
+    if (!h) return HPMC_ERR_INVALID_ARG;
+    cudaDeviceSynchronize();
+    invalidate_graph(h);
+    if (h->graph_stream) cudaStreamDestroy(h->graph_stream);
+    for (void* p : h->allocs) cudaFree(p);
+    delete h;
+    return 0;
+}
+
+int hpmc_set_moves(hpmc_t h, int32_t r, double d, double a, uint32_t nselect)
+{
+    if (!h) return HPMC_ERR_INVALID_ARG;
+    int rc = check_moves(d, a, nselect);
+    if (rc) return rc;
+    if (r >= (int32_t)h->R || r < -1) return HPMC_ERR_INVALID_ARG;
+    CK(cudaDeviceSynchronize());
+    for (uint32_t i = 0; i < h->R; ++i) {
+        if (r >= 0 && (uint32_t)r != i) continue;
+        h->hr[i].d = d;
+        h->hr[i].a = a;
+        h->hr[i].nselect = nselect;
+        const uint32_t pb = h->reps[i].pbase, cb = h->reps[i].cbase;
+        rc = rep_geometry(h, h->hr[i], h->reps[i]);
+        h->reps[i].pbase = pb;
+        h->reps[i].cbase = cb;
+        if (rc) return rc;
+    }
+    invalidate_graph(h);
+    rc = upload_reps(h, 0);
+    if (rc) return rc;
+    CK(cudaDeviceSynchronize());
+    return 0;
+}
+
+int hpmc_set_precision(hpmc_t h, int mode)
+{
+    if (!h || (mode != HPMC_FP64 && mode != HPMC_FP32_FILTERED)) return HPMC_ERR_INVALID_ARG;
+    h->precision = mode;
+    invalidate_graph(h);
+    return 0;
+}
+
+int hpmc_set_group_size(hpmc_t h, int lanes_per_cell, int warps_per_block)
+{
+    if (!h || gidx_of(lanes_per_cell) < 0 || warps_per_block < 1 || warps_per_block > 16)
+        return HPMC_ERR_INVALID_ARG;
+    const SetKernel K = [&] {
+        const int G0 = h->G;
+        h->G = lanes_per_cell;
+        SetKernel k = pick_kernel(h);
+        h->G = G0;
+        return k;
+    }();
+    if (!K.fn || K.smem_per_warp * (size_t)warps_per_block > 227 * 1024) return HPMC_ERR_INVALID_ARG;
+    h->G = lanes_per_cell;
+    h->wpb = warps_per_block;
+    invalidate_graph(h);
+    return 0;
+}
+
+int hpmc_sweep(hpmc_t h, uint32_t n, void* stream)
+{
+    if (!h) return HPMC_ERR_INVALID_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    h->last_stream = st;
+    for (uint32_t s = 0; s < n; ++s) {
+        int rc = enqueue_sweep(h, st);
+        if (rc) return rc;
+    }
+    return 0;
+}
+
+int hpmc_sweep_graph(hpmc_t h, uint32_t n, void* stream)
+{
+    if (!h) return HPMC_ERR_INVALID_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    h->last_stream = st;
+    if (n >= 2 && !h->graph[h->cur]) {
+        int prc = prepare_set(h);
+        if (prc) return prc;
+        if (!h->graph_stream) CK(cudaStreamCreateWithFlags(&h->graph_stream, cudaStreamNonBlocking));
+        CK(cudaStreamSynchronize(st));
+        const int cur0 = h->cur;
+        CK(cudaStreamBeginCapture(h->graph_stream, cudaStreamCaptureModeThreadLocal));
+        int rc = enqueue_sweep(h, h->graph_stream);
+        if (!rc) rc = enqueue_sweep(h, h->graph_stream);
+        cudaGraph_t g = nullptr;
+        cudaError_t e = cudaStreamEndCapture(h->graph_stream, &g);
+        h->cur = cur0;
+        if (rc) { if (g) cudaGraphDestroy(g); return rc; }
+        if (e != cudaSuccess) return cuda_fail(e);
+        e = cudaGraphInstantiate(&h->graph[cur0], g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) { h->graph[cur0] = nullptr; return cuda_fail(e); }
+    }
+    uint32_t s = 0;
+    for (; s + 2 <= n; s += 2) CK(cudaGraphLaunch(h->graph[h->cur], st));
+    if (s < n) {
+        int rc = enqueue_sweep(h, st);
+        if (rc) return rc;
+    }
+    return 0;
+}
+
+int hpmc_sync(hpmc_t h)
+{
+    if (!h) return HPMC_ERR_INVALID_ARG;
+    CK(cudaDeviceSynchronize());
+    return read_error(h);
+}
+
+int hpmc_counters(hpmc_t h, int32_t r, hpmc_counters_t* out)
+{
+    if (!h || !out || r < -1 || r >= (int32_t)h->R) return HPMC_ERR_INVALID_ARG;
+    CK(cudaDeviceSynchronize());
+    std::vector<unsigned long long> c((size_t)h->R * kNumCounters);
+    CK(cudaMemcpy(c.data(), h->dv.counters, sizeof(unsigned long long) * c.size(), cudaMemcpyDeviceToHost));
+    unsigned long long s[kNumCounters] = {};
+    for (uint32_t i = 0; i < h->R; ++i) {
+        if (r >= 0 && (uint32_t)r != i) continue;
+        for (int k = 0; k < kNumCounters; ++k) s[k] += c[(size_t)i * kNumCounters + k];
+    }
+    out->moves = s[CNT_MOVES];
+    out->accept = s[CNT_ACCEPT];
+    out->reject_overlap = s[CNT_REJ_OVERLAP];
+    out->reject_boundary = s[CNT_REJ_BOUNDARY];
+    out->cull_pairs = s[CNT_CULL];
+    out->overlap_checks = s[CNT_CHECKS];
+    out->fp64_rechecks = s[CNT_RECHECK];
+    out->gjk_cap = s[CNT_GJKCAP];
+    return read_error(h);
+}
+
+int hpmc_reset_counters(hpmc_t h)
+{
+    if (!h) return HPMC_ERR_INVALID_ARG;
+    CK(cudaDeviceSynchronize());
+    CK(cudaMemset(h->dv.counters, 0, sizeof(unsigned long long) * h->R * kNumCounters));
+    return 0;
+}
+
+int hpmc_check_overlaps(hpmc_t h, int32_t r, uint64_t* n_pairs)
+{
+    if (!h || !n_pairs || r < -1 || r >= (int32_t)h->R) return HPMC_ERR_INVALID_ARG;
+    CK(cudaDeviceSynchronize());
+    // a cell list with a zero shift, then every pair of stencil neighbours
+    CK(cudaMemset(h->dv.shift, 0, sizeof(double) * 3 * h->R));
+    int rc = enqueue_rebuild(h, 0, false);
+    if (rc) return rc;
+    h->cur ^= 1;
+    CK(cudaMemset(h->check_out, 0, sizeof(unsigned long long)));
+    const int T = 128;
+    if (h->dim == 2) {
+        if (h->nv == 5) k_check2d<5><<<(h->ntot + T - 1) / T, T>>>(h->dv, h->sh2, h->cur, r, h->check_out);
+        else k_check2d<0><<<(h->ntot + T - 1) / T, T>>>(h->dv, h->sh2, h->cur, r, h->check_out);
+    } else {
+        rc = hpmc_check3d_launch(h->dv, h->sh3, h->cur, r, h->check_out, h->ntot);
+        if (rc) return rc;
+    }
+    CK(cudaGetLastError());
+    unsigned long long n = 0;
+    CK(cudaMemcpy(&n, h->check_out, sizeof(n), cudaMemcpyDeviceToHost));
+    *n_pairs = n;
+    return read_error(h);
+}
+
+int hpmc_get_state(hpmc_t h, int32_t r, double* pos, double* orient, uint64_t* sweep)
+{
+    if (!h || r < 0 || r >= (int32_t)h->R) return HPMC_ERR_INVALID_ARG;
+    CK(cudaDeviceSynchronize());
+    k_unsort<<<(h->ntot + 255) / 256, 256>>>(h->dv, h->cur);
+    CK(cudaGetLastError());
+    CK(cudaDeviceSynchronize());
+    const Bufs& D = h->dv.buf[h->cur ^ 1];
+    const uint32_t N = h->hr[r].N, pb = h->reps[r].pbase;
+    const int dim = h->dim, qd = dim == 2 ? 2 : 4;
+    std::vector<double> col(N);
+    const double* src_p[3] = { D.px, D.py, D.pz };
+    const double* src_q[4] = { D.q0, D.q1, D.q2, D.q3 };
+    if (pos) {
+        for (int a = 0; a < dim; ++a) {
+            CK(cudaMemcpy(col.data(), src_p[a] + pb, sizeof(double) * N, cudaMemcpyDeviceToHost));
+            for (uint32_t i = 0; i < N; ++i) pos[(size_t)i * dim + a] = col[i];
+        }
+    }
+    if (orient) {
+        for (int a = 0; a < qd; ++a) {
+            CK(cudaMemcpy(col.data(), src_q[a] + pb, sizeof(double) * N, cudaMemcpyDeviceToHost));
+            for (uint32_t i = 0; i < N; ++i) orient[(size_t)i * qd + a] = col[i];
+        }
+    }
+    if (sweep) CK(cudaMemcpy(sweep, h->dv.sweep + r, sizeof(uint64_t), cudaMemcpyDeviceToHost));
+    return read_error(h);
+}
+
+int hpmc_set_state(hpmc_t h, int32_t r, const double* pos, const double* orient, uint64_t sweep)
+{
+    if (!h || r < 0 || r >= (int32_t)h->R) return HPMC_ERR_INVALID_ARG;
+    int rc = check_config(h->dim, h->hr[r], pos, orient);
+    if (rc) return rc;
+    CK(cudaDeviceSynchronize());
+    // bring every replica to tag order in buffer cur ^ 1, overwrite replica r,
+    // then make that buffer current
+    k_unsort<<<(h->ntot + 255) / 256, 256>>>(h->dv, h->cur);
+    CK(cudaGetLastError());
+    CK(cudaDeviceSynchronize());
+    h->cur ^= 1;
+    const Bufs& D = h->dv.buf[h->cur];
+    const uint32_t N = h->hr[r].N, pb = h->reps[r].pbase;
+    const int dim = h->dim, qd = dim == 2 ? 2 : 4;
+    std::vector<double> col(N);
+    double* dst_p[3] = { D.px, D.py, D.pz };
+    double* dst_q[4] = { D.q0, D.q1, D.q2, D.q3 };
+    for (int a = 0; a < dim; ++a) {
+        for (uint32_t i = 0; i < N; ++i) col[i] = pos[(size_t)i * dim + a];
+        CK(cudaMemcpy(dst_p[a] + pb, col.data(), sizeof(double) * N, cudaMemcpyHostToDevice));
+    }
+    for (int a = 0; a < qd; ++a) {
+        for (uint32_t i = 0; i < N; ++i) col[i] = orient[(size_t)i * qd + a];
+        CK(cudaMemcpy(dst_q[a] + pb, col.data(), sizeof(double) * N, cudaMemcpyHostToDevice));
+    }
+    CK(cudaMemcpy(h->dv.sweep + r, &sweep, sizeof(uint64_t), cudaMemcpyHostToDevice));
+    invalidate_graph(h);
+    return 0;
+}
+
+int hpmc_run_host(hpmc_t h, const double* pos, const double* orient, uint32_t n, double* pos_out,
+                  double* orient_out, hpmc_counters_t* out, void* stream)
+{
+    if (!h || !pos || !orient || !pos_out || !orient_out) return HPMC_ERR_INVALID_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    const int dim = h->dim, qd = dim == 2 ? 2 : 4;
+    const size_t N = h->ntot;
+    // upload (tag order) into the current buffer
+    Bufs& B = h->dv.buf[h->cur];
+    double* dst_p[3] = { B.px, B.py, B.pz };
+    double* dst_q[4] = { B.q0, B.q1, B.q2, B.q3 };
+    std::vector<double> col(N);
+    for (int a = 0; a < dim; ++a) {
+        for (size_t i = 0; i < N; ++i) col[i] = pos[i * dim + a];
+        CK(cudaMemcpyAsync(dst_p[a], col.data(), N * sizeof(double), cudaMemcpyHostToDevice, st));
+        CK(cudaStreamSynchronize(st));
+    }
+    for (int a = 0; a < qd; ++a) {
+        for (size_t i = 0; i < N; ++i) col[i] = orient[i * qd + a];
+        CK(cudaMemcpyAsync(dst_q[a], col.data(), N * sizeof(double), cudaMemcpyHostToDevice, st));
+        CK(cudaStreamSynchronize(st));
+    }
+    k_identity_tags<<<(h->ntot + 255) / 256, 256, 0, st>>>(h->dv, h->cur);
+    CK(cudaGetLastError());
+    int rc = hpmc_sweep_graph(h, n, stream);
+    if (rc) return rc;
+    k_unsort<<<(h->ntot + 255) / 256, 256, 0, st>>>(h->dv, h->cur);
+    CK(cudaGetLastError());
+    const Bufs& D = h->dv.buf[h->cur ^ 1];
+    const double* src_p[3] = { D.px, D.py, D.pz };
+    const double* src_q[4] = { D.q0, D.q1, D.q2, D.q3 };
+    for (int a = 0; a < dim; ++a) {
+        CK(cudaMemcpyAsync(col.data(), src_p[a], N * sizeof(double), cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        for (size_t i = 0; i < N; ++i) pos_out[i * dim + a] = col[i];
+    }
+    for (int a = 0; a < qd; ++a) {
+        CK(cudaMemcpyAsync(col.data(), src_q[a], N * sizeof(double), cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        for (size_t i = 0; i < N; ++i) orient_out[i * qd + a] = col[i];
+    }
+    if (out) return hpmc_counters(h, -1, out);
+    return read_error(h);
+}
+
+int hpmc_autotune(hpmc_t h, uint32_t n_trial, int* best_lanes, int* best_warps)
+{
+    if (!h || n_trial == 0) return HPMC_ERR_INVALID_ARG;
+    CK(cudaDeviceSynchronize());
+    const int qd = h->dim == 2 ? 2 : 4;
+    const size_t N = h->ntot;
+    // save the state in tag order and the sweep counters
+    std::vector<double> P(N * h->dim), Q(N * qd);
+    std::vector<uint64_t> sw(h->R);
+    std::vector<unsigned long long> cnt((size_t)h->R * kNumCounters);
+    k_unsort<<<(h->ntot + 255) / 256, 256>>>(h->dv, h->cur);
+    CK(cudaDeviceSynchronize());
+    {
+        const Bufs& D = h->dv.buf[h->cur ^ 1];
+        const double* sp[3] = { D.px, D.py, D.pz };
+        const double* sq[4] = { D.q0, D.q1, D.q2, D.q3 };
+        std::vector<double> col(N);
+        for (int a = 0; a < h->dim; ++a) {
+            CK(cudaMemcpy(col.data(), sp[a], N * sizeof(double), cudaMemcpyDeviceToHost));
+            for (size_t i = 0; i < N; ++i) P[i * h->dim + a] = col[i];
+        }
+        for (int a = 0; a < qd; ++a) {
+            CK(cudaMemcpy(col.data(), sq[a], N * sizeof(double), cudaMemcpyDeviceToHost));
+            for (size_t i = 0; i < N; ++i) Q[i * qd + a] = col[i];
+        }
+    }
+    CK(cudaMemcpy(sw.data(), h->dv.sweep, sizeof(uint64_t) * h->R, cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(cnt.data(), h->dv.counters, sizeof(unsigned long long) * cnt.size(), cudaMemcpyDeviceToHost));
+    const int G0 = h->G, W0 = h->wpb;
+    float best_ms = 1e30f;
+    int bg = G0, bw = W0;
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    const int wpbs[3] = { 2, 4, 8 };
+    for (int gi = 0; gi < 6; ++gi) {
+        for (int wi = 0; wi < 3; ++wi) {
+            if (hpmc_set_group_size(h, kGroupSizes[gi], wpbs[wi]) != 0) continue;
+            int rc = hpmc_sweep(h, 1, nullptr);      // warm-up
+            if (rc) continue;
+            CK(cudaEventRecord(e0));
+            rc = hpmc_sweep(h, n_trial, nullptr);
+            CK(cudaEventRecord(e1));
+            CK(cudaEventSynchronize(e1));
+            if (rc) continue;
+            float ms = 0.f;
+            CK(cudaEventElapsedTime(&ms, e0, e1));
+            if (ms < best_ms) { best_ms = ms; bg = kGroupSizes[gi]; bw = wpbs[wi]; }
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    h->G = bg;
+    h->wpb = bw;
+    invalidate_graph(h);
+    // restore
+    CK(cudaDeviceSynchronize());
+    int rc = upload_all(h, P.data(), Q.data(), 0);
+    if (rc) return rc;
+    CK(cudaMemcpy(h->dv.sweep, sw.data(), sizeof(uint64_t) * h->R, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(h->dv.counters, cnt.data(), sizeof(unsigned long long) * cnt.size(), cudaMemcpyHostToDevice));
+    CK(cudaDeviceSynchronize());
+    if (best_lanes) *best_lanes = bg;
+    if (best_warps) *best_warps = bw;
+    return read_error(h);
+}
+
+int hpmc_geometry(hpmc_t h, int32_t r, int32_t* nc, double* w, double* R)
+{
+    if (!h || r < 0 || r >= (int32_t)h->R) return HPMC_ERR_INVALID_ARG;
+    for (int a = 0; a < 3; ++a) {
+        if (nc) nc[a] = h->reps[r].nc[a];
+        if (w) w[a] = h->reps[r].w[a];
+    }
+    if (R) *R = h->Rc;
+    return 0;
+}
+
+int hpmc_launches_per_sweep(hpmc_t h, uint32_t* n)
+{
+    if (!h || !n) return HPMC_ERR_INVALID_ARG;
+    *n = 5 + (h->ntiles > 1 ? 2 : 0) + (1u << h->dim);
+    return 0;
+}
+
+int hpmc_filter_margins(hpmc_t h, int32_t r, double* e_in, double* e_cull, double* e_overlap)
+{
+    if (!h || r < 0 || r >= (int32_t)h->R) return HPMC_ERR_INVALID_ARG;
+    if (e_in) *e_in = h->reps[r].e_in;
+    if (e_cull) *e_cull = h->reps[r].e_cull;
+    if (e_overlap) *e_overlap = h->reps[r].e_sat;
+    return 0;
+}
+
+}  // extern "C"

@@ -1,0 +1,230 @@
+// hpmc_rebuild.cuh -- per-sweep grid shift and cell-list rebuild (Sec. 2.2.1,
+// Sec. 2.5.1): count with atomic arrival slots, exclusive scan, scatter of
+// tags, then a canonical placement (rank of the tag among the cell's tags)
+// that gathers the state into the other buffer in cell-sorted order and
+// refreshes the FP32 cell-relative mirror.
+#pragma once
+#include "hpmc_device.cuh"
+
+namespace hpmc {
+
+constexpr int kScanThreads = 1024;
+constexpr int kScanItems = 4;
+constexpr int kScanTile = kScanThreads * kScanItems;
+
+// One thread per replica: the grid shift of the sweep about to run, and the
+// sweep counter advance (the running sweep is sweep[r] - 1 afterwards).
+__global__ void k_shift(Dev dv)
+{
+    const uint32_t r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= dv.R) return;
+    const Rep& rp = dv.reps[r];
+    const uint64_t sweep = dv.sweep[r];
+    const uint4 b0 = shift_block(rp.seed, sweep, 0);
+    dv.shift[3 * r + 0] = rp.w[0] * u53(b0.x, b0.y);
+    dv.shift[3 * r + 1] = rp.w[1] * u53(b0.z, b0.w);
+    if (dv.dim == 3) {
+        const uint4 b1 = shift_block(rp.seed, sweep, 1);
+        dv.shift[3 * r + 2] = rp.w[2] * u53(b1.x, b1.y);
+    } else {
+        dv.shift[3 * r + 2] = 0.0;
+    }
+    dv.sweep[r] = sweep + 1;
+}
+
+// Cell of every particle of buffer `cur` and its arrival slot in the cell.
+__global__ void k_count(Dev dv, int cur)
+{
+    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= dv.ntot) return;
+    const uint32_t r = dv.rep_of[i];
+    const Rep& rp = dv.reps[r];
+    const Bufs& B = dv.buf[cur];
+    const int ix = cell_axis(B.px[i], dv.shift[3 * r], rp.L[0], rp.inv_w[0], rp.nc[0]);
+    const int iy = cell_axis(B.py[i], dv.shift[3 * r + 1], rp.L[1], rp.inv_w[1], rp.nc[1]);
+    int iz = 0;
+    if (dv.dim == 3) iz = cell_axis(B.pz[i], dv.shift[3 * r + 2], rp.L[2], rp.inv_w[2], rp.nc[2]);
+    const uint32_t c = rp.cbase + (uint32_t)ix + (uint32_t)rp.nc[0] * ((uint32_t)iy + (uint32_t)rp.nc[1] * (uint32_t)iz);
+    dv.cellid[i] = c;
+    dv.slot[i] = atomicAdd(dv.count + c, 1u);
+}
+
+// Block-wide exclusive scan of one tile of `count` into `start`; the tile
+// total goes to tile_sums[tile].  The counts are zeroed for the next sweep.
+__global__ void __launch_bounds__(kScanThreads) k_scan_tiles(Dev dv)
+{
+    __shared__ uint32_t wsum[kScanThreads / 32];
+    const uint32_t base = blockIdx.x * kScanTile + threadIdx.x * kScanItems;
+    uint32_t v[kScanItems];
+    uint32_t tsum = 0;
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) {
+        const uint32_t i = base + k;
+        v[k] = (i < dv.ctot) ? dv.count[i] : 0u;
+        tsum += v[k];
+    }
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) {
+        const uint32_t i = base + k;
+        if (i < dv.ctot) dv.count[i] = 0u;
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t incl = tsum;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t t = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += t;
+    }
+    if (lane == 31) wsum[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+        uint32_t w = wsum[lane];
+        uint32_t wi = w;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t t = __shfl_up_sync(0xffffffffu, wi, o);
+            if (lane >= o) wi += t;
+        }
+        wsum[lane] = wi - w;
+        if (lane == 31) dv.tile_sums[blockIdx.x] = wi;
+    }
+    __syncthreads();
+    uint32_t run = wsum[warp] + incl - tsum;
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) {
+        const uint32_t i = base + k;
+        if (i < dv.ctot) dv.start[i] = run;
+        run += v[k];
+    }
+}
+
+// Exclusive scan of the tile totals in place (single block, loops if needed).
+__global__ void __launch_bounds__(kScanThreads) k_scan_sums(Dev dv, uint32_t ntiles)
+{
+    __shared__ uint32_t wsum[kScanThreads / 32];
+    __shared__ uint32_t carry;
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (uint32_t b = 0; b < ntiles; b += kScanThreads) {
+        const uint32_t i = b + threadIdx.x;
+        const uint32_t x = i < ntiles ? dv.tile_sums[i] : 0u;
+        uint32_t incl = x;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t t = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += t;
+        }
+        if (lane == 31) wsum[warp] = incl;
+        __syncthreads();
+        if (warp == 0) {
+            uint32_t w = wsum[lane];
+            uint32_t wi = w;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t t = __shfl_up_sync(0xffffffffu, wi, o);
+                if (lane >= o) wi += t;
+            }
+            wsum[lane] = wi - w;
+        }
+        __syncthreads();
+        const uint32_t ex = carry + wsum[warp] + incl - x;
+        __syncthreads();
+        if (i < ntiles) dv.tile_sums[i] = ex;
+        if (threadIdx.x == kScanThreads - 1) carry = ex + x;
+        __syncthreads();
+    }
+}
+
+__global__ void k_scan_add(Dev dv)
+{
+    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= dv.ctot || i < (uint32_t)kScanTile) return;
+    dv.start[i] += dv.tile_sums[i / kScanTile];
+}
+
+// tags in arrival order
+__global__ void k_scatter_tags(Dev dv, int cur)
+{
+    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= dv.ntot) return;
+    dv.tmp_tag[dv.start[dv.cellid[i]] + dv.slot[i]] = dv.buf[cur].tag[i];
+}
+
+// Canonical placement: a particle's sorted slot is its cell's start plus the
+// number of tags in the cell below its own (ascending-tag order), then the
+// gather into buffer cur ^ 1 with the FP32 mirror.
+__global__ void k_place(Dev dv, int cur)
+{
+    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= dv.ntot) return;
+    const Bufs& S = dv.buf[cur];
+    const Bufs& D = dv.buf[cur ^ 1];
+    const uint32_t c = dv.cellid[i];
+    const uint32_t b = dv.start[c];
+    const uint32_t n = dv.start[c + 1] - b;
+    const uint32_t t = S.tag[i];
+    uint32_t rank = 0;
+    for (uint32_t j = 0; j < n; ++j) rank += (dv.tmp_tag[b + j] < t) ? 1u : 0u;
+    const uint32_t o = b + rank;
+    const uint32_t r = dv.rep_of[i];
+    const Rep& rp = dv.reps[r];
+    const uint32_t lc = c - rp.cbase;
+    const int ix = (int)(lc % (uint32_t)rp.nc[0]);
+    const int iy = (int)((lc / (uint32_t)rp.nc[0]) % (uint32_t)rp.nc[1]);
+    const double x = S.px[i], y = S.py[i];
+    D.px[o] = x;
+    D.py[o] = y;
+    D.tag[o] = t;
+    const float rx = (float)rel_in_cell(x, dv.shift[3 * r], rp.L[0], rp.w[0], ix);
+    const float ry = (float)rel_in_cell(y, dv.shift[3 * r + 1], rp.L[1], rp.w[1], iy);
+    if (dv.dim == 2) {
+        const double c0 = S.q0[i], s0 = S.q1[i];
+        D.q0[o] = c0;
+        D.q1[o] = s0;
+        D.f4a[o] = make_float4(rx, ry, (float)c0, (float)s0);
+    } else {
+        const int iz = (int)(lc / ((uint32_t)rp.nc[0] * (uint32_t)rp.nc[1]));
+        const double z = S.pz[i];
+        D.pz[o] = z;
+        const float rz = (float)rel_in_cell(z, dv.shift[3 * r + 2], rp.L[2], rp.w[2], iz);
+        const double w0 = S.q0[i], w1 = S.q1[i], w2 = S.q2[i], w3 = S.q3[i];
+        D.q0[o] = w0; D.q1[o] = w1; D.q2[o] = w2; D.q3[o] = w3;
+        D.f4a[o] = make_float4(rx, ry, rz, (float)w0);
+        D.f4b[o] = make_float4((float)w1, (float)w2, (float)w3, 0.0f);
+    }
+}
+
+// ---------------------------------------------------------------- checks
+// Count overlapping pairs (each unordered pair once: the lower tag counts
+// it) of the sorted buffer `b` with the FP64 contract predicate.
+template <int NV>
+__global__ void k_check2d(Dev dv, Shape2 sh, int b, int32_t only_r, unsigned long long* out)
+{
+    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= dv.ntot) return;
+    const uint32_t r = dv.rep_of[i];
+    if (only_r >= 0 && (int32_t)r != only_r) return;
+    const Rep& rp = dv.reps[r];
+    const Bufs& B = dv.buf[b];
+    const int ix = cell_axis(B.px[i], dv.shift[3 * r], rp.L[0], rp.inv_w[0], rp.nc[0]);
+    const int iy = cell_axis(B.py[i], dv.shift[3 * r + 1], rp.L[1], rp.inv_w[1], rp.nc[1]);
+    const uint32_t ti = B.tag[i];
+    unsigned long long n = 0;
+    for (int oy = -1; oy <= 1; ++oy)
+        for (int ox = -1; ox <= 1; ++ox) {
+            const int jx = (ix + ox + rp.nc[0]) % rp.nc[0];
+            const int jy = (iy + oy + rp.nc[1]) % rp.nc[1];
+            const uint32_t cc = rp.cbase + (uint32_t)jx + (uint32_t)rp.nc[0] * (uint32_t)jy;
+            for (uint32_t e = dv.start[cc]; e < dv.start[cc + 1]; ++e) {
+                if (B.tag[e] <= ti) continue;
+                const double Dx = min_image(B.px[e] - B.px[i], rp.L[0], rp.halfL[0]);
+                const double Dy = min_image(B.py[e] - B.py[i], rp.L[1], rp.halfL[1]);
+                if (Dx * Dx + Dy * Dy > sh.rc2) continue;
+                if (overlap2d64<NV>(sh, Dx, Dy, B.q0[i], B.q1[i], B.q0[e], B.q1[e])) n += 1;
+            }
+        }
+    if (n) atomicAdd(out, n);
+}
+
+}  // namespace hpmc

@@ -1,0 +1,94 @@
+// hpmc_types.h -- device data layout of a batch of replicas (host + device).
+//
+// All particle arrays are global over the batch: replica r owns the index
+// range [pbase, pbase + n) and the cell range [cbase, cbase + ncell).  Inside
+// a replica the particles are kept in cell-sorted order (rebuilt every sweep);
+// `tag` maps a sorted slot back to the particle's tag (0..n-1 per replica).
+#pragma once
+#include <cstdint>
+
+namespace hpmc {
+
+constexpr int kMaxV2 = 16;      // polygon vertices
+constexpr int kMaxV3 = 32;      // polyhedron vertices
+constexpr int kNumCounters = 8; // see hpmc_counters_t
+constexpr int kGjkMaxIt = 32;
+
+enum : int { CNT_MOVES = 0, CNT_ACCEPT, CNT_REJ_OVERLAP, CNT_REJ_BOUNDARY, CNT_CULL,
+             CNT_CHECKS, CNT_RECHECK, CNT_GJKCAP };
+
+enum : int { ERR_NONE = 0, ERR_CAPACITY = 1, ERR_TIMEOUT = 2 };
+
+// Per-replica constants (device array, one entry per replica).
+struct Rep {
+    double L[3], halfL[3], w[3], inv_w[3];
+    float w32[3];
+    int nc[3];
+    uint32_t n, pbase, cbase, ncell;
+    uint64_t seed;
+    double d, tau;           // move sizes (FP64 contract)
+    float d32, tau32;        // FP32 copies for the filter
+    uint32_t nselect;
+    // FP32 filter thresholds (certified; see hpmc_bounds.h), rounded outward:
+    float in_lo;             // rel' >  in_lo  and < in_hi[a]  -> inside  (all axes)
+    float in_hi[3];
+    float out_lo;            // rel' < out_lo or > out_hi[a]   -> outside (any axis)
+    float out_hi[3];
+    float cull_keep;         // |D32|^2 < cull_keep -> FP64 keeps the pair
+    float cull_skip;         // |D32|^2 > cull_skip -> FP64 culls the pair
+    float sat_e;             // separating-axis / support gap margin
+    double e_in, e_cull, e_sat;  // the same margins in FP64 (reporting)
+};
+
+// Polygon constants (kernel parameter, passed by value).
+struct Shape2 {
+    int nv;
+    double vx[kMaxV2], vy[kMaxV2];
+    double nx[kMaxV2], ny[kMaxV2];
+    double alo[kMaxV2], ahi[kMaxV2];
+    float fvx[kMaxV2], fvy[kMaxV2], fnx[kMaxV2], fny[kMaxV2], falo[kMaxV2], fahi[kMaxV2];
+    double rc2;
+    float frc2;
+};
+
+// Polyhedron constants (kernel parameter, passed by value).
+struct Shape3 {
+    int nv;
+    double v[kMaxV3][3];
+    float fv[kMaxV3][3];
+    double rc2;
+    float frc2;
+};
+
+// One copy of the particle state (the rebuild alternates between two).
+struct Bufs {
+    double* px; double* py; double* pz;
+    double* q0; double* q1; double* q2; double* q3;   // 2D uses q0 = cos, q1 = sin
+    float4* f4a;             // FP32 (rel.x, rel.y, c, s) 2D or (rel.x, rel.y, rel.z, qw) 3D
+    float4* f4b;             // 3D: (qx, qy, qz, 0)
+    uint32_t* tag;
+};
+
+// Device pointers of one batch (kernel parameter, passed by value).
+struct Dev {
+    int dim;
+    uint32_t R;              // replicas
+    uint32_t ntot;           // particles over all replicas
+    uint32_t ctot;           // cells over all replicas
+    const Rep* reps;
+    const uint32_t* rep_of;  // replica of each global particle slot
+    Bufs buf[2];             // the rebuild reads buf[cur] and writes buf[cur ^ 1]
+    // cell list
+    uint32_t* count;         // [ctot]
+    uint32_t* start;         // [ctot + 1]
+    uint32_t* tile_sums;     // scan scratch
+    uint32_t* cellid;        // [ntot] scratch: global cell of each particle
+    uint32_t* slot;          // [ntot] scratch: arrival slot in the cell
+    uint32_t* tmp_tag;       // [ntot] scratch: tags in arrival order
+    double* shift;           // [R * 3] grid shift of the current sweep
+    uint64_t* sweep;         // [R] sweep counter per replica
+    unsigned long long* counters;   // [R * kNumCounters]
+    int* error;              // device error word (ERR_*)
+};
+
+}  // namespace hpmc

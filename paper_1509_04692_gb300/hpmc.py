@@ -1,0 +1,262 @@
+"""Thin ctypes binding of libhpmc.so (the C ABI of include/hpmc.h).
+
+Argument marshalling only: every step of a sweep runs in the library's CUDA
+kernels.  There is no CPU fallback: importing this module raises if the
+library cannot be loaded, and every call raises ``HPMCError`` on a non-zero
+return code.  Streams are passed as raw ``cudaStream_t`` handles (an int, e.g.
+``torch.cuda.current_stream().cuda_stream``; 0 = the legacy default stream).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+HPMC_FP64 = 0
+HPMC_FP32_FILTERED = 1
+
+ERRORS = {
+    -1: "HPMC_ERR_INVALID_ARG", -2: "HPMC_ERR_BOX_TOO_SMALL", -3: "HPMC_ERR_OVERLAP",
+    -4: "HPMC_ERR_OOM", -5: "HPMC_ERR_CUDA", -6: "HPMC_ERR_TIMEOUT", -7: "HPMC_ERR_CAPACITY",
+    -8: "HPMC_ERR_NOT_READY",
+}
+
+# every symbol include/hpmc.h declares (the CPU tests check the exports)
+EXPORTS = [
+    "hpmc_batch_create", "hpmc_create", "hpmc_destroy", "hpmc_set_moves", "hpmc_set_precision",
+    "hpmc_set_group_size", "hpmc_sweep", "hpmc_sweep_graph", "hpmc_sync", "hpmc_counters",
+    "hpmc_reset_counters", "hpmc_check_overlaps", "hpmc_get_state", "hpmc_set_state",
+    "hpmc_run_host", "hpmc_autotune", "hpmc_geometry", "hpmc_launches_per_sweep",
+    "hpmc_filter_margins", "hpmc_strerror",
+]
+
+
+class HPMCError(RuntimeError):
+    def __init__(self, code, where):
+        self.code = code
+        super().__init__(f"{where}: {ERRORS.get(code, code)} ({_lib.hpmc_strerror(code).decode()})")
+
+
+class Counters(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_uint64) for n in (
+        "moves", "accept", "reject_overlap", "reject_boundary", "cull_pairs", "overlap_checks",
+        "fp64_rechecks", "gjk_cap")]
+
+    def as_dict(self):
+        return {n: int(getattr(self, n)) for n, _ in self._fields_}
+
+
+class ReplicaDesc(ctypes.Structure):
+    _fields_ = [("N", ctypes.c_uint32), ("box", ctypes.c_double * 3),
+                ("pos", ctypes.POINTER(ctypes.c_double)), ("orient", ctypes.POINTER(ctypes.c_double)),
+                ("seed", ctypes.c_uint64), ("d", ctypes.c_double), ("a", ctypes.c_double),
+                ("nselect", ctypes.c_uint32)]
+
+
+def _load():
+    path = _build.LIB
+    if not os.path.exists(path):
+        path = _build.build()
+    lib = ctypes.CDLL(path)
+    dp = ctypes.POINTER(ctypes.c_double)
+    vp = ctypes.c_void_p
+    i32, u32, u64 = ctypes.c_int32, ctypes.c_uint32, ctypes.c_uint64
+    sig = {
+        "hpmc_batch_create": [ctypes.c_int, dp, u32, ctypes.c_double, u32, ctypes.POINTER(ReplicaDesc),
+                              ctypes.POINTER(vp)],
+        "hpmc_create": [dp, ctypes.c_int, u32, dp, u32, dp, dp, u64, ctypes.c_double, ctypes.POINTER(vp)],
+        "hpmc_destroy": [vp],
+        "hpmc_set_moves": [vp, i32, ctypes.c_double, ctypes.c_double, u32],
+        "hpmc_set_precision": [vp, ctypes.c_int],
+        "hpmc_set_group_size": [vp, ctypes.c_int, ctypes.c_int],
+        "hpmc_sweep": [vp, u32, vp],
+        "hpmc_sweep_graph": [vp, u32, vp],
+        "hpmc_sync": [vp],
+        "hpmc_counters": [vp, i32, ctypes.POINTER(Counters)],
+        "hpmc_reset_counters": [vp],
+        "hpmc_check_overlaps": [vp, i32, ctypes.POINTER(u64)],
+        "hpmc_get_state": [vp, i32, dp, dp, ctypes.POINTER(u64)],
+        "hpmc_set_state": [vp, i32, dp, dp, u64],
+        "hpmc_run_host": [vp, dp, dp, u32, dp, dp, ctypes.POINTER(Counters), vp],
+        "hpmc_autotune": [vp, u32, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)],
+        "hpmc_geometry": [vp, i32, ctypes.POINTER(i32), dp, dp],
+        "hpmc_launches_per_sweep": [vp, ctypes.POINTER(u32)],
+        "hpmc_filter_margins": [vp, i32, dp, dp, dp],
+    }
+    for name, args in sig.items():
+        f = getattr(lib, name)
+        f.argtypes = args
+        f.restype = ctypes.c_int
+    lib.hpmc_strerror.argtypes = [ctypes.c_int]
+    lib.hpmc_strerror.restype = ctypes.c_char_p
+    return lib
+
+
+_lib = _load()
+
+
+def lib():
+    return _lib
+
+
+def _ck(rc, where):
+    if rc != 0:
+        raise HPMCError(rc, where)
+
+
+def _dp(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def _c64(a, shape=None):
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    if shape is not None:
+        a = a.reshape(shape)
+    return a
+
+
+class Batch:
+    """A batch of R replicas of one convex shape (R = 1: a single system)."""
+
+    def __init__(self, dim, verts, replicas, w_min=0.0):
+        """replicas: list of dicts with keys N, box, pos, orient, seed, d, a, nselect."""
+        self.dim = int(dim)
+        self.qd = 2 if self.dim == 2 else 4
+        v = _c64(verts).reshape(-1, self.dim)
+        self._keep = []
+        descs = (ReplicaDesc * len(replicas))()
+        self.N = []
+        for i, r in enumerate(replicas):
+            pos = _c64(r["pos"]).reshape(-1, self.dim)
+            ori = _c64(r["orient"]).reshape(-1, self.qd)
+            self._keep += [pos, ori]
+            box = list(np.broadcast_to(np.asarray(r["box"], dtype=np.float64), (self.dim,))) + [1.0] * (3 - self.dim)
+            descs[i].N = pos.shape[0]
+            descs[i].box = (ctypes.c_double * 3)(*box)
+            descs[i].pos = _dp(pos)
+            descs[i].orient = _dp(ori)
+            descs[i].seed = int(r["seed"])
+            descs[i].d = float(r.get("d", 0.1))
+            descs[i].a = float(r.get("a", 0.1))
+            descs[i].nselect = int(r.get("nselect", 4))
+            self.N.append(pos.shape[0])
+        h = ctypes.c_void_p()
+        _ck(_lib.hpmc_batch_create(self.dim, _dp(v), v.shape[0], float(w_min), len(replicas), descs,
+                                   ctypes.byref(h)), "hpmc_batch_create")
+        self.h = h
+        self.R = len(replicas)
+        self._keep = []
+
+    @classmethod
+    def single(cls, dim, verts, box, pos, orient, seed, d=0.1, a=0.1, nselect=4, w_min=0.0):
+        return cls(dim, verts, [dict(box=box, pos=pos, orient=orient, seed=seed, d=d, a=a,
+                                     nselect=nselect)], w_min=w_min)
+
+    def close(self):
+        if getattr(self, "h", None):
+            _lib.hpmc_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    # ---- configuration
+    def set_moves(self, d, a, nselect, r=-1):
+        _ck(_lib.hpmc_set_moves(self.h, int(r), float(d), float(a), int(nselect)), "hpmc_set_moves")
+
+    def set_precision(self, mode):
+        _ck(_lib.hpmc_set_precision(self.h, int(mode)), "hpmc_set_precision")
+
+    def set_group_size(self, lanes, warps=4):
+        _ck(_lib.hpmc_set_group_size(self.h, int(lanes), int(warps)), "hpmc_set_group_size")
+
+    # ---- running
+    def sweep(self, n, stream=0, graph=False):
+        f = _lib.hpmc_sweep_graph if graph else _lib.hpmc_sweep
+        _ck(f(self.h, int(n), ctypes.c_void_p(int(stream) if stream else None)), "hpmc_sweep")
+
+    def sync(self):
+        _ck(_lib.hpmc_sync(self.h), "hpmc_sync")
+
+    def counters(self, r=-1):
+        c = Counters()
+        _ck(_lib.hpmc_counters(self.h, int(r), ctypes.byref(c)), "hpmc_counters")
+        return c.as_dict()
+
+    def reset_counters(self):
+        _ck(_lib.hpmc_reset_counters(self.h), "hpmc_reset_counters")
+
+    def check_overlaps(self, r=-1):
+        n = ctypes.c_uint64()
+        _ck(_lib.hpmc_check_overlaps(self.h, int(r), ctypes.byref(n)), "hpmc_check_overlaps")
+        return int(n.value)
+
+    def get_state(self, r=0):
+        N = self.N[r]
+        pos = np.zeros((N, self.dim))
+        ori = np.zeros((N, self.qd))
+        sw = ctypes.c_uint64()
+        _ck(_lib.hpmc_get_state(self.h, int(r), _dp(pos), _dp(ori), ctypes.byref(sw)), "hpmc_get_state")
+        return pos, ori, int(sw.value)
+
+    def set_state(self, pos, orient, sweep=0, r=0):
+        pos = _c64(pos)
+        ori = _c64(orient)
+        _ck(_lib.hpmc_set_state(self.h, int(r), _dp(pos), _dp(ori), int(sweep)), "hpmc_set_state")
+
+    def run_host(self, pos, orient, n, pos_out, orient_out, stream=0):
+        c = Counters()
+        _ck(_lib.hpmc_run_host(self.h, _dp(pos), _dp(orient), int(n), _dp(pos_out), _dp(orient_out),
+                               ctypes.byref(c), ctypes.c_void_p(int(stream) if stream else None)),
+            "hpmc_run_host")
+        return c.as_dict()
+
+    def autotune(self, n_trial=8):
+        g = ctypes.c_int()
+        w = ctypes.c_int()
+        _ck(_lib.hpmc_autotune(self.h, int(n_trial), ctypes.byref(g), ctypes.byref(w)), "hpmc_autotune")
+        return g.value, w.value
+
+    def geometry(self, r=0):
+        nc = (ctypes.c_int32 * 3)()
+        w = np.zeros(3)
+        R = ctypes.c_double()
+        _ck(_lib.hpmc_geometry(self.h, int(r), nc, _dp(w), ctypes.byref(R)), "hpmc_geometry")
+        return dict(nc=np.array(list(nc)[: self.dim]), w=w[: self.dim].copy(), R=R.value)
+
+    def launches_per_sweep(self):
+        n = ctypes.c_uint32()
+        _ck(_lib.hpmc_launches_per_sweep(self.h, ctypes.byref(n)), "hpmc_launches_per_sweep")
+        return int(n.value)
+
+    def filter_margins(self, r=0):
+        a, b, c = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+        _ck(_lib.hpmc_filter_margins(self.h, int(r), ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)),
+            "hpmc_filter_margins")
+        return dict(e_in=a.value, e_cull=b.value, e_overlap=c.value)
+
+
+def from_system(sysm, w_min=None):
+    """Batch of one replica from an inputs.System."""
+    return Batch.single(sysm.dim, sysm.verts, sysm.L, sysm.pos, sysm.orient, sysm.seed, d=sysm.d,
+                        a=sysm.a, nselect=sysm.nselect,
+                        w_min=sysm.w_min if w_min is None else w_min)
+
+
+def from_systems(systems):
+    s0 = systems[0]
+    reps = [dict(box=s.L, pos=s.pos, orient=s.orient, seed=s.seed, d=s.d, a=s.a, nselect=s.nselect)
+            for s in systems]
+    return Batch(s0.dim, s0.verts, reps, w_min=s0.w_min)
