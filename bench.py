@@ -1,0 +1,354 @@
+"""Benchmark: trial moves/s of the checkerboard hard-particle MC sweep on GB300.
+
+Workload (the configuration the headline metric is quoted on): 4096 regular
+pentagons (circumradius 0.5) at area fraction 0.60, d = a = 0.165 (30%
+acceptance), nselect = 4, Philox seed 42, melted 1000 sweeps from the lattice
+start before timing.  One step = SWEEPS_PER_STEP sweeps (shift + cell-list
+rebuild + 4 checkerboard sets each), replayed from a CUDA graph.
+
+Headline `value`: FP32-filtered form (decisions identical to FP64), inputs
+resident in HBM.  `forms` reports the plain FP64 form on the same workload and
+the batched form (512 replicas of N ~ U{256..8192}, phi ~ U[0.40, 0.70]).
+`e2e`: the same metric through hpmc_run_host with host buffers (H2D + sweeps
++ D2H inside the timed region).  `cpu_baseline`: the C oracle on host cores.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_1509_04692_gb300 import inputs  # noqa: E402
+
+METRIC = "trial moves/sec on 1 GB300 (FP32-filtered+batched vs plain FP64), % of roofline"
+UNIT = "trial moves/s"
+WORKLOAD = "pentagon fluid N=4096 phi=0.60 d=a=0.165 (~30% acceptance), nselect=4, seed 42"
+SWEEPS_PER_STEP = 200
+MELT = 1000
+# roofline of the set kernel: FP32 lanes x 2 flop (FMA) x max SM clock
+SMS, FP32_LANES, MAX_MHZ = 152, 128, 2070.0
+PEAK_TFLOPS = SMS * FP32_LANES * 2 * MAX_MHZ * 1e6 / 1e12
+# algorithmic flops: move arithmetic + circumsphere culls + full SAT checks
+FLOP_MOVE, FLOP_CULL, FLOP_SAT = 30, 5, 330
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class ClockSampler:
+    """nvidia-smi samples during the timed region."""
+
+    def __init__(self, gpu):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--id={gpu}", f"--query-gpu={q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except Exception:
+            self.p.kill()
+        self.f.flush()
+        self.f.seek(0)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.f.read().splitlines():
+            c = [x.strip() for x in line.split(",")]
+            if len(c) < 9:
+                continue
+            try:
+                sm.append(float(c[1]))
+                mx.append(float(c[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, c[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        os.unlink(self.f.name)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def oracle_rate(s, melt, sweeps):
+    """Oracle (plain C, 1 thread) on the workload: melt, then time `sweeps`."""
+    from oracle import oracle as orc
+    ref = orc.OracleSystem(2, s.L, s.verts, w_min=s.w_min)
+    ref.set_moves(s.d, s.a, s.nselect, s.seed)
+    pos, ori = s.pos.copy(), s.orient.copy()
+    ref.sweep(pos, ori, 0, melt)
+    t0 = time.perf_counter()
+    c = ref.sweep(pos, ori, melt, sweeps)
+    dt = time.perf_counter() - t0
+    moves = int(c[0] + c[1] + c[2])
+    return moves / dt, moves, dt, (pos, ori)
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    s = inputs.fluid4096(42)
+    per_step = 40                     # sweeps of the oracle per step (bounded sample)
+    from oracle import oracle as orc
+    ref = orc.OracleSystem(2, s.L, s.verts)
+    ref.set_moves(s.d, s.a, s.nselect, s.seed)
+    pos, ori = s.pos.copy(), s.orient.copy()
+    ref.sweep(pos, ori, 0, MELT)
+    sweep = MELT
+    for _ in range(args.warmup):
+        ref.sweep(pos, ori, sweep, per_step)
+        sweep += per_step
+    moves = 0
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        c = ref.sweep(pos, ori, sweep, per_step)
+        sweep += per_step
+        moves += int(c[0] + c[1] + c[2])
+    dt = time.perf_counter() - t0
+    v = moves / dt
+    out = {"metric": METRIC, "value": v, "unit": UNIT, "impl": "reference", "n_gpus": ws,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic",
+           "config": {"workload": WORKLOAD, "sweeps_per_step": per_step, "melt_sweeps": MELT},
+           "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+                            "sample": f"{args.steps} x {per_step} sweeps of the 4096-pentagon fluid "
+                                      f"after a {MELT}-sweep melt (plain C oracle, 1 thread)"},
+           "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+           "gpu_launches": 0}
+    print(json.dumps(out))
+
+
+def time_steps(b, torch, stream, steps, warmup, flush):
+    for _ in range(warmup):
+        b.sweep(SWEEPS_PER_STEP, stream=stream.cuda_stream, graph=True)
+    torch.cuda.synchronize()
+    c0 = b.counters()
+    total_ms = 0.0
+    for _ in range(steps):
+        flush.zero_()                                  # evict the state from L2 between steps
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        b.sweep(SWEEPS_PER_STEP, stream=stream.cuda_stream, graph=True)
+        e1.record(stream)
+        e1.synchronize()
+        total_ms += e0.elapsed_time(e1)
+    c1 = b.counters()
+    d = {k: c1[k] - c0[k] for k in c1}
+    return total_ms, d
+
+
+def run_ours(args):
+    import torch
+    from paper_1509_04692_gb300 import hpmc
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        torch.cuda.set_device(0)
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+
+    s = inputs.fluid4096(42 + rank)
+    b = hpmc.from_system(s)
+    b.set_precision(hpmc.HPMC_FP32_FILTERED)
+    b.sweep(MELT, stream=stream.cuda_stream, graph=True)       # melt (untimed)
+    lanes, warps = b.autotune(8)                               # state restored afterwards
+    torch.cuda.synchronize()
+
+    if ws > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    sampler = ClockSampler(local) if rank == 0 else None
+    ms, cnt = time_steps(b, torch, stream, args.steps, args.warmup, flush)
+    clocks = sampler.stop() if sampler else None
+    moves = cnt["moves"]
+    if ws > 1:
+        t = torch.tensor([ms, float(moves)], dtype=torch.float64, device="cuda")
+        tmax = t.clone()
+        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
+        dist.all_reduce(t, op=dist.ReduceOp.SUM)
+        ms_job, moves_job = float(tmax[0]), float(t[1])
+    else:
+        ms_job, moves_job = ms, float(moves)
+    value = moves_job / (ms_job * 1e-3)
+    if rank != 0:
+        b.close()
+        if ws > 1:
+            dist.destroy_process_group()
+        return
+
+    # ---- roofline of the dominant kernel (the set kernel), CUDA events live
+    nsets = 4
+    b.reset_counters()
+    ms_rebuild, ms_sets = b.profile_sweeps(SWEEPS_PER_STEP, stream=stream.cuda_stream)
+    cp = b.counters()
+    set_ms = ms_sets / nsets
+    flop_per_sweep = (FLOP_MOVE * cp["moves"] + FLOP_CULL * cp["cull_pairs"] +
+                      FLOP_SAT * cp["overlap_checks"]) / SWEEPS_PER_STEP
+    achieved = (flop_per_sweep / nsets) / (set_ms * 1e-3) / 1e12
+    roofline = {"bound": "alu", "kernel": "k_set2d (checkerboard set)", "achieved": achieved,
+                "peak": PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / PEAK_TFLOPS,
+                "traffic": None,
+                "set_kernel_ms": set_ms, "rebuild_ms_per_sweep": ms_rebuild,
+                "peak_source": "152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz (nominal unit counts)",
+                "flops_per_move_model": f"{FLOP_MOVE} + {FLOP_CULL}*culls + {FLOP_SAT}*SAT checks"}
+
+    # ---- end to end through the C ABI with host buffers
+    N = s.N
+    p_in, o_in, _ = b.get_state()
+    pin_p = torch.from_numpy(np.ascontiguousarray(p_in)).pin_memory()
+    pin_o = torch.from_numpy(np.ascontiguousarray(o_in)).pin_memory()
+    out_p = torch.empty_like(pin_p).pin_memory()
+    out_o = torch.empty_like(pin_o).pin_memory()
+    torch.cuda.synchronize()
+    b.run_host(pin_p.numpy(), pin_o.numpy(), SWEEPS_PER_STEP, out_p.numpy(), out_o.numpy(),
+               stream=stream.cuda_stream)                    # warm-up
+    e2e_moves, e2e_dt = 0, 0.0
+    for _ in range(max(3, args.steps // 2)):
+        b.reset_counters()
+        t0 = time.perf_counter()
+        c = b.run_host(pin_p.numpy(), pin_o.numpy(), SWEEPS_PER_STEP, out_p.numpy(), out_o.numpy(),
+                       stream=stream.cuda_stream)
+        e2e_dt += time.perf_counter() - t0
+        e2e_moves += c["moves"]
+        pin_p.copy_(out_p)
+        pin_o.copy_(out_o)
+    e2e = {"value": e2e_moves / e2e_dt, "unit": UNIT,
+           "h2d_bytes_per_step": int(N * 4 * 8), "d2h_bytes_per_step": int(N * 4 * 8),
+           "api": "hpmc_run_host (pinned host buffers, H2D + 200 sweeps + D2H + counters)"}
+
+    forms = {"fp32_filtered": {"value": value, "fp64_rechecks": cnt["fp64_rechecks"],
+                               "overlap_checks": cnt["overlap_checks"],
+                               "acceptance": cnt["accept"] / max(1, moves)}}
+    # ---- plain FP64 form on the same workload (same trajectory)
+    b64 = hpmc.from_system(s)
+    b64.set_precision(hpmc.HPMC_FP64)
+    b64.sweep(MELT, stream=stream.cuda_stream, graph=True)
+    l64, w64 = b64.autotune(4)
+    ms64, c64 = time_steps(b64, torch, stream, max(2, args.steps // 2), 1, flush)
+    forms["fp64"] = {"value": c64["moves"] / (ms64 * 1e-3), "lanes_per_cell": l64,
+                     "warps_per_block": w64}
+    p32, o32, sw32 = b.get_state()
+    b64.close()
+
+    # ---- batched form: 512 independent replicas, one graph-captured launch sequence
+    if not args.no_batched:
+        reps = inputs.replica_systems(512)
+        bb = hpmc.from_systems(reps)
+        bb.set_precision(hpmc.HPMC_FP32_FILTERED)
+        bb.sweep(20, stream=stream.cuda_stream, graph=True)
+        lb, wb = bb.autotune(4)
+        msb, cb = time_steps(bb, torch, stream, 2, 1, flush)
+        forms["batched_512_replicas_fp32_filtered"] = {
+            "value": cb["moves"] / (msb * 1e-3), "replicas": 512,
+            "particles": int(sum(r.N for r in reps)), "lanes_per_cell": lb, "warps_per_block": wb,
+            "ms_per_step": msb / 2, "sweeps_per_step": SWEEPS_PER_STEP}
+        bb.close()
+
+    # ---- CPU baseline: the oracle on host cores, bounded sample
+    cpu = None
+    if not args.no_cpu:
+        rate, cmoves, cdt, _ = oracle_rate(s, MELT, args.cpu_sweeps)
+        cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"{args.cpu_sweeps} sweeps ({cmoves} trial moves, {cdt:.1f} s) of the same "
+                         f"4096-pentagon fluid after a {MELT}-sweep melt, plain C oracle, 1 thread"}
+
+    launches = args.steps * SWEEPS_PER_STEP * b.launches_per_sweep()
+    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": ms_job / args.steps, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64 (FP32 certified filter, FP64 state)",
+           "data": "synthetic",
+           "config": {"workload": WORKLOAD, "N": N, "phi": 0.60, "d": s.d, "a": s.a,
+                      "nselect": s.nselect, "sweeps_per_step": SWEEPS_PER_STEP, "melt_sweeps": MELT,
+                      "precision": "FP32_FILTERED", "lanes_per_cell": lanes, "warps_per_block": warps,
+                      "l2": "flushed between timed steps (256 MiB write); the 4096-particle state "
+                            "is L2-resident within a step",
+                      "parallelism": f"replicas only: {ws} independent replica(s), one per GPU"},
+           "roofline": roofline, "cpu_baseline": cpu, "clocks": clocks, "e2e": e2e,
+           "gpu_launches": launches, "forms": forms,
+           "counters": cnt}
+    print(json.dumps(out))
+    b.close()
+    if ws > 1:
+        dist.destroy_process_group()
+
+
+def run_profile(args):
+    """Small case for ncu captures: the benchmark fluid, a short melt, then
+    `--profile-sweeps` sweeps of the chosen precision form (direct launches)."""
+    import torch
+    from paper_1509_04692_gb300 import hpmc
+    torch.cuda.set_device(0)
+    if args.profile_workload == "batched":
+        b = hpmc.from_systems(inputs.replica_systems(512))
+    else:
+        b = hpmc.from_system(inputs.fluid4096(42))
+    b.set_precision(hpmc.HPMC_FP64 if args.profile_fp64 else hpmc.HPMC_FP32_FILTERED)
+    if args.lanes:
+        b.set_group_size(args.lanes, args.warps)
+    b.sweep(20)
+    b.sweep(args.profile_sweeps)
+    c = b.counters()
+    b.close()
+    print(json.dumps({"profile": args.profile_workload, "sweeps": args.profile_sweeps, "counters": c}))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--profile-sweeps", type=int, default=0,
+                    help="run the small ncu case instead of the benchmark")
+    ap.add_argument("--profile-workload", default="fluid4096", choices=["fluid4096", "batched"])
+    ap.add_argument("--profile-fp64", action="store_true")
+    ap.add_argument("--lanes", type=int, default=0)
+    ap.add_argument("--warps", type=int, default=4)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--cpu-sweeps", type=int, default=2000)
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-batched", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.profile_sweeps:
+        run_profile(args)
+    elif args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -125,8 +125,9 @@ int hpmc_set_group_size(hpmc_t h, int lanes_per_cell, int warps_per_block);
  * hpmc_sweep -- enqueue n sweeps on `stream`: per sweep the grid shift,
  * the cell-list rebuild and the 2^d checkerboard sets (Sec. 2.5.2), for
  * every replica.  Asynchronous; the sweep counter advances on the device.
- * With use_graph != 0 the per-sweep launch sequence is captured once into a
- * CUDA graph and replayed.
+ * hpmc_sweep launches the kernels directly; hpmc_sweep_graph captures the
+ * launch sequence of two sweeps once into a CUDA graph (per buffer parity)
+ * and replays it.  Both give the same trajectory.
  */
 int hpmc_sweep(hpmc_t h, uint32_t n, void* stream);
 int hpmc_sweep_graph(hpmc_t h, uint32_t n, void* stream);
@@ -174,6 +175,14 @@ int hpmc_run_host(hpmc_t h, const double* pos, const double* orient, uint32_t n,
  * depend on the choice.  *best_lanes / *best_warps receive it.  Synchronous.
  */
 int hpmc_autotune(hpmc_t h, uint32_t n_trial, int* best_lanes, int* best_warps);
+
+/*
+ * hpmc_profile_sweeps -- run n sweeps on `stream` with CUDA events recorded
+ * around the rebuild (shift + cell list) and around the 2^d set kernels of
+ * every sweep; synchronise and return the mean milliseconds per sweep of
+ * each phase.  The set kernels' mean duration is *ms_sets / 2^d.
+ */
+int hpmc_profile_sweeps(hpmc_t h, uint32_t n, void* stream, double* ms_rebuild, double* ms_sets);
 
 /* Geometry of replica r: cells per axis, cell width, circumradius. */
 int hpmc_geometry(hpmc_t h, int32_t r, int32_t* nc, double* w, double* R);

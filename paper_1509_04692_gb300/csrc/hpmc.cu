@@ -941,6 +941,53 @@ int hpmc_autotune(hpmc_t h, uint32_t n_trial, int* best_lanes, int* best_warps)
     return read_error(h);
 }
 
+int hpmc_profile_sweeps(hpmc_t h, uint32_t n, void* stream, double* ms_rebuild, double* ms_sets)
+{
+    if (!h || n == 0) return HPMC_ERR_INVALID_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    h->last_stream = st;
+    int rc = prepare_set(h);
+    if (rc) return rc;
+    std::vector<cudaEvent_t> ev(3 * (size_t)n);
+    for (auto& e : ev) CK(cudaEventCreate(&e));
+    for (uint32_t s = 0; s < n; ++s) {
+        CK(cudaEventRecord(ev[3 * s], st));
+        rc = enqueue_rebuild(h, st, true);
+        if (rc) break;
+        CK(cudaEventRecord(ev[3 * s + 1], st));
+        // the set kernels of enqueue_sweep, without its rebuild
+        const int nxt = h->cur ^ 1;
+        const int gi = gidx_of(h->G);
+        const uint32_t* ib = h->item_base_dev + (size_t)gi * (h->R + 1);
+        for (int sigma = 0; sigma < (1 << h->dim); ++sigma) {
+            void* args[5];
+            int nx = nxt, sg = sigma;
+            args[0] = &h->dv;
+            args[1] = h->dim == 2 ? (void*)&h->sh2 : (void*)&h->sh3;
+            args[2] = &nx;
+            args[3] = &sg;
+            args[4] = (void*)&ib;
+            CK(cudaLaunchKernel(h->cfg_fn, dim3(h->cfg_grid), dim3(32 * h->wpb), args, h->cfg_smem, st));
+        }
+        h->cur = nxt;
+        CK(cudaEventRecord(ev[3 * s + 2], st));
+    }
+    CK(cudaStreamSynchronize(st));
+    double a = 0.0, b = 0.0;
+    for (uint32_t s = 0; s < n && !rc; ++s) {
+        float x = 0.f, y = 0.f;
+        CK(cudaEventElapsedTime(&x, ev[3 * s], ev[3 * s + 1]));
+        CK(cudaEventElapsedTime(&y, ev[3 * s + 1], ev[3 * s + 2]));
+        a += x;
+        b += y;
+    }
+    for (auto& e : ev) cudaEventDestroy(e);
+    if (rc) return rc;
+    if (ms_rebuild) *ms_rebuild = a / n;
+    if (ms_sets) *ms_sets = b / n;
+    return read_error(h);
+}
+
 int hpmc_geometry(hpmc_t h, int32_t r, int32_t* nc, double* w, double* R)
 {
     if (!h || r < 0 || r >= (int32_t)h->R) return HPMC_ERR_INVALID_ARG;

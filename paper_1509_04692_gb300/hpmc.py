@@ -30,7 +30,7 @@ EXPORTS = [
     "hpmc_set_group_size", "hpmc_sweep", "hpmc_sweep_graph", "hpmc_sync", "hpmc_counters",
     "hpmc_reset_counters", "hpmc_check_overlaps", "hpmc_get_state", "hpmc_set_state",
     "hpmc_run_host", "hpmc_autotune", "hpmc_geometry", "hpmc_launches_per_sweep",
-    "hpmc_filter_margins", "hpmc_strerror",
+    "hpmc_filter_margins", "hpmc_strerror", "hpmc_profile_sweeps",
 ]
 
 
@@ -85,6 +85,7 @@ def _load():
         "hpmc_geometry": [vp, i32, ctypes.POINTER(i32), dp, dp],
         "hpmc_launches_per_sweep": [vp, ctypes.POINTER(u32)],
         "hpmc_filter_margins": [vp, i32, dp, dp, dp],
+        "hpmc_profile_sweeps": [vp, u32, vp, dp, dp],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -228,6 +229,13 @@ class Batch:
         w = ctypes.c_int()
         _ck(_lib.hpmc_autotune(self.h, int(n_trial), ctypes.byref(g), ctypes.byref(w)), "hpmc_autotune")
         return g.value, w.value
+
+    def profile_sweeps(self, n, stream=0):
+        """Mean ms per sweep of (rebuild, sets), CUDA events on `stream`."""
+        a, b = ctypes.c_double(), ctypes.c_double()
+        _ck(_lib.hpmc_profile_sweeps(self.h, int(n), ctypes.c_void_p(int(stream) if stream else None),
+                                     ctypes.byref(a), ctypes.byref(b)), "hpmc_profile_sweeps")
+        return a.value, b.value
 
     def geometry(self, r=0):
         nc = (ctypes.c_int32 * 3)()

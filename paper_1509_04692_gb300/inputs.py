@@ -183,6 +183,21 @@ def cube_system(N: int, phi: float, seed: int, name: str = "cubes", d: float = 0
                          "spacing": a_sp})
 
 
+# The 4096-pentagon fluid at area fraction 0.60: d = a = 0.165 gives a 30%
+# acceptance ratio.  Found with tune.tune_scale (d/a fixed at 1, bisection on
+# 100-sweep pilots) after a 3000-sweep melt from the lattice start at
+# d = a = 0.2; the chain is implementation independent, so any sweep
+# implementation reproduces it.
+FLUID4096_D = 0.165
+FLUID4096_A = 0.165
+
+
+def fluid4096(seed: int = 42) -> System:
+    """4096 regular pentagons, area fraction 0.60, moves sized for ~30% acceptance."""
+    return pentagon_system(4096, 0.60, seed, name="pentagon fluid N=4096 phi=0.60",
+                           d=FLUID4096_D, a=FLUID4096_A, nselect=4)
+
+
 def replica_params(n_replicas: int = 512, gen_seed: int = 2024, n_lo: int = 256,
                    n_hi: int = 8192, phi_lo: float = 0.40, phi_hi: float = 0.70):
     """(N_r, phi_r, seed_r = 42 + r) for a batch of independent replicas."""
