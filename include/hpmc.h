@@ -195,6 +195,45 @@ int hpmc_filter_margins(hpmc_t h, int32_t r, double* e_in, double* e_cull, doubl
 
 const char* hpmc_strerror(int code);
 
+/*
+ * hpmc_count_overlaps_noalloc -- count the overlapping pairs of one 2D
+ * configuration without allocating any memory.  The paper has no
+ * counterpart; this entry point exists for callers that cannot allocate
+ * device memory where they need the check (code running inside a custom
+ * memory pool or a callback that must not touch the allocator, tools that
+ * forbid allocation while recording work, embedders that own all device
+ * memory up front).
+ *   box        host, 2 doubles: L_x, L_y (periodic, positions in [0, L)).
+ *   verts      host, nv*2 doubles: convex counter-clockwise polygon, 3..16
+ *              vertices, local frame.
+ *   N          particles, 1..HPMC_NOALLOC_MAX_N.
+ *   pos_dev    device, N*2 doubles (x, y) per particle, caller-owned.
+ *   orient_dev device, N*2 doubles (cos, sin) per particle, caller-owned.
+ *   count_dev  device, one unsigned 64-bit counter, caller-owned; receives
+ *              the number of overlapping unordered pairs.
+ *   stream     cudaStream_t as void* (NULL = legacy default stream); the
+ *              call only enqueues work on it.
+ * The pair rule is the FP64 one of hpmc_check_overlaps (minimum image,
+ * circumsphere cull, separating axes) on the same cell grid (width rule of
+ * hpmc_batch_create, no shift).  The cell list lives in one fixed
+ * file-scope device array of the library (about 1.3 MB) that every device
+ * loading the library keeps until the process exits; the call performs no
+ * cudaMalloc, cudaFree or other allocation.  The first call on a device looks
+ * up that array's device address; make it before any stream capture.  All
+ * calls share the array and it keeps the last call's contents (the call
+ * clears what must start at zero), so calls whose work overlaps on the GPU
+ * (other streams, other threads) race and must be serialised by the caller.
+ * Errors: INVALID_ARG (null pointers, bad vertices, non-finite box),
+ * BOX_TOO_SMALL, SCRATCH_LIMIT (N > HPMC_NOALLOC_MAX_N or more than
+ * HPMC_NOALLOC_MAX_CELLS cells), CUDA.
+ */
+#define HPMC_ERR_SCRATCH_LIMIT  -9   /* size beyond the fixed no-allocation scratch */
+#define HPMC_NOALLOC_MAX_N      65536
+#define HPMC_NOALLOC_MAX_CELLS  65536
+int hpmc_count_overlaps_noalloc(const double* box, const double* verts, uint32_t nv, uint32_t N,
+                                const double* pos_dev, const double* orient_dev,
+                                unsigned long long* count_dev, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

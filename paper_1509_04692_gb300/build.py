@@ -17,7 +17,8 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libhpmc.so")
-UNITS = ["hpmc.cu", "set2d_f32.cu", "set2d_f64.cu", "set3d.cu", "set3d_f32.cu", "set3d_f64.cu"]
+UNITS = ["hpmc.cu", "set2d_f32.cu", "set2d_f64.cu", "set3d.cu", "set3d_f32.cu", "set3d_f64.cu",
+         "noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-fmad=false", "-Xcompiler", "-fPIC,-ffp-contract=off",
          "-I", INCLUDE]

@@ -475,6 +475,7 @@ const char* hpmc_strerror(int code)
     case HPMC_ERR_TIMEOUT: return "bounded device wait gave up";
     case HPMC_ERR_CAPACITY: return "a cell stencil exceeded the staging capacity";
     case HPMC_ERR_NOT_READY: return "call order violated";
+    case HPMC_ERR_SCRATCH_LIMIT: return "size exceeds the fixed scratch of the no-allocation entry point";
     default: return "unknown error";
     }
 }

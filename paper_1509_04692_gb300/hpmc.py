@@ -21,7 +21,7 @@ HPMC_FP32_FILTERED = 1
 ERRORS = {
     -1: "HPMC_ERR_INVALID_ARG", -2: "HPMC_ERR_BOX_TOO_SMALL", -3: "HPMC_ERR_OVERLAP",
     -4: "HPMC_ERR_OOM", -5: "HPMC_ERR_CUDA", -6: "HPMC_ERR_TIMEOUT", -7: "HPMC_ERR_CAPACITY",
-    -8: "HPMC_ERR_NOT_READY",
+    -8: "HPMC_ERR_NOT_READY", -9: "HPMC_ERR_SCRATCH_LIMIT",
 }
 
 # every symbol include/hpmc.h declares (the CPU tests check the exports)
@@ -30,7 +30,7 @@ EXPORTS = [
     "hpmc_set_group_size", "hpmc_sweep", "hpmc_sweep_graph", "hpmc_sync", "hpmc_counters",
     "hpmc_reset_counters", "hpmc_check_overlaps", "hpmc_get_state", "hpmc_set_state",
     "hpmc_run_host", "hpmc_autotune", "hpmc_geometry", "hpmc_launches_per_sweep",
-    "hpmc_filter_margins", "hpmc_strerror", "hpmc_profile_sweeps",
+    "hpmc_filter_margins", "hpmc_strerror", "hpmc_profile_sweeps", "hpmc_count_overlaps_noalloc",
 ]
 
 
