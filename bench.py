@@ -308,6 +308,8 @@ def run_profile(args):
     """Small case for ncu captures: the benchmark fluid, a short melt, then
     `--profile-sweeps` sweeps of the chosen precision form (direct launches)."""
     import torch
+    if args.trace:
+        os.environ["HPMC_TRACE"] = "1"          # load the -DHPMC_TRACE build
     from paper_1509_04692_gb300 import hpmc
     torch.cuda.set_device(0)
     if args.profile_workload == "batched":
@@ -320,8 +322,43 @@ def run_profile(args):
     b.sweep(20)
     b.sweep(args.profile_sweeps)
     c = b.counters()
+    out = {"profile": args.profile_workload, "sweeps": args.profile_sweeps, "counters": c}
+    if args.trace:
+        # clock64() stamps of the first item of every warp of the last set
+        # kernel: per-phase cycles (median / p90 over warps)
+        tr = b.trace_read().astype(np.int64)
+        used = tr[:, 0] != 0
+        tr = tr[used]
+        names = {1: "prologue", 2: "capacity check", 3: "staging", 4: "stencil tables",
+                 5: "precompute"}
+        phases = {}
+        prev = tr[:, 0]
+        for p in range(1, 28):
+            col = tr[:, p]
+            ok = col != 0
+            if not ok.any():
+                continue
+            d = (col - prev)[ok]
+            name = names.get(p, f"move{(p - 6) // 3}:" + ["propose", "cull+overlap", "accept"][(p - 6) % 3]
+                             if 6 <= p < 30 else "tail")
+            phases[name] = {"median": float(np.median(d)), "p90": float(np.percentile(d, 90))}
+            prev = np.where(ok, col, prev)
+        out["trace_cycles"] = phases
+        out["warps_traced"] = int(used.sum())
+        # global-timer entry (28) / exit (29) stamps: start spread and span, ns
+        ent, ex = tr[:, 28], tr[:, 29]
+        okx = (ent != 0) & (ex != 0)
+        if okx.any():
+            e0 = ent[okx].min()
+            out["warp_entry_ns"] = {"p50": float(np.median(ent[okx] - e0)),
+                                    "p90": float(np.percentile(ent[okx] - e0, 90)),
+                                    "max": float((ent[okx] - e0).max())}
+            out["warp_run_ns"] = {"p50": float(np.median(ex[okx] - ent[okx])),
+                                  "max": float((ex[okx] - ent[okx]).max())}
+            out["kernel_span_ns"] = float(ex[okx].max() - e0)
+        out["total_cycles_median"] = float(np.median(tr[:, 30] - tr[:, 0])) if (tr[:, 30] != 0).any() else None
     b.close()
-    print(json.dumps({"profile": args.profile_workload, "sweeps": args.profile_sweeps, "counters": c}))
+    print(json.dumps(out))
 
 
 def main():
@@ -332,6 +369,7 @@ def main():
     ap.add_argument("--profile-fp64", action="store_true")
     ap.add_argument("--lanes", type=int, default=0)
     ap.add_argument("--warps", type=int, default=4)
+    ap.add_argument("--trace", action="store_true", help="with --profile-sweeps: per-warp phase stamps")
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)

@@ -184,6 +184,15 @@ int hpmc_autotune(hpmc_t h, uint32_t n_trial, int* best_lanes, int* best_warps);
  */
 int hpmc_profile_sweeps(hpmc_t h, uint32_t n, void* stream, double* ms_rebuild, double* ms_sets);
 
+/*
+ * hpmc_trace_read -- libraries built with -DHPMC_TRACE record, for the first
+ * work item of every warp of the last set kernel, clock64() stamps at its
+ * phase boundaries (*n_points per warp; see HPMC_STAMP in the kernel source).
+ * Copies up to max_warps warps' stamps into out[max_warps * *n_points].
+ * Returns HPMC_ERR_NOT_READY in ordinary builds.  Synchronous.
+ */
+int hpmc_trace_read(hpmc_t h, uint64_t* out, uint32_t max_warps, uint32_t* n_points);
+
 /* Geometry of replica r: cells per axis, cell width, circumradius. */
 int hpmc_geometry(hpmc_t h, int32_t r, int32_t* nc, double* w, double* R);
 

@@ -17,6 +17,9 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libhpmc.so")
+# trace variant (-DHPMC_TRACE): per-warp clock64() phase stamps in the set kernels
+BUILD_TRACE = os.path.join(HERE, "_build_trace")
+LIB_TRACE = os.path.join(BUILD_TRACE, "libhpmc.so")
 UNITS = ["hpmc.cu", "set2d_f32.cu", "set2d_f64.cu", "set3d.cu", "set3d_f32.cu", "set3d_f64.cu",
          "noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
@@ -43,13 +46,17 @@ def _newest_input() -> float:
     return max(t, os.path.getmtime(__file__))
 
 
-def build(force: bool = False, verbose: bool = False, extra: list[str] | None = None) -> str:
-    os.makedirs(BUILD, exist_ok=True)
-    if not force and os.path.exists(LIB) and os.path.getmtime(LIB) >= _newest_input():
-        return LIB
+def build(force: bool = False, verbose: bool = False, extra: list[str] | None = None,
+          trace: bool = False) -> str:
+    bdir, lib = (BUILD_TRACE, LIB_TRACE) if trace else (BUILD, LIB)
+    if trace:
+        extra = list(extra or []) + ["-DHPMC_TRACE"]
+    os.makedirs(bdir, exist_ok=True)
+    if not force and os.path.exists(lib) and os.path.getmtime(lib) >= _newest_input():
+        return lib
     cc = nvcc()
     srcs = _sources()
-    objs = [os.path.join(BUILD, os.path.basename(s).replace(".cu", ".o")) for s in srcs]
+    objs = [os.path.join(bdir, os.path.basename(s).replace(".cu", ".o")) for s in srcs]
 
     def one(pair):
         s, o = pair
@@ -64,13 +71,14 @@ def build(force: bool = False, verbose: bool = False, extra: list[str] | None = 
     if verbose:
         for lg in logs:
             print(lg)
-    tmp = LIB + f".tmp{os.getpid()}"
+    tmp = lib + f".tmp{os.getpid()}"
     subprocess.check_call([cc, *ARCH, "-shared", "-o", tmp, *objs])
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":
     import sys
     print(build(force="--force" in sys.argv, verbose="-v" in sys.argv,
-                extra=["-Xptxas", "-v"] if "--ptxas" in sys.argv else None))
+                extra=["-Xptxas", "-v"] if "--ptxas" in sys.argv else None,
+                trace="--trace" in sys.argv))

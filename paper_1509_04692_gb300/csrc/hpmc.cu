@@ -218,6 +218,8 @@ int rep_geometry(const hpmc_batch* h, const HostRep& hr, Rep& rp)
     rp.seed = hr.seed;
     rp.d = hr.d;
     rp.tau = std::tan(0.5 * hr.a);
+    rp.d_s = rp.d * 0x1.0p-53;        // exact: power-of-two scaling
+    rp.tau_s = rp.tau * 0x1.0p-53;
     rp.d32 = (float)rp.d;
     rp.tau32 = (float)rp.tau;
     rp.nselect = hr.nselect;
@@ -254,8 +256,9 @@ int rep_geometry(const hpmc_batch* h, const HostRep& hr, Rep& rp)
 
 int check_moves(double d, double a, uint32_t nselect)
 {
-    if (!is_finite(d) || d < 0.0) return HPMC_ERR_INVALID_ARG;
-    if (!is_finite(a) || a < 0.0 || a >= 3.14159) return HPMC_ERR_INVALID_ARG;
+    // (nonzero sizes below 1e-250 would make d * 2^-53 subnormal)
+    if (!is_finite(d) || d < 0.0 || (d > 0.0 && d < 1e-250)) return HPMC_ERR_INVALID_ARG;
+    if (!is_finite(a) || a < 0.0 || a >= 3.14159 || (a > 0.0 && a < 1e-250)) return HPMC_ERR_INVALID_ARG;
     if (nselect == 0 || nselect > 65535) return HPMC_ERR_INVALID_ARG;
     return 0;
 }
@@ -554,6 +557,15 @@ int hpmc_batch_create(int dim, const double* verts, uint32_t nv, double w_min, u
         (rc = dalloc(h, &dv.counters, (size_t)R * kNumCounters)) || (rc = dalloc(h, &dv.error, 1)) ||
         (rc = dalloc(h, &h->item_base_dev, 6 * ((size_t)R + 1))) || (rc = dalloc(h, &h->check_out, 1)))
         return fail(rc);
+#ifdef HPMC_TRACE
+    dv.trace_warps = 65536;
+    if ((rc = dalloc(h, &dv.trace, (size_t)dv.trace_warps * kTracePoints))) return fail(rc);
+    if (cudaMemset(dv.trace, 0, sizeof(unsigned long long) * dv.trace_warps * kTracePoints) != cudaSuccess)
+        return fail(HPMC_ERR_CUDA);
+#else
+    dv.trace = nullptr;
+    dv.trace_warps = 0;
+#endif
 
     std::vector<uint32_t> tab;
     build_item_tables(h, tab);
@@ -1004,6 +1016,17 @@ int hpmc_launches_per_sweep(hpmc_t h, uint32_t* n)
 {
     if (!h || !n) return HPMC_ERR_INVALID_ARG;
     *n = 5 + (h->ntiles > 1 ? 2 : 0) + (1u << h->dim);
+    return 0;
+}
+
+int hpmc_trace_read(hpmc_t h, uint64_t* out, uint32_t max_warps, uint32_t* n_points)
+{
+    if (!h || !out || !n_points) return HPMC_ERR_INVALID_ARG;
+    *n_points = kTracePoints;
+    if (!h->dv.trace) return HPMC_ERR_NOT_READY;
+    CK(cudaDeviceSynchronize());
+    const uint32_t n = std::min(max_warps, h->dv.trace_warps);
+    CK(cudaMemcpy(out, h->dv.trace, sizeof(uint64_t) * n * kTracePoints, cudaMemcpyDeviceToHost));
     return 0;
 }
 

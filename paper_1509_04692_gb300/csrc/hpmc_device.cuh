@@ -52,6 +52,37 @@ __device__ __forceinline__ double u53(uint32_t a, uint32_t b)
     return __ull2double_rn(m) * 0x1.0p-53;
 }
 
+// 2*u53(a, b) - 1 scaled by 2^53: the integer j = 2k - 2^53 with
+// k = (a << 32 | b) >> 11, |j| <= 2^53, so (double)j is exact.  For a factor f,
+// fl((f * 2^-53) * j) equals fl(f * (2*u53 - 1)) bit for bit (the power-of-two
+// scaling of f is exact), with one integer-to-double conversion instead of
+// the conversion, scaling, doubling and subtraction of the direct form.
+__device__ __forceinline__ double pm53(uint32_t a, uint32_t b)
+{
+    const long long k = (long long)((((unsigned long long)a << 32) | b) >> 11);
+    return __ll2double_rn(2 * k - (1LL << 53));
+}
+
+// Periodic wrap of a coordinate moved by less than L, with the sign and
+// upper-bound tests done on the bit pattern (IEEE order of non-negative
+// doubles is the order of their bit patterns); same results as wrap_pos.
+__device__ __forceinline__ double wrap_pos_bits(double x, double L)
+{
+    const long long b = __double_as_longlong(x);
+    if (b < 0 && b != (long long)0x8000000000000000ULL) x = x + L;   // x < 0 (not -0)
+    if (__double_as_longlong(x) >= __double_as_longlong(L)) x = x - L;
+    return x;
+}
+
+// y = x - s (+ L when negative) with the sign test on the bit pattern
+__device__ __forceinline__ double cell_coord_bits(double x, double s, double L)
+{
+    double y = x - s;
+    const long long b = __double_as_longlong(y);
+    if (b < 0 && b != (long long)0x8000000000000000ULL) y = y + L;
+    return y;
+}
+
 // FP32 stand-in for 2*u53(a, b) - 1 built from the 24 top bits of a; exact
 // in FP32 and within 2^-23 of the FP64 value.
 __device__ __forceinline__ float m24(uint32_t a)
@@ -99,12 +130,13 @@ __device__ __forceinline__ Trial2 propose2d(const Rep& rp, double x, double y, d
                                             uint32_t r1, uint32_t r2, uint32_t r3, uint32_t r4,
                                             uint32_t r5, uint32_t r6)
 {
-    const double dx = rp.d * (2.0 * u53(r1, r2) - 1.0);
-    const double dy = rp.d * (2.0 * u53(r3, r4) - 1.0);
-    const double t = rp.tau * (2.0 * u53(r5, r6) - 1.0);
+    // d * (2 u53 - 1) etc., see pm53
+    const double dx = rp.d_s * pm53(r1, r2);
+    const double dy = rp.d_s * pm53(r3, r4);
+    const double t = rp.tau_s * pm53(r5, r6);
     Trial2 o;
-    o.x = wrap_pos(x + dx, rp.L[0]);
-    o.y = wrap_pos(y + dy, rp.L[1]);
+    o.x = wrap_pos_bits(x + dx, rp.L[0]);
+    o.y = wrap_pos_bits(y + dy, rp.L[1]);
     const double tt = t * t;
     const double inv = 1.0 / (1.0 + tt);
     const double cd = (1.0 - tt) * inv;
@@ -145,15 +177,15 @@ __device__ __forceinline__ Trial3 propose3d(const Rep& rp, const double x[3], co
                                             const uint32_t* r)
 {
     Trial3 o;
-    const double dx = rp.d * (2.0 * u53(r[1], r[2]) - 1.0);
-    const double dy = rp.d * (2.0 * u53(r[3], r[4]) - 1.0);
-    const double dz = rp.d * (2.0 * u53(r[5], r[6]) - 1.0);
-    const double v0 = rp.tau * (2.0 * u53(r[7], r[8]) - 1.0);
-    const double v1 = rp.tau * (2.0 * u53(r[9], r[10]) - 1.0);
-    const double v2 = rp.tau * (2.0 * u53(r[11], r[12]) - 1.0);
-    o.x[0] = wrap_pos(x[0] + dx, rp.L[0]);
-    o.x[1] = wrap_pos(x[1] + dy, rp.L[1]);
-    o.x[2] = wrap_pos(x[2] + dz, rp.L[2]);
+    const double dx = rp.d_s * pm53(r[1], r[2]);
+    const double dy = rp.d_s * pm53(r[3], r[4]);
+    const double dz = rp.d_s * pm53(r[5], r[6]);
+    const double v0 = rp.tau_s * pm53(r[7], r[8]);
+    const double v1 = rp.tau_s * pm53(r[9], r[10]);
+    const double v2 = rp.tau_s * pm53(r[11], r[12]);
+    o.x[0] = wrap_pos_bits(x[0] + dx, rp.L[0]);
+    o.x[1] = wrap_pos_bits(x[1] + dy, rp.L[1]);
+    o.x[2] = wrap_pos_bits(x[2] + dz, rp.L[2]);
     const double vv = (v0 * v0 + v1 * v1) + v2 * v2;
     const double inv = 1.0 / sqrt(1.0 + vv);
     const double dq[4] = { inv, v0 * inv, v1 * inv, v2 * inv };
@@ -191,6 +223,40 @@ __device__ __forceinline__ bool sat_half64(const Shape2& sh, double cr, double s
         if (sh.ahi[k] < lo || hi < sh.alo[k]) return true;
     }
     return false;
+}
+
+// One axis of D: half hf = 0 tests A's normal k with B placed in A's frame,
+// hf = 1 tests B's normal k with A placed in B's frame; the operations are
+// those sat_half64 performs for that axis, so D(...) separates iff some
+// (hf, k) returns true here.
+template <int NV>
+__device__ __forceinline__ bool axis_separates64(const Shape2& sh, int hf, int k, double Dx, double Dy,
+                                                 double cA, double sA, double cB, double sB)
+{
+    const int nv = NV ? NV : sh.nv;
+    const double cr = cA * cB + sA * sB;
+    const double sr = cA * sB - sA * cB;
+    double cc, ss, lx, ly;
+    if (hf == 0) {
+        cc = cr; ss = sr;
+        lx = cA * Dx + sA * Dy;
+        ly = cA * Dy - sA * Dx;
+    } else {
+        cc = cr; ss = -sr;
+        lx = -(cB * Dx + sB * Dy);
+        ly = -(cB * Dy - sB * Dx);
+    }
+    double lo = 0.0, hi = 0.0;
+#pragma unroll
+    for (int i = 0; i < (NV ? NV : kMaxV2); ++i) {
+        if (!NV && i >= nv) break;
+        const double px = (cc * sh.vx[i] - ss * sh.vy[i]) + lx;
+        const double py = (ss * sh.vx[i] + cc * sh.vy[i]) + ly;
+        const double t = sh.nx[k] * px + sh.ny[k] * py;
+        lo = (i == 0 || t < lo) ? t : lo;
+        hi = (i == 0 || t > hi) ? t : hi;
+    }
+    return sh.ahi[k] < lo || hi < sh.alo[k];
 }
 
 // D(Delta, zA, zB): true = overlap (touching counts), false = separated.

@@ -13,6 +13,30 @@ constexpr int kMaxV2 = 16;      // polygon vertices
 constexpr int kMaxV3 = 32;      // polyhedron vertices
 constexpr int kNumCounters = 8; // see hpmc_counters_t
 constexpr int kGjkMaxIt = 32;
+constexpr int kTracePoints = 32;
+
+// Warp phase stamps (Sec. 2.5.3 used clock64() traces of one warp to compare
+// queue designs).  Compiled in only with -DHPMC_TRACE.
+#ifdef HPMC_TRACE
+#define HPMC_STAMP(dv, warp_id, first, lane, point)                                      \
+    do {                                                                                 \
+        if ((first) && (lane) == 0 && (dv).trace && (warp_id) < (dv).trace_warps &&      \
+            (point) < kTracePoints)                                                      \
+            (dv).trace[(size_t)(warp_id) * kTracePoints + (point)] = clock64();          \
+    } while (0)
+// global nanosecond timer (comparable across SMs) for entry / exit stamps
+#define HPMC_STAMP_NS(dv, warp_id, lane, point)                                          \
+    do {                                                                                 \
+        if ((lane) == 0 && (dv).trace && (warp_id) < (dv).trace_warps) {                 \
+            unsigned long long t_;                                                       \
+            asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t_));                       \
+            (dv).trace[(size_t)(warp_id) * kTracePoints + (point)] = t_;                 \
+        }                                                                                \
+    } while (0)
+#else
+#define HPMC_STAMP(dv, warp_id, first, lane, point) do { } while (0)
+#define HPMC_STAMP_NS(dv, warp_id, lane, point) do { } while (0)
+#endif
 
 enum : int { CNT_MOVES = 0, CNT_ACCEPT, CNT_REJ_OVERLAP, CNT_REJ_BOUNDARY, CNT_CULL,
              CNT_CHECKS, CNT_RECHECK, CNT_GJKCAP };
@@ -27,6 +51,7 @@ struct Rep {
     uint32_t n, pbase, cbase, ncell;
     uint64_t seed;
     double d, tau;           // move sizes (FP64 contract)
+    double d_s, tau_s;       // d * 2^-53 and tau * 2^-53 (exact; see pm53)
     float d32, tau32;        // FP32 copies for the filter
     uint32_t nselect;
     // FP32 filter thresholds (certified; see hpmc_bounds.h), rounded outward:
@@ -89,6 +114,10 @@ struct Dev {
     uint64_t* sweep;         // [R] sweep counter per replica
     unsigned long long* counters;   // [R * kNumCounters]
     int* error;              // device error word (ERR_*)
+    // warp phase timestamps (trace builds only, -DHPMC_TRACE): kTracePoints
+    // clock64() stamps of the first work item of each warp of a set kernel
+    unsigned long long* trace;
+    uint32_t trace_warps;
 };
 
 }  // namespace hpmc

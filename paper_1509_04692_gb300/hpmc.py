@@ -31,6 +31,7 @@ EXPORTS = [
     "hpmc_reset_counters", "hpmc_check_overlaps", "hpmc_get_state", "hpmc_set_state",
     "hpmc_run_host", "hpmc_autotune", "hpmc_geometry", "hpmc_launches_per_sweep",
     "hpmc_filter_margins", "hpmc_strerror", "hpmc_profile_sweeps", "hpmc_count_overlaps_noalloc",
+    "hpmc_trace_read",
 ]
 
 
@@ -57,9 +58,11 @@ class ReplicaDesc(ctypes.Structure):
 
 
 def _load():
-    path = _build.LIB
+    # HPMC_TRACE=1 selects the trace build (per-warp phase stamps)
+    trace = os.environ.get("HPMC_TRACE", "") not in ("", "0")
+    path = _build.LIB_TRACE if trace else _build.LIB
     if not os.path.exists(path):
-        path = _build.build()
+        path = _build.build(trace=trace)
     lib = ctypes.CDLL(path)
     dp = ctypes.POINTER(ctypes.c_double)
     vp = ctypes.c_void_p
@@ -86,6 +89,7 @@ def _load():
         "hpmc_launches_per_sweep": [vp, ctypes.POINTER(u32)],
         "hpmc_filter_margins": [vp, i32, dp, dp, dp],
         "hpmc_profile_sweeps": [vp, u32, vp, dp, dp],
+        "hpmc_trace_read": [vp, ctypes.POINTER(u64), u32, ctypes.POINTER(u32)],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -236,6 +240,14 @@ class Batch:
         _ck(_lib.hpmc_profile_sweeps(self.h, int(n), ctypes.c_void_p(int(stream) if stream else None),
                                      ctypes.byref(a), ctypes.byref(b)), "hpmc_profile_sweeps")
         return a.value, b.value
+
+    def trace_read(self, max_warps=65536):
+        """Per-warp clock64() phase stamps of the last set kernel (trace builds)."""
+        buf = np.zeros((max_warps, 32), dtype=np.uint64)
+        n = ctypes.c_uint32()
+        _ck(_lib.hpmc_trace_read(self.h, buf.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)), max_warps,
+                                 ctypes.byref(n)), "hpmc_trace_read")
+        return buf[:, : n.value]
 
     def geometry(self, r=0):
         nc = (ctypes.c_int32 * 3)()
