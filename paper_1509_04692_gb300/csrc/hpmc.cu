@@ -248,6 +248,8 @@ int rep_geometry(const hpmc_batch* h, const HostRep& hr, Rep& rp)
     rp.cull_keep = f32_down(h->rc2 - g.e_cull);
     rp.cull_skip = f32_up(h->rc2 + g.e_cull);
     rp.sat_e = f32_up(g.e_sat);
+    rp.e_dlt32 = f32_up(g.e_dlt);
+    rp.e_ori32 = f32_up(g.e_ori);
     rp.e_in = g.e_in;
     rp.e_cull = g.e_cull;
     rp.e_sat = g.e_sat;

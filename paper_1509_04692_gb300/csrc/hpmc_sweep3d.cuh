@@ -1,0 +1,450 @@
+// hpmc_sweep3d.cuh -- one checkerboard set of the 3D sweep (Sec. 2.5.2, 8 sets).
+//
+// Same organisation as the 2D kernel: one warp takes a strip of S = 32/G
+// consecutive active cells along x of one (y, z) row of one replica; the nine
+// neighbour rows that the strip's 3x3x3 stencils touch are contiguous ranges
+// of the cell-sorted state and are staged into shared memory with coalesced
+// 16-byte loads.  The nselect moves of a cell are sequential; the cells of a
+// warp run in lockstep; the G lanes of a cell split its circumsphere cull;
+// survivors go to a warp-wide shared-memory pair queue drained 32 pairs at a
+// time, one pair per lane (GJK is a long sequential iteration, so a pair is
+// not split further), skipping pairs of moves already known to overlap.
+//
+// F32 = true : cull and in-cell decisions certified in FP32; each pair runs
+//              the certified FP32 GJK (hpmc_gjk32.cuh) and falls back to the
+//              FP64 contract GJK when a branch cannot be certified.
+// F32 = false: plain FP64 contract.
+#pragma once
+#include "hpmc_device.cuh"
+#include "hpmc_gjk32.cuh"
+
+namespace hpmc {
+
+template <int G, bool F32>
+struct Warp3 {
+    static constexpr int S = 32 / G;                  // cells per strip
+    static constexpr int M = 2 * S + 1;               // staged cells per row
+    static constexpr int CAPX = 9 * M * 4;
+    static constexpr int CAP = CAPX < 256 ? 256 : (CAPX > 1024 ? 1024 : CAPX);
+    static constexpr int QCAP = 64;
+    float4 ea[F32 ? CAP : 1];                         // FP32 rel.x, rel.y, rel.z, qw
+    float4 eb[F32 ? CAP : 1];                         // FP32 qx, qy, qz, -
+    double ep[F32 ? 1 : CAP][3];                      // FP64 position
+    double eq[F32 ? 1 : CAP][4];                      // FP64 quaternion
+    uint32_t gidx[CAP];
+    uint16_t sbeg[9][M + 1];
+    uint16_t beg[S][27];
+    uint16_t pfx[S][28];
+    float4 qd[QCAP];                                  // queued Delta32
+    uint16_t qe[QCAP];
+    uint8_t qg[QCAP];
+    float4 tra[S], trb[S];                            // FP32 trial: rel', qw' / qx', qy', qz'
+    double tp[S][3], tq[S][4];                        // FP64 trial (FP64 form)
+    uint32_t rw[S][12];                               // words r1..r12
+    uint16_t eA[S];
+    unsigned int ovmask;
+};
+
+__device__ __forceinline__ uint32_t row_count3(const uint32_t* start, uint32_t rowbase, int nc0, int xa, int len)
+{
+    if (xa + len <= nc0) return start[rowbase + xa + len] - start[rowbase + xa];
+    return (start[rowbase + nc0] - start[rowbase + xa]) + (start[rowbase + (xa + len - nc0)] - start[rowbase]);
+}
+
+__device__ __forceinline__ Trial3 trial3_of(const Rep& rp, const Bufs& B, uint32_t gA, const uint32_t* w12)
+{
+    const double x[3] = { B.px[gA], B.py[gA], B.pz[gA] };
+    const double q[4] = { B.q0[gA], B.q1[gA], B.q2[gA], B.q3[gA] };
+    uint32_t r[13];
+    r[0] = 0;
+#pragma unroll
+    for (int k = 0; k < 12; ++k) r[k + 1] = w12[k];
+    return propose3d(rp, x, q, r);
+}
+
+template <int G, bool F32, int NV>
+__global__ void __launch_bounds__(256, 2)
+k_set3d(Dev dv, Shape3 sh, int nxt, int sigma, const uint32_t* __restrict__ item_base)
+{
+    using W = Warp3<G, F32>;
+    constexpr int S = W::S;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    W& ws = reinterpret_cast<W*>(smem_raw)[threadIdx.x >> 5];
+    const int lane = threadIdx.x & 31;
+    const int grp = lane / G;
+    const int sl = lane - grp * G;
+    const unsigned FULL = 0xffffffffu;
+    const Bufs B = dv.buf[nxt];
+    const uint32_t* __restrict__ start = dv.start;
+    const uint32_t nitems = item_base[dv.R];
+    const uint32_t wpb = blockDim.x >> 5;
+
+    for (uint32_t item = blockIdx.x * wpb + (threadIdx.x >> 5); item < nitems; item += gridDim.x * wpb) {
+        uint32_t lo = 0, hi = dv.R;
+        while (hi - lo > 1) {
+            const uint32_t mid = (lo + hi) >> 1;
+            if (__ldg(item_base + mid) <= item) lo = mid; else hi = mid;
+        }
+        const uint32_t r = lo;
+        const Rep& rp = dv.reps[r];
+        const int nc0 = rp.nc[0], nc1 = rp.nc[1], nc2 = rp.nc[2];
+        const int nax = nc0 >> 1;
+        const int spr = (nax + S - 1) / S;
+        const uint32_t local = item - __ldg(item_base + r);
+        const int row = (int)(local / spr);
+        const int strip = (int)(local - (uint32_t)row * spr);
+        const int ny2 = nc1 >> 1;
+        const int iy = 2 * (row % ny2) + ((sigma >> 1) & 1);
+        const int iz = 2 * (row / ny2) + ((sigma >> 2) & 1);
+        const int jfirst = strip * S;
+        const int Sv = min(S, nax - jfirst);
+        const uint64_t sweep = dv.sweep[r] - 1;
+        const double shx = dv.shift[3 * r], shy = dv.shift[3 * r + 1], shz = dv.shift[3 * r + 2];
+        const uint64_t seed = rp.seed;
+        const uint32_t nsel = rp.nselect;
+        unsigned c_moves = 0, c_acc = 0, c_rov = 0, c_rbd = 0, c_cull = 0, c_chk = 0, c_rechk = 0, c_cap = 0;
+        uint32_t rowbase[9];
+#pragma unroll
+        for (int q = 0; q < 9; ++q) {
+            const int jy = (iy + (q % 3) - 1 + nc1) % nc1;
+            const int jz = (iz + (q / 3) - 1 + nc2) % nc2;
+            rowbase[q] = rp.cbase + (uint32_t)nc0 * ((uint32_t)jy + (uint32_t)nc1 * (uint32_t)jz);
+        }
+        const double iwy = (double)iy * rp.w[1];
+        const double iwz = (double)iz * rp.w[2];
+
+        int j0 = 0;
+        while (j0 < Sv) {
+            // ---- sub-strip [j0, j1) whose nine staged rows fit CAP
+            int j1 = Sv;
+            bool skip_cell = false;
+            for (;;) {
+                const int xa = ((sigma & 1) + 2 * (jfirst + j0) - 1 + nc0) % nc0;
+                const int len = 2 * (j1 - j0) + 1;
+                uint32_t cnt = 0;
+                if (lane < 9) cnt = row_count3(start, rowbase[lane], nc0, xa, len);
+                const uint32_t tot = __reduce_add_sync(FULL, cnt);
+                if (tot <= (uint32_t)W::CAP) break;
+                if (j1 == j0 + 1) { skip_cell = true; break; }
+                j1 = j0 + (j1 - j0) / 2;
+            }
+            if (skip_cell) {
+                if (lane == 0) atomicOr(dv.error, ERR_CAPACITY);
+                j0 += 1;
+                continue;
+            }
+            const int xa = ((sigma & 1) + 2 * (jfirst + j0) - 1 + nc0) % nc0;
+            const int Mp = 2 * (j1 - j0) + 1;
+            const int mwrap = (xa + Mp > nc0) ? nc0 - xa : Mp;
+            // ---- stage the nine rows
+            uint32_t off = 0;
+#pragma unroll 1
+            for (int q = 0; q < 9; ++q) {
+                uint32_t run = 0;
+                for (int mb = 0; mb < Mp; mb += 32) {
+                    const int m = mb + lane;
+                    uint32_t cnt = 0;
+                    if (m < Mp) {
+                        const uint32_t c = rowbase[q] + (uint32_t)((xa + m) % nc0);
+                        cnt = start[c + 1] - start[c];
+                    }
+                    uint32_t incl = cnt;
+#pragma unroll
+                    for (int o = 1; o < 32; o <<= 1) {
+                        const uint32_t t = __shfl_up_sync(FULL, incl, o);
+                        if (lane >= o) incl += t;
+                    }
+                    if (m < Mp) ws.sbeg[q][m] = (uint16_t)(off + run + incl - cnt);
+                    run += __shfl_sync(FULL, incl, 31);
+                }
+                if (lane == 0) ws.sbeg[q][Mp] = (uint16_t)(off + run);
+                __syncwarp();
+                const uint32_t gA0 = start[rowbase[q] + xa];
+                const uint32_t gB0 = start[rowbase[q]];
+                const uint32_t lenA = (mwrap < Mp) ? (uint32_t)ws.sbeg[q][mwrap] - off : run;
+                for (uint32_t t = lane; t < run; t += 32) {
+                    const uint32_t gi = t < lenA ? gA0 + t : gB0 + (t - lenA);
+                    const uint32_t si = off + t;
+                    ws.gidx[si] = gi;
+                    if (F32) {
+                        ws.ea[si] = B.f4a[gi];
+                        ws.eb[si] = B.f4b[gi];
+                    } else {
+                        ws.ep[si][0] = B.px[gi]; ws.ep[si][1] = B.py[gi]; ws.ep[si][2] = B.pz[gi];
+                        ws.eq[si][0] = B.q0[gi]; ws.eq[si][1] = B.q1[gi];
+                        ws.eq[si][2] = B.q2[gi]; ws.eq[si][3] = B.q3[gi];
+                    }
+                }
+                off += run;
+            }
+            __syncwarp();
+            // ---- stencil tables
+            const bool valid = grp < (j1 - j0);
+            const int mc = 1 + 2 * grp;
+            const int ix = (sigma & 1) + 2 * (jfirst + j0 + grp);
+            const uint32_t cell_local = (uint32_t)ix + (uint32_t)nc0 * ((uint32_t)iy + (uint32_t)nc1 * (uint32_t)iz);
+            const double iwx = (double)ix * rp.w[0];
+            if (sl == 0) {
+                uint16_t p = 0;
+                ws.pfx[grp][0] = 0;
+#pragma unroll
+                for (int q = 0; q < 27; ++q) {
+                    const int qr = q / 3, qc = q % 3;            // row (y, z), column x
+                    const uint16_t b = valid ? ws.sbeg[qr][mc - 1 + qc] : 0;
+                    const uint16_t e = valid ? ws.sbeg[qr][mc + qc] : 0;
+                    ws.beg[grp][q] = b;
+                    p = (uint16_t)(p + (e - b));
+                    ws.pfx[grp][q + 1] = p;
+                }
+            }
+            __syncwarp();
+            const uint32_t cb = valid ? ws.sbeg[4][mc] : 0;    // centre row (y, z) = q 4
+            const uint32_t n_c = valid ? (uint32_t)ws.sbeg[4][mc + 1] - cb : 0;
+            const int T = ws.pfx[grp][27];
+            const bool live_cell = valid && n_c > 0;
+
+#pragma unroll 1
+            for (uint32_t k = 0; k < nsel; ++k) {
+                int status = 0;
+                if (sl == 0 && live_cell) {
+                    c_moves += 1;
+                    uint32_t w16[16];
+#pragma unroll
+                    for (int b = 0; b < 4; ++b) {
+                        const uint4 bb = move_block(seed, sweep, (uint32_t)sigma, cell_local, k, (uint32_t)b);
+                        w16[4 * b] = bb.x; w16[4 * b + 1] = bb.y; w16[4 * b + 2] = bb.z; w16[4 * b + 3] = bb.w;
+                    }
+                    const uint32_t eA = cb + __umulhi(w16[0], n_c);
+#pragma unroll
+                    for (int q = 0; q < 12; ++q) ws.rw[grp][q] = w16[q + 1];
+                    ws.eA[grp] = (uint16_t)eA;
+                    if (F32) {
+                        const float4 fa = ws.ea[eA], fb = ws.eb[eA];
+                        const float rx = __fadd_rn(fa.x, __fmul_rn(rp.d32, m24(w16[1])));
+                        const float ry = __fadd_rn(fa.y, __fmul_rn(rp.d32, m24(w16[3])));
+                        const float rz = __fadd_rn(fa.z, __fmul_rn(rp.d32, m24(w16[5])));
+                        const float v0 = __fmul_rn(rp.tau32, m24(w16[7]));
+                        const float v1 = __fmul_rn(rp.tau32, m24(w16[9]));
+                        const float v2 = __fmul_rn(rp.tau32, m24(w16[11]));
+                        const float vv = __fmaf_rn(v0, v0, __fmaf_rn(v1, v1, __fmul_rn(v2, v2)));
+                        const float inv = __frcp_rn(__fsqrt_rn(__fadd_rn(1.0f, vv)));
+                        const float d0 = inv, d1 = __fmul_rn(v0, inv), d2 = __fmul_rn(v1, inv), d3 = __fmul_rn(v2, inv);
+                        const float a0 = fa.w, a1 = fb.x, a2 = fb.y, a3 = fb.z;
+                        const float q0 = a0 * d0 - a1 * d1 - a2 * d2 - a3 * d3;
+                        const float q1 = a0 * d1 + a1 * d0 + a2 * d3 - a3 * d2;
+                        const float q2 = a0 * d2 - a1 * d3 + a2 * d0 + a3 * d1;
+                        const float q3 = a0 * d3 + a1 * d2 - a2 * d1 + a3 * d0;
+                        ws.tra[grp] = make_float4(rx, ry, rz, q0);
+                        ws.trb[grp] = make_float4(q1, q2, q3, 0.f);
+                        const bool out = rx < rp.out_lo || ry < rp.out_lo || rz < rp.out_lo || rx > rp.out_hi[0] ||
+                                         ry > rp.out_hi[1] || rz > rp.out_hi[2];
+                        const bool in = rx > rp.in_lo && ry > rp.in_lo && rz > rp.in_lo && rx < rp.in_hi[0] &&
+                                        ry < rp.in_hi[1] && rz < rp.in_hi[2];
+                        if (out) {
+                            status = 2;
+                        } else if (in) {
+                            status = 1;
+                        } else {
+                            c_rechk += 1;
+                            const Trial3 t3 = trial3_of(rp, B, ws.gidx[eA], ws.rw[grp]);
+                            const bool ok = cell_axis(t3.x[0], shx, rp.L[0], rp.inv_w[0], nc0) == ix &&
+                                            cell_axis(t3.x[1], shy, rp.L[1], rp.inv_w[1], nc1) == iy &&
+                                            cell_axis(t3.x[2], shz, rp.L[2], rp.inv_w[2], nc2) == iz;
+                            status = ok ? 1 : 2;
+                        }
+                    } else {
+                        const double x[3] = { ws.ep[eA][0], ws.ep[eA][1], ws.ep[eA][2] };
+                        const double qa[4] = { ws.eq[eA][0], ws.eq[eA][1], ws.eq[eA][2], ws.eq[eA][3] };
+                        const Trial3 t3 = propose3d(rp, x, qa, w16);
+#pragma unroll
+                        for (int a = 0; a < 3; ++a) ws.tp[grp][a] = t3.x[a];
+#pragma unroll
+                        for (int a = 0; a < 4; ++a) ws.tq[grp][a] = t3.q[a];
+                        const bool ok = cell_axis(t3.x[0], shx, rp.L[0], rp.inv_w[0], nc0) == ix &&
+                                        cell_axis(t3.x[1], shy, rp.L[1], rp.inv_w[1], nc1) == iy &&
+                                        cell_axis(t3.x[2], shz, rp.L[2], rp.inv_w[2], nc2) == iz;
+                        status = ok ? 1 : 2;
+                    }
+                }
+                if (lane == 0) ws.ovmask = 0u;
+                status = __shfl_sync(FULL, status, grp * G);
+                __syncwarp();
+                const int myA = (status == 1) ? (int)ws.eA[grp] : -1;
+                float4 ta = make_float4(0.f, 0.f, 0.f, 0.f);
+                double tpx = 0.0, tpy = 0.0, tpz = 0.0;
+                if (status == 1) {
+                    if (F32) ta = ws.tra[grp];
+                    else { tpx = ws.tp[grp][0]; tpy = ws.tp[grp][1]; tpz = ws.tp[grp][2]; }
+                }
+                // ---- cull into the pair queue, drain with GJK
+                int qn = 0;
+#pragma unroll 1
+                for (int it = 0;; ++it) {
+                    const int t = sl + it * G;
+                    const bool live = (status == 1) && t < T && !((ws.ovmask >> grp) & 1u);
+                    bool keep = false;
+                    float4 dl = make_float4(0.f, 0.f, 0.f, 0.f);
+                    int e = 0;
+                    if (live) {
+                        int q = 0;
+#pragma unroll
+                        for (int qq = 1; qq < 27; ++qq) q += (t >= (int)ws.pfx[grp][qq]) ? 1 : 0;
+                        e = ws.beg[grp][q] + (t - ws.pfx[grp][q]);
+                        if (e != myA) {
+                            c_cull += 1;
+                            const int ox = q % 3 - 1, oy = (q / 3) % 3 - 1, oz = q / 9 - 1;
+                            if (F32) {
+                                const float4 f = ws.ea[e];
+                                dl.x = __fsub_rn(__fadd_rn(f.x, (float)ox * rp.w32[0]), ta.x);
+                                dl.y = __fsub_rn(__fadd_rn(f.y, (float)oy * rp.w32[1]), ta.y);
+                                dl.z = __fsub_rn(__fadd_rn(f.z, (float)oz * rp.w32[2]), ta.z);
+                                const float q32 = __fmaf_rn(dl.x, dl.x, __fmaf_rn(dl.y, dl.y, __fmul_rn(dl.z, dl.z)));
+                                if (q32 < rp.cull_keep) {
+                                    keep = true;
+                                } else if (q32 > rp.cull_skip) {
+                                    keep = false;
+                                } else {
+                                    c_rechk += 1;
+                                    const Trial3 t3 = trial3_of(rp, B, ws.gidx[myA], ws.rw[grp]);
+                                    const uint32_t gB = ws.gidx[e];
+                                    const double Dx = min_image(B.px[gB] - t3.x[0], rp.L[0], rp.halfL[0]);
+                                    const double Dy = min_image(B.py[gB] - t3.x[1], rp.L[1], rp.halfL[1]);
+                                    const double Dz = min_image(B.pz[gB] - t3.x[2], rp.L[2], rp.halfL[2]);
+                                    keep = ((Dx * Dx + Dy * Dy) + Dz * Dz) <= sh.rc2;
+                                }
+                            } else {
+                                const double Dx = min_image(ws.ep[e][0] - tpx, rp.L[0], rp.halfL[0]);
+                                const double Dy = min_image(ws.ep[e][1] - tpy, rp.L[1], rp.halfL[1]);
+                                const double Dz = min_image(ws.ep[e][2] - tpz, rp.L[2], rp.halfL[2]);
+                                keep = ((Dx * Dx + Dy * Dy) + Dz * Dz) <= sh.rc2;
+                            }
+                        }
+                    }
+                    const unsigned bal = __ballot_sync(FULL, keep);
+                    if (keep) {
+                        const int pos = qn + __popc(bal & ((1u << lane) - 1u));
+                        ws.qe[pos] = (uint16_t)e;
+                        ws.qg[pos] = (uint8_t)grp;
+                        ws.qd[pos] = dl;
+                    }
+                    qn += __popc(bal);
+                    const bool any_live = __any_sync(FULL, live) != 0;
+                    __syncwarp();
+                    while (qn >= 32 || (!any_live && qn > 0)) {
+                        const int np = qn < 32 ? qn : 32;
+                        if (lane < np) {
+                            const int e2 = ws.qe[lane];
+                            const int g2 = ws.qg[lane];
+                            if (!((ws.ovmask >> g2) & 1u)) {
+                                c_chk += 1;
+                                bool ov;
+                                int its = 0;
+                                if (F32) {
+                                    const float4 d2 = ws.qd[lane];
+                                    const float4 a1 = ws.tra[g2], a2 = ws.trb[g2];
+                                    const float4 b1 = ws.ea[e2], b2 = ws.eb[e2];
+                                    const float qa[4] = { a1.w, a2.x, a2.y, a2.z };
+                                    const float qb[4] = { b1.w, b2.x, b2.y, b2.z };
+                                    const int v = gjk32c<NV>(sh, d2.x, d2.y, d2.z, rp.e_dlt32, qa, rp.e_ori32, qb,
+                                                             0x1.0002p-24f, &its);
+                                    if (v == GJK32_UNCERTAIN) {
+                                        c_rechk += 1;
+                                        const Trial3 t3 = trial3_of(rp, B, ws.gidx[ws.eA[g2]], ws.rw[g2]);
+                                        const uint32_t gB = ws.gidx[e2];
+                                        const double D[3] = { min_image(B.px[gB] - t3.x[0], rp.L[0], rp.halfL[0]),
+                                                              min_image(B.py[gB] - t3.x[1], rp.L[1], rp.halfL[1]),
+                                                              min_image(B.pz[gB] - t3.x[2], rp.L[2], rp.halfL[2]) };
+                                        const double qB[4] = { B.q0[gB], B.q1[gB], B.q2[gB], B.q3[gB] };
+                                        its = 0;
+                                        ov = overlap3d64<NV>(sh, D, t3.q, qB, &its);
+                                    } else {
+                                        ov = (v == GJK32_OVERLAP);
+                                    }
+                                } else {
+                                    const double D[3] = { min_image(ws.ep[e2][0] - ws.tp[g2][0], rp.L[0], rp.halfL[0]),
+                                                          min_image(ws.ep[e2][1] - ws.tp[g2][1], rp.L[1], rp.halfL[1]),
+                                                          min_image(ws.ep[e2][2] - ws.tp[g2][2], rp.L[2], rp.halfL[2]) };
+                                    const double qa[4] = { ws.tq[g2][0], ws.tq[g2][1], ws.tq[g2][2], ws.tq[g2][3] };
+                                    const double qb[4] = { ws.eq[e2][0], ws.eq[e2][1], ws.eq[e2][2], ws.eq[e2][3] };
+                                    ov = overlap3d64<NV>(sh, D, qa, qb, &its);
+                                }
+                                if (its > kGjkMaxIt) c_cap += 1;
+                                if (ov) atomicOr(&ws.ovmask, 1u << g2);
+                            }
+                        }
+                        __syncwarp();
+                        const int rest = qn - np;
+                        uint16_t te = 0; uint8_t tg = 0; float4 td = make_float4(0.f, 0.f, 0.f, 0.f);
+                        if (lane < rest) { te = ws.qe[np + lane]; tg = ws.qg[np + lane]; td = ws.qd[np + lane]; }
+                        __syncwarp();
+                        if (lane < rest) { ws.qe[lane] = te; ws.qg[lane] = tg; ws.qd[lane] = td; }
+                        __syncwarp();
+                        qn = rest;
+                    }
+                    if (!any_live && qn == 0) break;
+                }
+                // ---- accept or reject
+                if (sl == 0 && status != 0) {
+                    if (status == 2) {
+                        c_rbd += 1;
+                    } else if ((ws.ovmask >> grp) & 1u) {
+                        c_rov += 1;
+                    } else {
+                        c_acc += 1;
+                        const int eA = ws.eA[grp];
+                        const uint32_t gA = ws.gidx[eA];
+                        Trial3 t3;
+                        if (F32) {
+                            t3 = trial3_of(rp, B, gA, ws.rw[grp]);
+                        } else {
+#pragma unroll
+                            for (int a = 0; a < 3; ++a) t3.x[a] = ws.tp[grp][a];
+#pragma unroll
+                            for (int a = 0; a < 4; ++a) t3.q[a] = ws.tq[grp][a];
+                        }
+                        B.px[gA] = t3.x[0]; B.py[gA] = t3.x[1]; B.pz[gA] = t3.x[2];
+                        B.q0[gA] = t3.q[0]; B.q1[gA] = t3.q[1]; B.q2[gA] = t3.q[2]; B.q3[gA] = t3.q[3];
+                        const float4 na = make_float4((float)(cell_coord_bits(t3.x[0], shx, rp.L[0]) - iwx),
+                                                      (float)(cell_coord_bits(t3.x[1], shy, rp.L[1]) - iwy),
+                                                      (float)(cell_coord_bits(t3.x[2], shz, rp.L[2]) - iwz),
+                                                      (float)t3.q[0]);
+                        const float4 nb = make_float4((float)t3.q[1], (float)t3.q[2], (float)t3.q[3], 0.f);
+                        B.f4a[gA] = na;
+                        B.f4b[gA] = nb;
+                        if (F32) { ws.ea[eA] = na; ws.eb[eA] = nb; }
+                        else {
+#pragma unroll
+                            for (int a = 0; a < 3; ++a) ws.ep[eA][a] = t3.x[a];
+#pragma unroll
+                            for (int a = 0; a < 4; ++a) ws.eq[eA][a] = t3.q[a];
+                        }
+                    }
+                }
+                __syncwarp();
+            }
+            j0 = j1;
+            __syncwarp();
+        }
+        c_moves = __reduce_add_sync(FULL, c_moves);
+        c_acc = __reduce_add_sync(FULL, c_acc);
+        c_rov = __reduce_add_sync(FULL, c_rov);
+        c_rbd = __reduce_add_sync(FULL, c_rbd);
+        c_cull = __reduce_add_sync(FULL, c_cull);
+        c_chk = __reduce_add_sync(FULL, c_chk);
+        c_rechk = __reduce_add_sync(FULL, c_rechk);
+        c_cap = __reduce_add_sync(FULL, c_cap);
+        if (lane == 0) {
+            unsigned long long* C = dv.counters + (size_t)r * kNumCounters;
+            atomicAdd(C + CNT_MOVES, (unsigned long long)c_moves);
+            atomicAdd(C + CNT_ACCEPT, (unsigned long long)c_acc);
+            atomicAdd(C + CNT_REJ_OVERLAP, (unsigned long long)c_rov);
+            atomicAdd(C + CNT_REJ_BOUNDARY, (unsigned long long)c_rbd);
+            atomicAdd(C + CNT_CULL, (unsigned long long)c_cull);
+            atomicAdd(C + CNT_CHECKS, (unsigned long long)c_chk);
+            if (c_rechk) atomicAdd(C + CNT_RECHECK, (unsigned long long)c_rechk);
+            if (c_cap) atomicAdd(C + CNT_GJKCAP, (unsigned long long)c_cap);
+        }
+    }
+}
+
+}  // namespace hpmc

@@ -62,6 +62,8 @@ struct Rep {
     float cull_keep;         // |D32|^2 < cull_keep -> FP64 keeps the pair
     float cull_skip;         // |D32|^2 > cull_skip -> FP64 culls the pair
     float sat_e;             // separating-axis / support gap margin
+    float e_dlt32;           // |Delta32 - Delta64| per component (3D GJK input bound)
+    float e_ori32;           // |q'32 - q'64| per component of the FP32 trial orientation
     double e_in, e_cull, e_sat;  // the same margins in FP64 (reporting)
 };
 

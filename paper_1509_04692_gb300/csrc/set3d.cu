@@ -1,4 +1,4 @@
-// 3D (convex polyhedra) units: overlap-check kernel and the set-kernel table.
+// 3D (convex polyhedra): overlap-check kernel.
 #include "hpmc_device.cuh"
 #include "hpmc_launch.h"
 
@@ -43,9 +43,6 @@ __global__ void k_check3d(Dev dv, Shape3 sh, int b, int32_t only_r, unsigned lon
             }
     if (n) atomicAdd(out, n);
 }
-
-SetKernel set3d_f32_kernel(int, bool) { return { nullptr, 0 }; }
-SetKernel set3d_f64_kernel(int, bool) { return { nullptr, 0 }; }
 
 }  // namespace hpmc
 
