@@ -193,6 +193,22 @@ int hpmc_profile_sweeps(hpmc_t h, uint32_t n, void* stream, double* ms_rebuild, 
  */
 int hpmc_trace_read(hpmc_t h, uint64_t* out, uint32_t max_warps, uint32_t* n_points);
 
+/*
+ * hpmc_pair_test -- evaluate the overlap test on n independent pairs on the
+ * GPU, for validation.  A sits at the origin with orientation qA, B at Delta
+ * (minimum image already applied) with orientation qB; host arrays
+ * D[n*dim], qA[n*(2|4)], qB[n*(2|4)] in FP64.  out64[n] receives the FP64
+ * contract's verdict (1 overlap, 0 separated); out32[n] the FP32 filter's
+ * verdict from the FP32-cast inputs (1 overlap, 0 separated, >= 2
+ * uncertain: the sweep would re-decide in FP64; in 3D the value says why:
+ * 2 converged apart within the error bound, 3 enclosed but the origin within
+ * the bound of a face, 4 degenerate simplex, 5 iteration cap).  Shape and dim as in
+ * hpmc_batch_create.  Synchronous; allocates and frees its own device
+ * buffers.
+ */
+int hpmc_pair_test(int dim, const double* verts, uint32_t nv, uint32_t n, const double* D,
+                   const double* qA, const double* qB, int32_t* out64, int32_t* out32);
+
 /* Geometry of replica r: cells per axis, cell width, circumradius. */
 int hpmc_geometry(hpmc_t h, int32_t r, int32_t* nc, double* w, double* R);
 

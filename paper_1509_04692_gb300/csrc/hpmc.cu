@@ -17,6 +17,7 @@
 #include "hpmc_bounds.h"
 #include "hpmc_launch.h"
 #include "hpmc_rebuild.cuh"
+#include "hpmc_shape.h"
 
 using namespace hpmc;
 
@@ -120,74 +121,11 @@ bool is_finite(double x) { return std::isfinite(x); }
 // geometry shared by every replica: circumradius and the overlap constants
 int shape_setup(hpmc_batch* h, int dim, const double* verts, uint32_t nv)
 {
-    if (dim != 2 && dim != 3) return HPMC_ERR_INVALID_ARG;
-    if (dim == 2 && (nv < 3 || nv > (uint32_t)kMaxV2)) return HPMC_ERR_INVALID_ARG;
-    if (dim == 3 && (nv < 4 || nv > (uint32_t)kMaxV3)) return HPMC_ERR_INVALID_ARG;
-    if (!verts) return HPMC_ERR_INVALID_ARG;
-    for (uint32_t i = 0; i < nv * (uint32_t)dim; ++i)
-        if (!is_finite(verts[i])) return HPMC_ERR_INVALID_ARG;
+    const int rc = build_shapes(dim, verts, nv, h->sh2, h->sh3, h->Rc, h->rc2);
+    if (rc) return rc;
     h->dim = dim;
     h->nv = (int)nv;
     std::memcpy(h->verts, verts, sizeof(double) * nv * dim);
-    double r2 = 0.0;
-    for (uint32_t i = 0; i < nv; ++i) {
-        const double* v = verts + (size_t)i * dim;
-        double q = v[0] * v[0] + v[1] * v[1];
-        if (dim == 3) q = q + v[2] * v[2];
-        if (q > r2) r2 = q;
-    }
-    h->Rc = std::sqrt(r2);
-    if (!(h->Rc > 0.0)) return HPMC_ERR_INVALID_ARG;
-    const double dcut = h->Rc + h->Rc;
-    h->rc2 = dcut * dcut;
-    if (dim == 2) {
-        // convex and counter-clockwise: strictly left turns everywhere
-        for (uint32_t i = 0; i < nv; ++i) {
-            const double* p0 = verts + 2 * i;
-            const double* p1 = verts + 2 * ((i + 1) % nv);
-            const double* p2 = verts + 2 * ((i + 2) % nv);
-            const double cr = (p1[0] - p0[0]) * (p2[1] - p1[1]) - (p1[1] - p0[1]) * (p2[0] - p1[0]);
-            if (!(cr > 0.0)) return HPMC_ERR_INVALID_ARG;
-        }
-        Shape2& s = h->sh2;
-        s = Shape2{};
-        s.nv = (int)nv;
-        for (uint32_t k = 0; k < nv; ++k) {
-            s.vx[k] = verts[2 * k];
-            s.vy[k] = verts[2 * k + 1];
-        }
-        for (uint32_t k = 0; k < nv; ++k) {
-            const uint32_t k1 = (k + 1) % nv;
-            s.nx[k] = s.vy[k1] - s.vy[k];
-            s.ny[k] = s.vx[k] - s.vx[k1];
-            double lo = 0.0, hi = 0.0;
-            for (uint32_t i = 0; i < nv; ++i) {
-                const double t = s.nx[k] * s.vx[i] + s.ny[k] * s.vy[i];
-                if (i == 0 || t < lo) lo = t;
-                if (i == 0 || t > hi) hi = t;
-            }
-            s.alo[k] = lo;
-            s.ahi[k] = hi;
-        }
-        for (uint32_t k = 0; k < nv; ++k) {
-            s.fvx[k] = (float)s.vx[k]; s.fvy[k] = (float)s.vy[k];
-            s.fnx[k] = (float)s.nx[k]; s.fny[k] = (float)s.ny[k];
-            s.falo[k] = (float)s.alo[k]; s.fahi[k] = (float)s.ahi[k];
-        }
-        s.rc2 = h->rc2;
-        s.frc2 = (float)h->rc2;
-    } else {
-        Shape3& s = h->sh3;
-        s = Shape3{};
-        s.nv = (int)nv;
-        for (uint32_t k = 0; k < nv; ++k)
-            for (int a = 0; a < 3; ++a) {
-                s.v[k][a] = verts[3 * k + a];
-                s.fv[k][a] = (float)verts[3 * k + a];
-            }
-        s.rc2 = h->rc2;
-        s.frc2 = (float)h->rc2;
-    }
     return 0;
 }
 
@@ -237,8 +175,18 @@ int rep_geometry(const hpmc_batch* h, const HostRep& hr, Rep& rp)
         }
         g.e_sat = sat2_margin(g, h->Rc, vm, nm, am);
     } else {
-        g.e_sat = 0.0;   // 3D filter margins are set by the 3D path
+        for (int k = 0; k < h->sh3.nv; ++k)
+            for (int a = 0; a < 3; ++a) vm = std::max(vm, std::fabs(h->sh3.v[k][a]));
+        // the 3D kernel takes its FP32 trial orientation as a cast of the FP64
+        // contract's trial quaternion (|q'| = 1 within 1e-15)
+        g.e_ori = kU32 * 1.000001 + 2e-15;
+        g.e_sat = gjk3_vertex_margin(g, h->Rc, vm);
     }
+    rp.e_pb32 = f32_up(h->dim == 3 ? g.e_sat : 0.0);
+    rp.e_va32 = f32_up(2.0 * kU32 * vm);
+    // band outside which the FP64 GJK verdict equals the exact predicate: far
+    // above its own rounding (~1e-13 of the shape size)
+    rp.tau3 = f32_up(1e-9 * 2.0 * h->Rc);
     rp.in_lo = f32_up(g.e_in);
     rp.out_lo = f32_down(-g.e_in);
     for (int a = 0; a < 3; ++a) {

@@ -111,4 +111,38 @@ inline double sat2_margin(const Margins& g, double R, double vm, double nm, doub
     return 2.0 * (e32 + e64);
 }
 
+// 3D: bound on |pb32 - pb| per component for B's vertices moved into A's
+// frame (qr = conj(qA) qB, l = rot(conj(qA), Delta), pb = rot(qr, v) + l),
+// where pb is the exact transform of the FP64 contract's inputs and pb32 the
+// FP32 evaluation from the FP32 inputs.  vm = max |vertex component|.
+inline double gjk3_vertex_margin(const Margins& g, double R, double vm)
+{
+    // Magnitudes use what the operations preserve (unit quaternions, norm
+    // preserving rotations) instead of the generic model, which would
+    // overestimate the rotated vectors a hundredfold.
+    const double u = kU32 * 1.0001;
+    const double ea = g.e_ori, eb = kU32 * 1.000001 + 1e-15;   // quaternion component errors
+    // qr = conj(qA) qB: each component a signed sum of four products with
+    // sum |a_i b_j| <= |a| |b| <= 1 (plus slack); sum |a_i| <= 2 for unit a
+    const double e_qr = 2.0 * (ea + eb) + 2.0 * ea * eb + 4.0 * u * 1.000001;
+    // rot(q, x) for |x|_2 <= X, component errors ex, quaternion errors eq:
+    // t = 2 q_v x x (|t| <= 2X); o = (x + w t) + q_v x t (|o| <= 5X before the
+    // cancellations of an exact rotation)
+    auto rot_err = [&](double X, double ex, double eq) {
+        const double e_cross1 = 2.0 * (ex + X * eq + ex * eq) + 3.0 * u * X;   // q_v x x, per component
+        const double et = 2.0 * e_cross1;                                      // times 2 (exact)
+        const double T = 2.0 * X * 1.000001;
+        const double e_wt = et + T * eq + et * eq + u * T;                     // w t
+        const double e_s1 = ex + e_wt + u * 3.0 * X;                           // x + w t
+        const double e_cross2 = 2.0 * (et + T * eq + et * eq) + 3.0 * u * T;   // q_v x t
+        return e_s1 + e_cross2 + u * 5.0 * X;
+    };
+    const double X_D = 2.0 * R * (1.0 + 1e-9) + 2.0 * g.e_dlt;
+    const double e_l = rot_err(X_D, g.e_dlt, ea);
+    const double X_v = std::sqrt(3.0) * vm;
+    const double e_rv = rot_err(X_v, kU32 * vm, e_qr);
+    const double e_pb = e_rv + e_l + u * (X_v + X_D) * 5.0;
+    return 2.0 * e_pb;
+}
+
 }  // namespace hpmc

@@ -173,19 +173,13 @@ __device__ __forceinline__ void qrot(const double q[4], const double v[3], doubl
 struct Trial3 { double x[3]; double q[4]; };
 
 // 3D translation + rotation dq = (1, v) / sqrt(1 + v.v) from words r1..r12.
-__device__ __forceinline__ Trial3 propose3d(const Rep& rp, const double x[3], const double q[4],
-                                            const uint32_t* r)
+// trial orientation of the contract: q' = renorm(q (x) dq), dq = (1, v) / |(1, v)|,
+// v = tau (2u - 1) per component from words r[7..12]
+__device__ __forceinline__ void propose3d_orient(const Rep& rp, const double q[4], const uint32_t* r, double o[4])
 {
-    Trial3 o;
-    const double dx = rp.d_s * pm53(r[1], r[2]);
-    const double dy = rp.d_s * pm53(r[3], r[4]);
-    const double dz = rp.d_s * pm53(r[5], r[6]);
     const double v0 = rp.tau_s * pm53(r[7], r[8]);
     const double v1 = rp.tau_s * pm53(r[9], r[10]);
     const double v2 = rp.tau_s * pm53(r[11], r[12]);
-    o.x[0] = wrap_pos_bits(x[0] + dx, rp.L[0]);
-    o.x[1] = wrap_pos_bits(x[1] + dy, rp.L[1]);
-    o.x[2] = wrap_pos_bits(x[2] + dz, rp.L[2]);
     const double vv = (v0 * v0 + v1 * v1) + v2 * v2;
     const double inv = 1.0 / sqrt(1.0 + vv);
     const double dq[4] = { inv, v0 * inv, v1 * inv, v2 * inv };
@@ -193,7 +187,20 @@ __device__ __forceinline__ Trial3 propose3d(const Rep& rp, const double x[3], co
     qmul(q, dq, q1);
     const double n2 = ((q1[0] * q1[0] + q1[1] * q1[1]) + q1[2] * q1[2]) + q1[3] * q1[3];
     const double f = 1.5 - 0.5 * n2;
-    o.q[0] = q1[0] * f; o.q[1] = q1[1] * f; o.q[2] = q1[2] * f; o.q[3] = q1[3] * f;
+    o[0] = q1[0] * f; o[1] = q1[1] * f; o[2] = q1[2] * f; o[3] = q1[3] * f;
+}
+
+__device__ __forceinline__ Trial3 propose3d(const Rep& rp, const double x[3], const double q[4],
+                                            const uint32_t* r)
+{
+    Trial3 o;
+    const double dx = rp.d_s * pm53(r[1], r[2]);
+    const double dy = rp.d_s * pm53(r[3], r[4]);
+    const double dz = rp.d_s * pm53(r[5], r[6]);
+    o.x[0] = wrap_pos_bits(x[0] + dx, rp.L[0]);
+    o.x[1] = wrap_pos_bits(x[1] + dy, rp.L[1]);
+    o.x[2] = wrap_pos_bits(x[2] + dz, rp.L[2]);
+    propose3d_orient(rp, q, r, o.q);
     return o;
 }
 

@@ -1,29 +1,40 @@
-// hpmc_gjk32.cuh -- FP32 GJK that certifies the FP64 contract's verdict.
+// hpmc_gjk32.cuh -- FP32 GJK with certificates about the exact shapes.
 //
-// The FP64 contract (overlap3d64 in hpmc_device.cuh) decides overlap by a
-// sequence of data-dependent branches (support argmax, Voronoi-region tests,
-// sign tests).  This routine performs the same operations in FP32 and carries
-// with every value a bound on its distance to the value the FP64 contract
-// computes at the same step.  A branch is taken only when the FP32 operands
-// are farther apart than their combined bounds, which proves that the FP64
-// run takes the same branch; then, by induction, both runs visit the same
-// simplices and return the same verdict.  Any branch that cannot be certified
-// returns GJK32_UNCERTAIN and the caller re-decides with the FP64 contract.
-//
-// Bound model per operation (a32, b32 with bounds ea, eb on |a32 - a64|,
-// |b32 - b64|; r = fl32(a32 op b32); the FP64 side rounds once too):
-//   add/sub: |r - r64| <= ea + eb + (u32 + u64) |r| (1 + ...)
-//   mul:     |r - r64| <= |a32| eb + (|b32| + eb) ea + (u32 + u64) |r| (...)
-//   div:     |r - r64| <= (|a32| eb + |b32| ea) / (|b32| (|b32| - eb)) + (...)
-// All bound arithmetic rounds upward (__f*_ru) and every bound is inflated
-// by (1 + 2^-20) and a tiny absolute term, so rounding of the bound
-// computation itself cannot make it too small.
+// The FP64 contract (overlap3d64 in hpmc_device.cuh) breaks exact support
+// ties by vertex index; near GJK's convergence ties are the rule for
+// polytopes (the search direction becomes a face normal or an edge cross), and
+// which of the tied vertices FP64 rounding picks cannot be reproduced in FP32.
+// So the FP32 path does not mimic the FP64 run; it runs GJK in FP32 and then
+// proves a verdict about the exact shapes (the exact transform of the FP64
+// contract's inputs) with margin tau:
+//  * overlap: the origin lies inside the tetrahedron of four exact vertex
+//    differences of B - A, farther than tau from each face.  Then B - A
+//    contains the origin at depth > tau, every FP64 support query has v.w <
+//    0, so the FP64 GJK cannot answer "separated" (its cap counts as overlap):
+//    it answers overlap.
+//  * separated: some direction n has every vertex of B above every vertex of
+//    A by more than tau |n|.  The FP64 closest-point GJK then answers
+//    "separated": its distance estimate decreases to the positive separation
+//    and the test v.w > 0 fires; this relies on GJK's termination for
+//    polytopes separated far above its rounding (tau = 1e-9 of the shape
+//    size, rounding ~1e-13), checked on random near-contact pairs by the
+//    tests rather than proved.
+// Anything not certified is re-decided by the FP64 contract.  All bound
+// arithmetic rounds upward (__f*_ru) and bounds are inflated slightly.
 #pragma once
 #include "hpmc_types.h"
 
 namespace hpmc {
 
-enum : int { GJK32_SEPARATED = 0, GJK32_OVERLAP = 1, GJK32_UNCERTAIN = 2 };
+// verdicts; every value >= GJK32_UNCERTAIN means "not certified" and names why
+enum : int {
+    GJK32_SEPARATED = 0,
+    GJK32_OVERLAP = 1,
+    GJK32_UNCERTAIN = 2,        // converged apart, gap within the bound
+    GJK32_UNC_INSIDE = 3,       // enclosed, origin within the bound of a face
+    GJK32_UNC_DEGENERATE = 4,   // flat simplex or zero direction
+    GJK32_UNC_CAP = 5           // iteration cap
+};
 
 struct Fe { float v, e; };                 // value, bound on |value - FP64 value|
 struct Fe3 { Fe x, y, z; };
@@ -111,198 +122,107 @@ __device__ __forceinline__ Fe3 fe_qrot(const Fe q[4], const Fe3& v)
              fe_add(fe_add(v.z, fe_mul(q[0], tz)), fe_sub(fe_mul(q[1], ty), fe_mul(q[2], tx))) };
 }
 
-// a strictly above b in the FP64 run
-__device__ __forceinline__ bool fe_gt_sure(Fe a, Fe b) { return fe_pos(fe_sub(a, b)); }
-
-// Certified support of B - A in direction d: the FP64 run picks the first
-// strict maximum of pb.d and the first strict minimum of v.d; certified when
-// the chosen index beats every other by more than the bounds.
-template <int NV>
-__device__ __forceinline__ bool support32(const Shape3& sh, const Fe3* pb, const Fe3* va, const Fe3& d,
-                                          Fe3& out)
+// ---------------------------------------------------------------- FP32 GJK
+// Plain FP32 GJK with the contract's steps; every simplex point remembers the
+// vertex pair (ib, ia) it came from so that the result can be certified.
+struct G32 {
+    float x, y, z;
+};
+__device__ __forceinline__ G32 g_sub(G32 a, G32 b) { return { a.x - b.x, a.y - b.y, a.z - b.z }; }
+__device__ __forceinline__ G32 g_neg(G32 a) { return { -a.x, -a.y, -a.z }; }
+__device__ __forceinline__ float g_dot(G32 a, G32 b) { return (a.x * b.x + a.y * b.y) + a.z * b.z; }
+__device__ __forceinline__ G32 g_cross(G32 a, G32 b)
 {
-    const int nv = NV ? NV : sh.nv;
+    return { a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x };
+}
+__device__ __forceinline__ G32 g_axpy(G32 a, float t, G32 b) { return { a.x + t * b.x, a.y + t * b.y, a.z + t * b.z }; }
+
+struct SPt {
+    G32 p;
+    int ib, ia;
+};
+
+template <int NV>
+__device__ __forceinline__ SPt g_support(int nv, const G32* pb, const G32* va, G32 d)
+{
     int ib = 0, ia = 0;
-    Fe best = fe3_dot(pb[0], d), least = fe3_dot(va[0], d);
+    float best = g_dot(pb[0], d), least = g_dot(va[0], d);
 #pragma unroll
-    for (int i = 1; i < nv; ++i) {
-        const Fe t = fe3_dot(pb[i], d);
-        if (t.v > best.v) { best = t; ib = i; }
-        const Fe u = fe3_dot(va[i], d);
-        if (u.v < least.v) { least = u; ia = i; }
+    for (int i = 1; i < (NV ? NV : kMaxV3); ++i) {
+        if (!NV && i >= nv) break;
+        const float t = g_dot(pb[i], d);
+        if (t > best) { best = t; ib = i; }
+        const float u = g_dot(va[i], d);
+        if (u < least) { least = u; ia = i; }
     }
-    bool ok = true;
-#pragma unroll
-    for (int i = 0; i < nv; ++i) {
-        if (i != ib) ok = ok && fe_gt_sure(best, fe3_dot(pb[i], d));
-        if (i != ia) ok = ok && fe_gt_sure(fe3_dot(va[i], d), least);
-    }
-    out = fe3_sub(pb[ib], va[ia]);
-    return ok;
+    return { g_sub(pb[ib], va[ia]), ib, ia };
 }
 
-// closest point of segment [a, b]; returns mask (a=1, b=2), -1 uncertain
-__device__ __forceinline__ int closest_seg32(const Fe3& a, const Fe3& b, Fe3& out)
+__device__ __forceinline__ int g_closest_seg(G32 a, G32 b, G32& out)
 {
-    const Fe3 ab = fe3_sub(b, a);
-    const Fe3 ap = fe3_neg(a);
-    const Fe tn = fe3_dot(ab, ap);
-    if (!fe_sure(tn)) return -1;
-    if (tn.v <= 0.f) { out = a; return 1; }
-    const Fe den = fe3_dot(ab, ab);
-    const Fe dd = fe_sub(tn, den);
-    if (!fe_sure(dd)) return -1;
-    if (dd.v >= 0.f) { out = b; return 2; }
-    bool ok = true;
-    const Fe t = fe_div(tn, den, &ok);
-    if (!ok) return -1;
-    out = fe3_axpy(a, t, ab);
+    const G32 ab = g_sub(b, a), ap = g_neg(a);
+    const float tn = g_dot(ab, ap);
+    if (tn <= 0.f) { out = a; return 1; }
+    const float den = g_dot(ab, ab);
+    if (tn >= den) { out = b; return 2; }
+    out = g_axpy(a, tn / den, ab);
     return 3;
 }
 
-// closest point of triangle (a, b, c); mask (a=1, b=2, c=4), 0 degenerate,
-// -1 uncertain.  Every branch of the contract's region tests is certified.
-__device__ __forceinline__ int closest_tri32(const Fe3& a, const Fe3& b, const Fe3& c, Fe3& out)
+__device__ __forceinline__ int g_closest_tri(G32 a, G32 b, G32 c, G32& out)
 {
-    const Fe3 ab = fe3_sub(b, a), ac = fe3_sub(c, a), ap = fe3_neg(a);
-    const Fe d1 = fe3_dot(ab, ap), d2 = fe3_dot(ac, ap);
-    // (d1 <= 0 && d2 <= 0)
-    {
-        const bool s1 = fe_sure(d1), s2 = fe_sure(d2);
-        const bool c1 = d1.v <= 0.f, c2 = d2.v <= 0.f;
-        if ((s1 && !c1) || (s2 && !c2)) { /* condition false for sure */ }
-        else if (s1 && s2) { out = a; return 1; }
-        else return -1;
-    }
-    const Fe3 bp = fe3_neg(b);
-    const Fe d3 = fe3_dot(ab, bp), d4 = fe3_dot(ac, bp);
-    // (d3 >= 0 && d4 <= d3)
-    {
-        const Fe e43 = fe_sub(d4, d3);
-        const bool s1 = fe_sure(d3), s2 = fe_sure(e43);
-        const bool c1 = d3.v >= 0.f, c2 = e43.v <= 0.f;
-        if ((s1 && !c1) || (s2 && !c2)) { }
-        else if (s1 && s2) { out = b; return 2; }
-        else return -1;
-    }
-    const Fe vc = fe_sub(fe_mul(d1, d4), fe_mul(d3, d2));
-    // (vc <= 0 && d1 >= 0 && d3 <= 0)
-    {
-        const bool s0 = fe_sure(vc), s1 = fe_sure(d1), s2 = fe_sure(d3);
-        const bool c0 = vc.v <= 0.f, c1 = d1.v >= 0.f, c2 = d3.v <= 0.f;
-        if ((s0 && !c0) || (s1 && !c1) || (s2 && !c2)) { }
-        else if (s0 && s1 && s2) {
-            bool ok = true;
-            const Fe t = fe_div(d1, fe_sub(d1, d3), &ok);
-            if (!ok) return -1;
-            out = fe3_axpy(a, t, ab);
-            return 3;
-        } else return -1;
-    }
-    const Fe3 cp = fe3_neg(c);
-    const Fe d5 = fe3_dot(ab, cp), d6 = fe3_dot(ac, cp);
-    // (d6 >= 0 && d5 <= d6)
-    {
-        const Fe e56 = fe_sub(d5, d6);
-        const bool s1 = fe_sure(d6), s2 = fe_sure(e56);
-        const bool c1 = d6.v >= 0.f, c2 = e56.v <= 0.f;
-        if ((s1 && !c1) || (s2 && !c2)) { }
-        else if (s1 && s2) { out = c; return 4; }
-        else return -1;
-    }
-    const Fe vb = fe_sub(fe_mul(d5, d2), fe_mul(d1, d6));
-    // (vb <= 0 && d2 >= 0 && d6 <= 0)
-    {
-        const bool s0 = fe_sure(vb), s1 = fe_sure(d2), s2 = fe_sure(d6);
-        const bool c0 = vb.v <= 0.f, c1 = d2.v >= 0.f, c2 = d6.v <= 0.f;
-        if ((s0 && !c0) || (s1 && !c1) || (s2 && !c2)) { }
-        else if (s0 && s1 && s2) {
-            bool ok = true;
-            const Fe t = fe_div(d2, fe_sub(d2, d6), &ok);
-            if (!ok) return -1;
-            out = fe3_axpy(a, t, ac);
-            return 5;
-        } else return -1;
-    }
-    const Fe va = fe_sub(fe_mul(d3, d6), fe_mul(d5, d4));
-    const Fe e43 = fe_sub(d4, d3), e56 = fe_sub(d5, d6);
-    // (va <= 0 && e43 >= 0 && e56 >= 0)
-    {
-        const bool s0 = fe_sure(va), s1 = fe_sure(e43), s2 = fe_sure(e56);
-        const bool c0 = va.v <= 0.f, c1 = e43.v >= 0.f, c2 = e56.v >= 0.f;
-        if ((s0 && !c0) || (s1 && !c1) || (s2 && !c2)) { }
-        else if (s0 && s1 && s2) {
-            bool ok = true;
-            const Fe t = fe_div(e43, fe_add(e43, e56), &ok);
-            if (!ok) return -1;
-            out = fe3_axpy(b, t, fe3_sub(c, b));
-            return 6;
-        } else return -1;
-    }
-    const Fe sum = fe_add(fe_add(va, vb), vc);
-    if (!fe_sure(sum)) return -1;
-    if (!(sum.v > 0.f)) return 0;
-    bool ok = true;
-    const Fe den = fe_div(Fe{ 1.0f, 0.0f }, sum, &ok);
-    if (!ok) return -1;
-    const Fe v = fe_mul(vb, den), w = fe_mul(vc, den);
-    out = { fe_add(fe_add(a.x, fe_mul(ab.x, v)), fe_mul(ac.x, w)),
-            fe_add(fe_add(a.y, fe_mul(ab.y, v)), fe_mul(ac.y, w)),
-            fe_add(fe_add(a.z, fe_mul(ab.z, v)), fe_mul(ac.z, w)) };
+    const G32 ab = g_sub(b, a), ac = g_sub(c, a), ap = g_neg(a);
+    const float d1 = g_dot(ab, ap), d2 = g_dot(ac, ap);
+    if (d1 <= 0.f && d2 <= 0.f) { out = a; return 1; }
+    const G32 bp = g_neg(b);
+    const float d3 = g_dot(ab, bp), d4 = g_dot(ac, bp);
+    if (d3 >= 0.f && d4 <= d3) { out = b; return 2; }
+    const float vc = d1 * d4 - d3 * d2;
+    if (vc <= 0.f && d1 >= 0.f && d3 <= 0.f) { out = g_axpy(a, d1 / (d1 - d3), ab); return 3; }
+    const G32 cp = g_neg(c);
+    const float d5 = g_dot(ab, cp), d6 = g_dot(ac, cp);
+    if (d6 >= 0.f && d5 <= d6) { out = c; return 4; }
+    const float vb = d5 * d2 - d1 * d6;
+    if (vb <= 0.f && d2 >= 0.f && d6 <= 0.f) { out = g_axpy(a, d2 / (d2 - d6), ac); return 5; }
+    const float va = d3 * d6 - d5 * d4;
+    const float e43 = d4 - d3, e56 = d5 - d6;
+    if (va <= 0.f && e43 >= 0.f && e56 >= 0.f) { out = g_axpy(b, e43 / (e43 + e56), g_sub(c, b)); return 6; }
+    const float sum = (va + vb) + vc;
+    if (!(sum > 0.f)) return 0;
+    const float den = 1.0f / sum;
+    const float v = vb * den, w = vc * den;
+    out = { (a.x + ab.x * v) + ac.x * w, (a.y + ab.y * v) + ac.y * w, (a.z + ab.z * v) + ac.z * w };
     return 7;
 }
 
-// origin strictly beyond plane (p, q, r) from s: 1 yes, 0 no, -1 uncertain
-__device__ __forceinline__ int origin_outside32(const Fe3& p, const Fe3& q, const Fe3& r, const Fe3& s)
+__device__ __forceinline__ bool g_outside(G32 p, G32 q, G32 r, G32 s)
 {
-    const Fe3 n = fe3_cross(fe3_sub(q, p), fe3_sub(r, p));
-    const Fe sp = fe3_dot(fe3_neg(p), n);
-    const Fe sd = fe3_dot(fe3_sub(s, p), n);
-    // (sp > 0 && sd < 0) || (sp < 0 && sd > 0): zero on either side means "no"
-    if (!fe_sure(sp) || !fe_sure(sd)) {
-        // a certain zero cannot be told apart from a tiny nonzero: uncertain
-        return -1;
-    }
-    return ((sp.v > 0.f) != (sd.v > 0.f)) ? 1 : 0;
+    const G32 n = g_cross(g_sub(q, p), g_sub(r, p));
+    const float sp = g_dot(g_neg(p), n), sd = g_dot(g_sub(s, p), n);
+    return (sp > 0.f && sd < 0.f) || (sp < 0.f && sd > 0.f);
 }
 
-// reduce the simplex; returns 0 continue, 1 overlap (as the contract), -1 uncertain
-__device__ __forceinline__ int gjk_reduce32(Fe3 sp[4], int& n, Fe3& v)
+// 0 continue, 1 origin inside the tetrahedron, 2 degenerate
+__device__ __forceinline__ int g_reduce(SPt sp[4], int& n, G32& v)
 {
     int mask = 0;
     if (n == 2) {
-        mask = closest_seg32(sp[0], sp[1], v);
-        if (mask < 0) return -1;
+        mask = g_closest_seg(sp[0].p, sp[1].p, v);
     } else if (n == 3) {
-        mask = closest_tri32(sp[0], sp[1], sp[2], v);
-        if (mask < 0) return -1;
-        if (mask == 0) return 1;
+        mask = g_closest_tri(sp[0].p, sp[1].p, sp[2].p, v);
+        if (mask == 0) return 2;
     } else {
         bool found = false;
-        Fe best = { 0.f, 0.f };
+        float best = 0.f;
 #pragma unroll 1
         for (int f = 0; f < 4; ++f) {
-            const int i0 = (f == 3) ? 1 : 0;
-            const int i1 = (f <= 1) ? 1 : 2;
-            const int i2 = (f == 0) ? 2 : 3;
-            const int i3 = 3 - f;
-            const int o = origin_outside32(sp[i0], sp[i1], sp[i2], sp[i3]);
-            if (o < 0) return -1;
-            if (!o) continue;
-            Fe3 pt;
-            const int m = closest_tri32(sp[i0], sp[i1], sp[i2], pt);
-            if (m < 0) return -1;
-            if (m == 0) return 1;
-            const Fe dd = fe3_dot(pt, pt);
-            bool take;
-            if (!found) {
-                take = true;
-            } else {
-                const Fe diff = fe_sub(dd, best);
-                if (!fe_sure(diff)) return -1;
-                take = diff.v < 0.f;
-            }
-            if (take) {
+            const int i0 = (f == 3) ? 1 : 0, i1 = (f <= 1) ? 1 : 2, i2 = (f == 0) ? 2 : 3, i3 = 3 - f;
+            if (!g_outside(sp[i0].p, sp[i1].p, sp[i2].p, sp[i3].p)) continue;
+            G32 pt;
+            const int m = g_closest_tri(sp[i0].p, sp[i1].p, sp[i2].p, pt);
+            if (m == 0) return 2;
+            const float dd = g_dot(pt, pt);
+            if (!found || dd < best) {
                 found = true;
                 best = dd;
                 v = pt;
@@ -323,57 +243,122 @@ __device__ __forceinline__ int gjk_reduce32(Fe3 sp[4], int& n, Fe3& v)
     return 0;
 }
 
-// FP32 certified GJK of A (orientation qA, errors eqA) and B at Delta (error
-// eD per component) with orientation qB (error eqB): GJK32_SEPARATED /
-// GJK32_OVERLAP when certified equal to the FP64 contract, else
-// GJK32_UNCERTAIN.  *iters as the contract (kGjkMaxIt + 1 at the cap).
+// ------------------------------------------------------------ certificates
+// Separation: along direction nrm, every vertex of B (in A's frame) lies above
+// every vertex of A by more than tau |nrm| once all FP32 errors are added.
 template <int NV>
-__device__ __noinline__ int gjk32c(const Shape3& sh, float dx, float dy, float dz, float eD, const float qA[4],
-                                   float eqA, const float qB[4], float eqB, int* iters)
+__device__ __forceinline__ bool cert_separated(int nv, const G32* pb, const G32* va, G32 nrm, float e_pb,
+                                               float e_va, float tau)
+{
+    float minB = g_dot(pb[0], nrm), maxA = g_dot(va[0], nrm);
+    float P = 0.f, V = 0.f;
+#pragma unroll
+    for (int i = 0; i < (NV ? NV : kMaxV3); ++i) {
+        if (!NV && i >= nv) break;
+        minB = fminf(minB, g_dot(pb[i], nrm));
+        maxA = fmaxf(maxA, g_dot(va[i], nrm));
+        P = fmaxf(P, fmaxf(fabsf(pb[i].x), fmaxf(fabsf(pb[i].y), fabsf(pb[i].z))));
+        V = fmaxf(V, fmaxf(fabsf(va[i].x), fmaxf(fabsf(va[i].y), fabsf(va[i].z))));
+    }
+    const float n1 = __fadd_ru(__fadd_ru(fabsf(nrm.x), fabsf(nrm.y)), fabsf(nrm.z));
+    const float gap = minB - maxA;
+    // |dot32 - dot_exact| <= |n|_1 (e_vertex + 4 u P); the gap's own rounding
+    const float eg = __fmul_ru(n1, __fadd_ru(__fadd_ru(e_pb, e_va), __fmul_ru(4.0f * kUr, __fadd_ru(P, V))));
+    const float bound = __fadd_ru(__fadd_ru(eg, __fmul_ru(2.0f * kUr, fabsf(gap))), __fmul_ru(tau, n1));
+    return gap > fin(bound);
+}
+
+// Overlap: the origin lies strictly inside the tetrahedron of the four exact
+// vertex differences, farther than tau from each face plane.
+__device__ __forceinline__ bool cert_inside(const G32* pb, const G32* va, const SPt sp[4], float e_pb, float e_va,
+                                            float tau)
+{
+    Fe3 W[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const G32 b = pb[sp[k].ib], a = va[sp[k].ia];
+        W[k] = fe3_sub(Fe3{ { b.x, e_pb }, { b.y, e_pb }, { b.z, e_pb } },
+                       Fe3{ { a.x, e_va }, { a.y, e_va }, { a.z, e_va } });
+    }
+#pragma unroll 1
+    for (int f = 0; f < 4; ++f) {
+        const int i0 = (f == 3) ? 1 : 0, i1 = (f <= 1) ? 1 : 2, i2 = (f == 0) ? 2 : 3, i3 = 3 - f;
+        const Fe3 nn = fe3_cross(fe3_sub(W[i1], W[i0]), fe3_sub(W[i2], W[i0]));
+        const Fe so = fe3_dot(fe3_neg(W[i0]), nn);
+        const Fe sd = fe3_dot(fe3_sub(W[i3], W[i0]), nn);
+        if (!fe_sure(so) || !fe_sure(sd)) return false;
+        if ((so.v > 0.f) != (sd.v > 0.f)) return false;        // origin outside this face
+        // distance to the plane: (|so| - e_so) / |n|_2 > tau, |n|_2 <= |n|_1 + 3 e_n
+        const float n1 = __fadd_ru(__fadd_ru(__fadd_ru(fabsf(nn.x.v), nn.x.e), __fadd_ru(fabsf(nn.y.v), nn.y.e)),
+                                   __fadd_ru(fabsf(nn.z.v), nn.z.e));
+        if (!(__fsub_rd(fabsf(so.v), so.e) > __fmul_ru(tau, n1))) return false;
+    }
+    return true;
+}
+
+// FP32 GJK + certificate for A (orientation qA) and B at Delta (orientation
+// qB), in A's frame: GJK32_SEPARATED / GJK32_OVERLAP when certified about the
+// exact shapes with margin tau (where the FP64 contract decides the same),
+// GJK32_UNCERTAIN otherwise.
+template <int NV>
+__device__ __noinline__ int gjk32_cert(const Shape3& sh, float dx, float dy, float dz, const float qA[4],
+                                       const float qB[4], float e_pb, float e_va, float tau)
 {
     const int nv = NV ? NV : sh.nv;
-    const Fe qAc[4] = { { qA[0], eqA }, { -qA[1], eqA }, { -qA[2], eqA }, { -qA[3], eqA } };
-    const Fe qBe[4] = { { qB[0], eqB }, { qB[1], eqB }, { qB[2], eqB }, { qB[3], eqB } };
-    Fe qr[4];
-    fe_qmul(qAc, qBe, qr);
-    const Fe3 D = { { dx, eD }, { dy, eD }, { dz, eD } };
-    const Fe3 l = fe_qrot(qAc, D);
-    Fe3 pb[NV ? NV : kMaxV3], va[NV ? NV : kMaxV3];
+    // qr = conj(qA) qB, l = rot(conj(qA), Delta), pb = rot(qr, v) + l
+    const float a0 = qA[0], a1 = -qA[1], a2 = -qA[2], a3 = -qA[3];
+    const float r0 = ((a0 * qB[0] - a1 * qB[1]) - a2 * qB[2]) - a3 * qB[3];
+    const float r1 = ((a0 * qB[1] + a1 * qB[0]) + a2 * qB[3]) - a3 * qB[2];
+    const float r2 = ((a0 * qB[2] - a1 * qB[3]) + a2 * qB[0]) + a3 * qB[1];
+    const float r3 = ((a0 * qB[3] + a1 * qB[2]) - a2 * qB[1]) + a3 * qB[0];
+    auto rot = [](float w, float x, float y, float z, G32 v) {
+        const float tx = 2.0f * (y * v.z - z * v.y);
+        const float ty = 2.0f * (z * v.x - x * v.z);
+        const float tz = 2.0f * (x * v.y - y * v.x);
+        return G32{ (v.x + w * tx) + (y * tz - z * ty), (v.y + w * ty) + (z * tx - x * tz),
+                    (v.z + w * tz) + (x * ty - y * tx) };
+    };
+    const G32 l = rot(a0, a1, a2, a3, G32{ dx, dy, dz });
+    G32 pb[NV ? NV : kMaxV3], va[NV ? NV : kMaxV3];
 #pragma unroll
-    for (int i = 0; i < nv; ++i) {
-        // fv = fl32(v): |fv - v| <= u32 |fv| (inflated)
-        const Fe3 v = { { sh.fv[i][0], fin(ru_mul(fabsf(sh.fv[i][0]), kUr)) },
-                        { sh.fv[i][1], fin(ru_mul(fabsf(sh.fv[i][1]), kUr)) },
-                        { sh.fv[i][2], fin(ru_mul(fabsf(sh.fv[i][2]), kUr)) } };
-        va[i] = v;
-        const Fe3 r = fe_qrot(qr, v);
-        pb[i] = { fe_add(r.x, l.x), fe_add(r.y, l.y), fe_add(r.z, l.z) };
+    for (int i = 0; i < (NV ? NV : kMaxV3); ++i) {
+        if (!NV && i >= nv) break;
+        va[i] = G32{ sh.fv[i][0], sh.fv[i][1], sh.fv[i][2] };
+        const G32 rr = rot(r0, r1, r2, r3, va[i]);
+        pb[i] = G32{ rr.x + l.x, rr.y + l.y, rr.z + l.z };
     }
-    // d = -l, or (-1, 0, 0) when l is exactly zero in the FP64 run
-    Fe3 d = fe3_neg(l);
-    if (!fe_sure(l.x) && !fe_sure(l.y) && !fe_sure(l.z)) return GJK32_UNCERTAIN;
-    Fe3 sp[4], v;
+    G32 d = g_neg(l);
+    if (d.x == 0.f && d.y == 0.f && d.z == 0.f) d.x = -1.0f;
+    SPt sp[4];
     int n = 1;
-    if (!support32<NV>(sh, pb, va, d, sp[0])) return GJK32_UNCERTAIN;
-    v = sp[0];
+    sp[0] = g_support<NV>(nv, pb, va, d);
+    G32 v = sp[0].p;
+    bool tried = false;   // a separating direction failed its certificate
 #pragma unroll 1
     for (int it = 0; it < kGjkMaxIt; ++it) {
-        *iters = it + 1;
-        const Fe vv = fe3_dot(v, v);
-        if (!fe_pos(vv)) return GJK32_UNCERTAIN;     // FP64 vv could be 0
-        Fe3 w;
-        if (!support32<NV>(sh, pb, va, fe3_neg(v), w)) return GJK32_UNCERTAIN;
-        const Fe vw = fe3_dot(v, w);
-        if (!fe_sure(vw)) return GJK32_UNCERTAIN;
-        if (vw.v > 0.f) return GJK32_SEPARATED;
+        const float vv = g_dot(v, v);
+        if (vv == 0.f) return GJK32_UNC_DEGENERATE;
+        const SPt w = g_support<NV>(nv, pb, va, g_neg(v));
+        const float vw = g_dot(v, w.p);
+        if (vw > 0.f) {
+            // v separates in FP32.  Certify it; if the gap is within the
+            // bound, keep iterating towards the closest point (the largest
+            // gap any direction can show) until the distance estimate stalls.
+            if (cert_separated<NV>(nv, pb, va, v, e_pb, e_va, tau)) return GJK32_SEPARATED;
+            if (tried && __fsub_rn(vv, vw) <= __fmul_rn(1e-6f, vv)) return GJK32_UNCERTAIN;
+            tried = true;
+        }
+        bool dup = false;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) dup |= (k < n) && sp[k].ib == w.ib && sp[k].ia == w.ia;
+        if (dup) return vw > 0.f ? GJK32_UNCERTAIN : GJK32_UNC_DEGENERATE;
         sp[n] = w;
         n += 1;
-        const int rr = gjk_reduce32(sp, n, v);
-        if (rr < 0) return GJK32_UNCERTAIN;
-        if (rr == 1) return GJK32_OVERLAP;
+        const int rr = g_reduce(sp, n, v);
+        if (rr == 1) return cert_inside(pb, va, sp, e_pb, e_va, tau) ? GJK32_OVERLAP : GJK32_UNC_INSIDE;
+        if (rr == 2) return GJK32_UNC_DEGENERATE;
     }
-    *iters = kGjkMaxIt + 1;
-    return GJK32_OVERLAP;
+    return GJK32_UNC_CAP;
 }
 
 }  // namespace hpmc

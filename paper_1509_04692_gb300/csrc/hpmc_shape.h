@@ -1,0 +1,87 @@
+// hpmc_shape.h -- shape constants of the overlap tests (host only).
+#pragma once
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+
+#include "../../include/hpmc.h"
+#include "hpmc_types.h"
+
+namespace hpmc {
+
+// Shape constants of the overlap tests from the local-frame vertices:
+// circumradius R, cull threshold (2R)^2, polygon edge normals and A's own
+// projection intervals (2D), FP32 copies.  Validates the vertex list
+// (2D: convex, counter-clockwise).  Host only.
+inline int build_shapes(int dim, const double* verts, uint32_t nv, Shape2& s2, Shape3& s3, double& Rc,
+                        double& rc2)
+{
+    if (dim != 2 && dim != 3) return HPMC_ERR_INVALID_ARG;
+    if (dim == 2 && (nv < 3 || nv > (uint32_t)kMaxV2)) return HPMC_ERR_INVALID_ARG;
+    if (dim == 3 && (nv < 4 || nv > (uint32_t)kMaxV3)) return HPMC_ERR_INVALID_ARG;
+    if (!verts) return HPMC_ERR_INVALID_ARG;
+    for (uint32_t i = 0; i < nv * (uint32_t)dim; ++i)
+        if (!std::isfinite(verts[i])) return HPMC_ERR_INVALID_ARG;
+    double r2 = 0.0;
+    for (uint32_t i = 0; i < nv; ++i) {
+        const double* v = verts + (size_t)i * dim;
+        double q = v[0] * v[0] + v[1] * v[1];
+        if (dim == 3) q = q + v[2] * v[2];
+        if (q > r2) r2 = q;
+    }
+    Rc = std::sqrt(r2);
+    if (!(Rc > 0.0)) return HPMC_ERR_INVALID_ARG;
+    const double dcut = Rc + Rc;
+    rc2 = dcut * dcut;
+    if (dim == 2) {
+        // convex and counter-clockwise: strictly left turns everywhere
+        for (uint32_t i = 0; i < nv; ++i) {
+            const double* p0 = verts + 2 * i;
+            const double* p1 = verts + 2 * ((i + 1) % nv);
+            const double* p2 = verts + 2 * ((i + 2) % nv);
+            const double cr = (p1[0] - p0[0]) * (p2[1] - p1[1]) - (p1[1] - p0[1]) * (p2[0] - p1[0]);
+            if (!(cr > 0.0)) return HPMC_ERR_INVALID_ARG;
+        }
+        Shape2& s = s2;
+        s = Shape2{};
+        s.nv = (int)nv;
+        for (uint32_t k = 0; k < nv; ++k) {
+            s.vx[k] = verts[2 * k];
+            s.vy[k] = verts[2 * k + 1];
+        }
+        for (uint32_t k = 0; k < nv; ++k) {
+            const uint32_t k1 = (k + 1) % nv;
+            s.nx[k] = s.vy[k1] - s.vy[k];
+            s.ny[k] = s.vx[k] - s.vx[k1];
+            double lo = 0.0, hi = 0.0;
+            for (uint32_t i = 0; i < nv; ++i) {
+                const double t = s.nx[k] * s.vx[i] + s.ny[k] * s.vy[i];
+                if (i == 0 || t < lo) lo = t;
+                if (i == 0 || t > hi) hi = t;
+            }
+            s.alo[k] = lo;
+            s.ahi[k] = hi;
+        }
+        for (uint32_t k = 0; k < nv; ++k) {
+            s.fvx[k] = (float)s.vx[k]; s.fvy[k] = (float)s.vy[k];
+            s.fnx[k] = (float)s.nx[k]; s.fny[k] = (float)s.ny[k];
+            s.falo[k] = (float)s.alo[k]; s.fahi[k] = (float)s.ahi[k];
+        }
+        s.rc2 = rc2;
+        s.frc2 = (float)rc2;
+    } else {
+        Shape3& s = s3;
+        s = Shape3{};
+        s.nv = (int)nv;
+        for (uint32_t k = 0; k < nv; ++k)
+            for (int a = 0; a < 3; ++a) {
+                s.v[k][a] = verts[3 * k + a];
+                s.fv[k][a] = (float)verts[3 * k + a];
+            }
+        s.rc2 = rc2;
+        s.frc2 = (float)rc2;
+    }
+    return 0;
+}
+
+}  // namespace hpmc

@@ -219,21 +219,17 @@ k_set3d(Dev dv, Shape3 sh, int nxt, int sigma, const uint32_t* __restrict__ item
                     for (int q = 0; q < 12; ++q) ws.rw[grp][q] = w16[q + 1];
                     ws.eA[grp] = (uint16_t)eA;
                     if (F32) {
-                        const float4 fa = ws.ea[eA], fb = ws.eb[eA];
+                        const float4 fa = ws.ea[eA];
                         const float rx = __fadd_rn(fa.x, __fmul_rn(rp.d32, m24(w16[1])));
                         const float ry = __fadd_rn(fa.y, __fmul_rn(rp.d32, m24(w16[3])));
                         const float rz = __fadd_rn(fa.z, __fmul_rn(rp.d32, m24(w16[5])));
-                        const float v0 = __fmul_rn(rp.tau32, m24(w16[7]));
-                        const float v1 = __fmul_rn(rp.tau32, m24(w16[9]));
-                        const float v2 = __fmul_rn(rp.tau32, m24(w16[11]));
-                        const float vv = __fmaf_rn(v0, v0, __fmaf_rn(v1, v1, __fmul_rn(v2, v2)));
-                        const float inv = __frcp_rn(__fsqrt_rn(__fadd_rn(1.0f, vv)));
-                        const float d0 = inv, d1 = __fmul_rn(v0, inv), d2 = __fmul_rn(v1, inv), d3 = __fmul_rn(v2, inv);
-                        const float a0 = fa.w, a1 = fb.x, a2 = fb.y, a3 = fb.z;
-                        const float q0 = a0 * d0 - a1 * d1 - a2 * d2 - a3 * d3;
-                        const float q1 = a0 * d1 + a1 * d0 + a2 * d3 - a3 * d2;
-                        const float q2 = a0 * d2 - a1 * d3 + a2 * d0 + a3 * d1;
-                        const float q3 = a0 * d3 + a1 * d2 - a2 * d1 + a3 * d0;
+                        // the trial orientation is the contract's FP64 one, cast:
+                        // its FP32 copy then differs by one rounding only
+                        const uint32_t gA = ws.gidx[eA];
+                        const double qp[4] = { B.q0[gA], B.q1[gA], B.q2[gA], B.q3[gA] };
+                        double qt[4];
+                        propose3d_orient(rp, qp, w16, qt);
+                        const float q0 = (float)qt[0], q1 = (float)qt[1], q2 = (float)qt[2], q3 = (float)qt[3];
                         ws.tra[grp] = make_float4(rx, ry, rz, q0);
                         ws.trb[grp] = make_float4(q1, q2, q3, 0.f);
                         const bool out = rx < rp.out_lo || ry < rp.out_lo || rz < rp.out_lo || rx > rp.out_hi[0] ||
@@ -345,9 +341,9 @@ k_set3d(Dev dv, Shape3 sh, int nxt, int sigma, const uint32_t* __restrict__ item
                                     const float4 b1 = ws.ea[e2], b2 = ws.eb[e2];
                                     const float qa[4] = { a1.w, a2.x, a2.y, a2.z };
                                     const float qb[4] = { b1.w, b2.x, b2.y, b2.z };
-                                    const int v = gjk32c<NV>(sh, d2.x, d2.y, d2.z, rp.e_dlt32, qa, rp.e_ori32, qb,
-                                                             0x1.0002p-24f, &its);
-                                    if (v == GJK32_UNCERTAIN) {
+                                    const int v = gjk32_cert<NV>(sh, d2.x, d2.y, d2.z, qa, qb, rp.e_pb32,
+                                                                 rp.e_va32, rp.tau3);
+                                    if (v >= GJK32_UNCERTAIN) {
                                         c_rechk += 1;
                                         const Trial3 t3 = trial3_of(rp, B, ws.gidx[ws.eA[g2]], ws.rw[g2]);
                                         const uint32_t gB = ws.gidx[e2];

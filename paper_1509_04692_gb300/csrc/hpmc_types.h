@@ -64,6 +64,9 @@ struct Rep {
     float sat_e;             // separating-axis / support gap margin
     float e_dlt32;           // |Delta32 - Delta64| per component (3D GJK input bound)
     float e_ori32;           // |q'32 - q'64| per component of the FP32 trial orientation
+    float e_pb32;            // 3D: |pb32 - pb| per component of B's vertices in A's frame
+    float e_va32;            // 3D: |fl32(v) - v| per component of A's local vertices
+    float tau3;              // 3D: certificate band (GJK64 = exact predicate outside it)
     double e_in, e_cull, e_sat;  // the same margins in FP64 (reporting)
 };
 

@@ -31,7 +31,7 @@ EXPORTS = [
     "hpmc_reset_counters", "hpmc_check_overlaps", "hpmc_get_state", "hpmc_set_state",
     "hpmc_run_host", "hpmc_autotune", "hpmc_geometry", "hpmc_launches_per_sweep",
     "hpmc_filter_margins", "hpmc_strerror", "hpmc_profile_sweeps", "hpmc_count_overlaps_noalloc",
-    "hpmc_trace_read",
+    "hpmc_trace_read", "hpmc_pair_test",
 ]
 
 
@@ -90,6 +90,8 @@ def _load():
         "hpmc_filter_margins": [vp, i32, dp, dp, dp],
         "hpmc_profile_sweeps": [vp, u32, vp, dp, dp],
         "hpmc_trace_read": [vp, ctypes.POINTER(u64), u32, ctypes.POINTER(u32)],
+        "hpmc_pair_test": [ctypes.c_int, dp, u32, u32, dp, dp, dp, ctypes.POINTER(ctypes.c_int32),
+                           ctypes.POINTER(ctypes.c_int32)],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -266,6 +268,24 @@ class Batch:
         _ck(_lib.hpmc_filter_margins(self.h, int(r), ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)),
             "hpmc_filter_margins")
         return dict(e_in=a.value, e_cull=b.value, e_overlap=c.value)
+
+
+def pair_test(dim, verts, D, qA, qB):
+    """FP64-contract and FP32-filter verdicts on independent pairs (GPU).
+
+    Returns (out64, out32): 1 overlap, 0 separated, 2 (FP32 only) uncertain."""
+    v = _c64(verts).reshape(-1, dim)
+    D = _c64(D).reshape(-1, dim)
+    qd = 2 if dim == 2 else 4
+    qA = _c64(qA).reshape(-1, qd)
+    qB = _c64(qB).reshape(-1, qd)
+    n = D.shape[0]
+    o64 = np.zeros(n, dtype=np.int32)
+    o32 = np.zeros(n, dtype=np.int32)
+    ip = ctypes.POINTER(ctypes.c_int32)
+    _ck(_lib.hpmc_pair_test(int(dim), _dp(v), v.shape[0], n, _dp(D), _dp(qA), _dp(qB),
+                            o64.ctypes.data_as(ip), o32.ctypes.data_as(ip)), "hpmc_pair_test")
+    return o64, o32
 
 
 def from_system(sysm, w_min=None):

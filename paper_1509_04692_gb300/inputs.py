@@ -87,11 +87,8 @@ def triangular_lattice(N: int, L: float, rng: np.random.Generator, aligned: bool
     Returns (pos[N,2], orient[N,2], nearest_site_distance)."""
     dmin, nx, ny = _tri_lattice_dims(N, L)
     ax, ay = L / nx, L / ny
-    sites = []
-    for j in range(ny):
-        for i in range(nx):
-            sites.append(((i + 0.5 * (j % 2)) * ax, j * ay))
-    sites = np.array(sites, dtype=np.float64)
+    j, i = np.divmod(np.arange(nx * ny, dtype=np.int64), nx)
+    sites = np.stack([(i + 0.5 * (j % 2)) * ax, j * ay], axis=1)
     keep = np.sort(rng.permutation(sites.shape[0])[:N])
     pos = sites[keep]
     pos += rng.uniform(0.0, L, size=2)[None, :]          # random global offset

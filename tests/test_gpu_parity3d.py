@@ -52,7 +52,9 @@ def test_cubes_512_bit_exact(mode):
     ref = oracle_run(s, 40)
     got = gpu_run(s, 40, mode)
     assert_same(got, ref)
-    assert got[3]["gjk_cap"] == ref[3]
+    # (which pairs are evaluated depends on the early-exit order, so only
+    # decisions are compared; the GJK cap is never reached here anyway)
+    assert got[3]["gjk_cap"] == 0 and ref[3] == 0
     assert got[4] == 0
 
 
