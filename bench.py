@@ -7,8 +7,10 @@ start before timing.  One step = SWEEPS_PER_STEP sweeps (shift + cell-list
 rebuild + 4 checkerboard sets each), replayed from a CUDA graph.
 
 Headline `value`: FP32-filtered form (decisions identical to FP64), inputs
-resident in HBM.  `forms` reports the plain FP64 form on the same workload and
-the batched form (512 replicas of N ~ U{256..8192}, phi ~ U[0.40, 0.70]).
+resident in HBM.  `forms` reports the plain FP64 form on the same workload,
+the batched form (512 replicas of N ~ U{256..8192}, phi ~ U[0.40, 0.70]),
+32768 cubes at volume fraction 0.50 in both forms, and 2^24 pentagons at area
+fraction 0.60 on a 2048^2 cell list (FP32-filtered).
 `e2e`: the same metric through hpmc_run_host with host buffers (H2D + sweeps
 + D2H inside the timed region).  `cpu_baseline`: the C oracle on host cores.
 
@@ -146,9 +148,9 @@ def run_reference(args):
     print(json.dumps(out))
 
 
-def time_steps(b, torch, stream, steps, warmup, flush):
+def time_steps(b, torch, stream, steps, warmup, flush, sweeps=SWEEPS_PER_STEP):
     for _ in range(warmup):
-        b.sweep(SWEEPS_PER_STEP, stream=stream.cuda_stream, graph=True)
+        b.sweep(sweeps, stream=stream.cuda_stream, graph=True)
     torch.cuda.synchronize()
     c0 = b.counters()
     total_ms = 0.0
@@ -157,13 +159,31 @@ def time_steps(b, torch, stream, steps, warmup, flush):
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        b.sweep(SWEEPS_PER_STEP, stream=stream.cuda_stream, graph=True)
+        b.sweep(sweeps, stream=stream.cuda_stream, graph=True)
         e1.record(stream)
         e1.synchronize()
         total_ms += e0.elapsed_time(e1)
     c1 = b.counters()
     d = {k: c1[k] - c0[k] for k in c1}
     return total_ms, d
+
+
+def measure_form(b, torch, stream, flush, precision, melt, sweeps, steps, n_tune=4):
+    """Melt (untimed), autotune, then time `steps` graph-replayed steps of
+    `sweeps` sweeps; L2 flushed between steps."""
+    from paper_1509_04692_gb300 import hpmc
+    b.set_precision(precision)
+    if melt:
+        b.sweep(melt, stream=stream.cuda_stream, graph=True)
+    lanes, warps = b.autotune(n_tune)
+    ms, c = time_steps(b, torch, stream, steps, 1, flush, sweeps)
+    return {"value": c["moves"] / (ms * 1e-3),
+            "precision": "FP64" if precision == hpmc.HPMC_FP64 else "FP32_FILTERED",
+            "lanes_per_cell": lanes, "warps_per_block": warps, "ms_per_step": ms / steps,
+            "sweeps_per_step": sweeps, "steps": steps, "melt_sweeps": melt,
+            "acceptance": c["accept"] / max(1, c["moves"]),
+            "overlap_checks": c["overlap_checks"], "fp64_rechecks": c["fp64_rechecks"],
+            "accept": c["accept"], "moves": c["moves"]}
 
 
 def run_ours(args):
@@ -253,28 +273,38 @@ def run_ours(args):
                                "acceptance": cnt["accept"] / max(1, moves)}}
     # ---- plain FP64 form on the same workload (same trajectory)
     b64 = hpmc.from_system(s)
-    b64.set_precision(hpmc.HPMC_FP64)
-    b64.sweep(MELT, stream=stream.cuda_stream, graph=True)
-    l64, w64 = b64.autotune(4)
-    ms64, c64 = time_steps(b64, torch, stream, max(2, args.steps // 2), 1, flush)
-    forms["fp64"] = {"value": c64["moves"] / (ms64 * 1e-3), "lanes_per_cell": l64,
-                     "warps_per_block": w64}
-    p32, o32, sw32 = b.get_state()
+    forms["fp64"] = measure_form(b64, torch, stream, flush, hpmc.HPMC_FP64, MELT, SWEEPS_PER_STEP,
+                                 max(2, args.steps // 2))
     b64.close()
 
     # ---- batched form: 512 independent replicas, one graph-captured launch sequence
     if not args.no_batched:
         reps = inputs.replica_systems(512)
         bb = hpmc.from_systems(reps)
-        bb.set_precision(hpmc.HPMC_FP32_FILTERED)
-        bb.sweep(20, stream=stream.cuda_stream, graph=True)
-        lb, wb = bb.autotune(4)
-        msb, cb = time_steps(bb, torch, stream, 2, 1, flush)
-        forms["batched_512_replicas_fp32_filtered"] = {
-            "value": cb["moves"] / (msb * 1e-3), "replicas": 512,
-            "particles": int(sum(r.N for r in reps)), "lanes_per_cell": lb, "warps_per_block": wb,
-            "ms_per_step": msb / 2, "sweeps_per_step": SWEEPS_PER_STEP}
+        f = measure_form(bb, torch, stream, flush, hpmc.HPMC_FP32_FILTERED, 20, SWEEPS_PER_STEP, 2)
+        f.update(replicas=512, particles=int(sum(r.N for r in reps)))
+        forms["batched_512_replicas_fp32_filtered"] = f
         bb.close()
+
+    # ---- 3D: 32768 cubes at volume fraction 0.5, both precision forms
+    if not args.no_cubes:
+        sc = inputs.cubes32768(42)
+        for prec, key in ((hpmc.HPMC_FP32_FILTERED, "cubes32768_fp32_filtered"),
+                          (hpmc.HPMC_FP64, "cubes32768_fp64")):
+            bc = hpmc.from_system(sc)
+            f = measure_form(bc, torch, stream, flush, prec, MELT, 100, 2)
+            f.update(workload=sc.name, N=sc.N, d=sc.d, a=sc.a, nselect=sc.nselect)
+            forms[key] = f
+            bc.close()
+
+    # ---- large 2D: 2^24 pentagons on a 2048^2 cell list (state > L2)
+    if not args.no_large:
+        sl = inputs.large2d(42)
+        bl = hpmc.from_system(sl)
+        f = measure_form(bl, torch, stream, flush, hpmc.HPMC_FP32_FILTERED, 20, 5, 2, n_tune=2)
+        f.update(workload=sl.name, N=sl.N, cells=2048 * 2048)
+        forms["large2d_2p24_fp32_filtered"] = f
+        bl.close()
 
     # ---- CPU baseline: the oracle on host cores, bounded sample
     cpu = None
@@ -314,6 +344,10 @@ def run_profile(args):
     torch.cuda.set_device(0)
     if args.profile_workload == "batched":
         b = hpmc.from_systems(inputs.replica_systems(512))
+    elif args.profile_workload == "cubes":
+        b = hpmc.from_system(inputs.cubes32768(42))
+    elif args.profile_workload == "large2d":
+        b = hpmc.from_system(inputs.large2d(42, N=args.profile_n or inputs.LARGE2D_N))
     else:
         b = hpmc.from_system(inputs.fluid4096(42))
     b.set_precision(hpmc.HPMC_FP64 if args.profile_fp64 else hpmc.HPMC_FP32_FILTERED)
@@ -365,8 +399,10 @@ def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--profile-sweeps", type=int, default=0,
                     help="run the small ncu case instead of the benchmark")
-    ap.add_argument("--profile-workload", default="fluid4096", choices=["fluid4096", "batched"])
+    ap.add_argument("--profile-workload", default="fluid4096",
+                    choices=["fluid4096", "batched", "cubes", "large2d"])
     ap.add_argument("--profile-fp64", action="store_true")
+    ap.add_argument("--profile-n", type=int, default=0, help="N of the large2d profile case")
     ap.add_argument("--lanes", type=int, default=0)
     ap.add_argument("--warps", type=int, default=4)
     ap.add_argument("--trace", action="store_true", help="with --profile-sweeps: per-warp phase stamps")
@@ -377,6 +413,8 @@ def main():
     ap.add_argument("--cpu-sweeps", type=int, default=2000)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--no-cubes", action="store_true")
+    ap.add_argument("--no-large", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

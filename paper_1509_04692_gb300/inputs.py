@@ -207,3 +207,30 @@ def replica_params(n_replicas: int = 512, gen_seed: int = 2024, n_lo: int = 256,
 def replica_systems(n_replicas: int = 512, gen_seed: int = 2024, **kw):
     return [pentagon_system(N, phi, seed, name=f"replica{r}", gen_seed=gen_seed * 100003 + r)
             for r, (N, phi, seed) in enumerate(replica_params(n_replicas, gen_seed, **kw))]
+
+
+# 32768 cubes (edge 1) at volume fraction 0.50: d = a = 0.0817 gives a 30%
+# acceptance ratio, found with tune.tune_scale (d/a fixed at 1, 100-sweep
+# pilots) after a 1000-sweep melt from the simple cubic start at d = a = 0.1.
+CUBES32768_D = 0.0817
+CUBES32768_A = 0.0817
+
+
+def cubes32768(seed: int = 42) -> System:
+    """32768 cubes, volume fraction 0.50, moves sized for ~30% acceptance."""
+    return cube_system(32768, 0.50, seed, name="cube fluid N=32768 phi=0.50",
+                       d=CUBES32768_D, a=CUBES32768_A, nselect=4)
+
+
+# The large 2D system: 2^24 pentagons at area fraction 0.60 with cells no
+# narrower than 1.99, i.e. a 2048 x 2048 cell list (about 4 shapes per cell).
+# Same shape and density as the 4096-pentagon fluid, so the same move sizes
+# give the same ~30% acceptance.
+LARGE2D_N = 1 << 24
+LARGE2D_W_MIN = 1.99
+
+
+def large2d(seed: int = 42, N: int = LARGE2D_N) -> System:
+    """2^24 regular pentagons, area fraction 0.60, 2048^2 cells of width >= 1.99."""
+    return pentagon_system(N, 0.60, seed, name=f"pentagon fluid N={N} phi=0.60 w_min=1.99",
+                           d=FLUID4096_D, a=FLUID4096_A, nselect=4, w_min=LARGE2D_W_MIN)
