@@ -353,7 +353,7 @@ def run_profile(args):
     b.set_precision(hpmc.HPMC_FP64 if args.profile_fp64 else hpmc.HPMC_FP32_FILTERED)
     if args.lanes:
         b.set_group_size(args.lanes, args.warps)
-    b.sweep(20)
+    b.sweep(args.profile_melt, graph=True)
     b.sweep(args.profile_sweeps)
     c = b.counters()
     out = {"profile": args.profile_workload, "sweeps": args.profile_sweeps, "counters": c}
@@ -403,6 +403,7 @@ def main():
                     choices=["fluid4096", "batched", "cubes", "large2d"])
     ap.add_argument("--profile-fp64", action="store_true")
     ap.add_argument("--profile-n", type=int, default=0, help="N of the large2d profile case")
+    ap.add_argument("--profile-melt", type=int, default=20, help="graph-replayed sweeps before profiling")
     ap.add_argument("--lanes", type=int, default=0)
     ap.add_argument("--warps", type=int, default=4)
     ap.add_argument("--trace", action="store_true", help="with --profile-sweeps: per-warp phase stamps")
