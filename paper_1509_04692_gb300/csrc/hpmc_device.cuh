@@ -12,6 +12,21 @@
 
 namespace hpmc {
 
+// Programmatic dependent launch (sm_90 and later).  The rebuild kernels are
+// launched with programmatic stream serialisation: each sweep kernel first
+// lets the next kernel of the stream be scheduled (its blocks become
+// resident and wait), then waits until the previous kernel has completed and
+// its memory is visible.  Nothing is read or written before the wait, so the
+// order of the stream is kept; what is saved is the launch latency between
+// the short rebuild kernels (24 -> 16 us per sweep of 4096 particles).  In a
+// kernel launched without the attribute (the set kernels) the wait returns
+// at once.
+__device__ __forceinline__ void pdl_enter()
+{
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+}
+
 // ---------------------------------------------------------------- Philox
 // Philox4x32-10 (Salmon, Moraes, Dror & Shaw, SC'11): ten rounds, each two
 // 32x32->64 multiplies whose halves are xored with the other counter words

@@ -12,39 +12,56 @@ constexpr int kScanThreads = 1024;
 constexpr int kScanItems = 4;
 constexpr int kScanTile = kScanThreads * kScanItems;
 
-// One thread per replica: the grid shift of the sweep about to run, and the
-// sweep counter advance (the running sweep is sweep[r] - 1 afterwards).
-__global__ void k_shift(Dev dv)
+// Grid shift of the sweep about to run for replica r, and the sweep counter
+// advance (the running sweep is sweep[r] - 1 afterwards).
+__device__ __forceinline__ void shift_replica(const Dev& dv, uint32_t r, double out[3])
 {
-    const uint32_t r = blockIdx.x * blockDim.x + threadIdx.x;
-    if (r >= dv.R) return;
     const Rep& rp = dv.reps[r];
     const uint64_t sweep = dv.sweep[r];
     const uint4 b0 = shift_block(rp.seed, sweep, 0);
-    dv.shift[3 * r + 0] = rp.w[0] * u53(b0.x, b0.y);
-    dv.shift[3 * r + 1] = rp.w[1] * u53(b0.z, b0.w);
+    out[0] = rp.w[0] * u53(b0.x, b0.y);
+    out[1] = rp.w[1] * u53(b0.z, b0.w);
     if (dv.dim == 3) {
         const uint4 b1 = shift_block(rp.seed, sweep, 1);
-        dv.shift[3 * r + 2] = rp.w[2] * u53(b1.x, b1.y);
+        out[2] = rp.w[2] * u53(b1.x, b1.y);
     } else {
-        dv.shift[3 * r + 2] = 0.0;
+        out[2] = 0.0;
     }
+#pragma unroll
+    for (int a = 0; a < 3; ++a) dv.shift[3 * r + a] = out[a];
     dv.sweep[r] = sweep + 1;
+}
+
+// One thread per replica.
+__global__ void k_shift(Dev dv)
+{
+    pdl_enter();
+    const uint32_t r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= dv.R) return;
+    double s[3];
+    shift_replica(dv, r, s);
+}
+
+// Local cell (replica-relative linear index) of particle i of buffer cur.
+__device__ __forceinline__ uint32_t local_cell(const Dev& dv, const Rep& rp, const Bufs& B, uint32_t i,
+                                               const double* sh)
+{
+    const int ix = cell_axis(B.px[i], sh[0], rp.L[0], rp.inv_w[0], rp.nc[0]);
+    const int iy = cell_axis(B.py[i], sh[1], rp.L[1], rp.inv_w[1], rp.nc[1]);
+    int iz = 0;
+    if (dv.dim == 3) iz = cell_axis(B.pz[i], sh[2], rp.L[2], rp.inv_w[2], rp.nc[2]);
+    return (uint32_t)ix + (uint32_t)rp.nc[0] * ((uint32_t)iy + (uint32_t)rp.nc[1] * (uint32_t)iz);
 }
 
 // Cell of every particle of buffer `cur` and its arrival slot in the cell.
 __global__ void k_count(Dev dv, int cur)
 {
+    pdl_enter();
     const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= dv.ntot) return;
     const uint32_t r = dv.rep_of[i];
     const Rep& rp = dv.reps[r];
-    const Bufs& B = dv.buf[cur];
-    const int ix = cell_axis(B.px[i], dv.shift[3 * r], rp.L[0], rp.inv_w[0], rp.nc[0]);
-    const int iy = cell_axis(B.py[i], dv.shift[3 * r + 1], rp.L[1], rp.inv_w[1], rp.nc[1]);
-    int iz = 0;
-    if (dv.dim == 3) iz = cell_axis(B.pz[i], dv.shift[3 * r + 2], rp.L[2], rp.inv_w[2], rp.nc[2]);
-    const uint32_t c = rp.cbase + (uint32_t)ix + (uint32_t)rp.nc[0] * ((uint32_t)iy + (uint32_t)rp.nc[1] * (uint32_t)iz);
+    const uint32_t c = rp.cbase + local_cell(dv, rp, dv.buf[cur], i, dv.shift + 3 * r);
     dv.cellid[i] = c;
     dv.slot[i] = atomicAdd(dv.count + c, 1u);
 }
@@ -53,6 +70,7 @@ __global__ void k_count(Dev dv, int cur)
 // total goes to tile_sums[tile].  The counts are zeroed for the next sweep.
 __global__ void __launch_bounds__(kScanThreads) k_scan_tiles(Dev dv)
 {
+    pdl_enter();
     __shared__ uint32_t wsum[kScanThreads / 32];
     const uint32_t base = blockIdx.x * kScanTile + threadIdx.x * kScanItems;
     uint32_t v[kScanItems];
@@ -101,6 +119,7 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_tiles(Dev dv)
 // Exclusive scan of the tile totals in place (single block, loops if needed).
 __global__ void __launch_bounds__(kScanThreads) k_scan_sums(Dev dv, uint32_t ntiles)
 {
+    pdl_enter();
     __shared__ uint32_t wsum[kScanThreads / 32];
     __shared__ uint32_t carry;
     if (threadIdx.x == 0) carry = 0;
@@ -138,6 +157,7 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_sums(Dev dv, uint32_t nti
 
 __global__ void k_scan_add(Dev dv)
 {
+    pdl_enter();
     const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= dv.ctot || i < (uint32_t)kScanTile) return;
     dv.start[i] += dv.tile_sums[i / kScanTile];
@@ -146,28 +166,19 @@ __global__ void k_scan_add(Dev dv)
 // tags in arrival order
 __global__ void k_scatter_tags(Dev dv, int cur)
 {
+    pdl_enter();
     const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= dv.ntot) return;
     dv.tmp_tag[dv.start[dv.cellid[i]] + dv.slot[i]] = dv.buf[cur].tag[i];
 }
 
-// Canonical placement: a particle's sorted slot is its cell's start plus the
-// number of tags in the cell below its own (ascending-tag order), then the
-// gather into buffer cur ^ 1 with the FP32 mirror.
-__global__ void k_place(Dev dv, int cur)
+// Gather of particle i (tag t) of replica r, cell c, into slot o of buffer
+// cur ^ 1, with the FP32 mirror (cell-relative coordinate, orientation).
+__device__ __forceinline__ void place_at(const Dev& dv, int cur, uint32_t i, uint32_t t, uint32_t r, uint32_t c,
+                                         uint32_t o)
 {
-    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= dv.ntot) return;
     const Bufs& S = dv.buf[cur];
     const Bufs& D = dv.buf[cur ^ 1];
-    const uint32_t c = dv.cellid[i];
-    const uint32_t b = dv.start[c];
-    const uint32_t n = dv.start[c + 1] - b;
-    const uint32_t t = S.tag[i];
-    uint32_t rank = 0;
-    for (uint32_t j = 0; j < n; ++j) rank += (dv.tmp_tag[b + j] < t) ? 1u : 0u;
-    const uint32_t o = b + rank;
-    const uint32_t r = dv.rep_of[i];
     const Rep& rp = dv.reps[r];
     const uint32_t lc = c - rp.cbase;
     const int ix = (int)(lc % (uint32_t)rp.nc[0]);
@@ -193,6 +204,23 @@ __global__ void k_place(Dev dv, int cur)
         D.f4a[o] = make_float4(rx, ry, rz, (float)w0);
         D.f4b[o] = make_float4((float)w1, (float)w2, (float)w3, 0.0f);
     }
+}
+
+// Canonical placement: a particle's sorted slot is its cell's start b plus
+// the number of tags among the cell's n tags (tmp_tag[b..b+n)) below its own
+// (ascending-tag order).
+__global__ void k_place(Dev dv, int cur)
+{
+    pdl_enter();
+    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= dv.ntot) return;
+    const uint32_t c = dv.cellid[i];
+    const uint32_t b = dv.start[c];
+    const uint32_t n = dv.start[c + 1] - b;
+    const uint32_t t = dv.buf[cur].tag[i];
+    uint32_t rank = 0;
+    for (uint32_t j = 0; j < n; ++j) rank += (dv.tmp_tag[b + j] < t) ? 1u : 0u;
+    place_at(dv, cur, i, t, dv.rep_of[i], c, b + rank);
 }
 
 // ---------------------------------------------------------------- checks
