@@ -402,9 +402,11 @@ k_set2d(Dev dv, Shape2 sh, int nxt, int sigma, const uint32_t* __restrict__ item
                         for (int q = 0; q < 6; ++q) ws.rw[grp][q] = wr[q];
                         ws.eA[grp] = (uint16_t)eA;
                         if (F32) {
-                            // prefetch A's FP64 state for the update (used after the tests)
                             const uint32_t gA = ws.gidx[eA];
-                            ax64 = B.px[gA]; ay64 = B.py[gA]; ac64 = B.q0[gA]; as64 = B.q1[gA];
+                            if (!LAT) {
+                                // prefetch A's FP64 state for the update (used after the tests)
+                                ax64 = B.px[gA]; ay64 = B.py[gA]; ac64 = B.q0[gA]; as64 = B.q1[gA];
+                            }
                             const float4 f = ws.ent[eA];
                             const float rx = __fadd_rn(f.x, fdx), ry = __fadd_rn(f.y, fdy);
                             const float cz = __fmaf_rn(f.z, fcd, -__fmul_rn(f.w, fsd));
@@ -420,8 +422,8 @@ k_set2d(Dev dv, Shape2 sh, int nxt, int sigma, const uint32_t* __restrict__ item
                                 status = 1;
                             } else {
                                 c_rechk += 1;
-                                const Trial2 t2 = propose2d(rp, ax64, ay64, ac64, as64, wr[0], wr[1], wr[2],
-                                                            wr[3], wr[4], wr[5]);
+                                const Trial2 t2 = propose2d(rp, B.px[gA], B.py[gA], B.q0[gA], B.q1[gA], wr[0],
+                                                            wr[1], wr[2], wr[3], wr[4], wr[5]);
                                 const bool ok = cell_axis(t2.x, shx, rp.L[0], rp.inv_w[0], nc0) == ix &&
                                                 cell_axis(t2.y, shy, rp.L[1], rp.inv_w[1], nc1) == iy;
                                 status = ok ? 1 : 2;
@@ -443,6 +445,15 @@ k_set2d(Dev dv, Shape2 sh, int nxt, int sigma, const uint32_t* __restrict__ item
                     HPMC_STAMP(dv, wid, first, lane, 6 + 3 * (int)k);
                     __syncwarp();
                     const int myA = (status == 1) ? (int)ws.eA[grp] : -1;
+                    // latency regime: lanes 0 and 1 of the cell prefetch the FP64
+                    // state the lane-split update needs (own coordinate, c, s)
+                    double pf_p = 0.0, pf_c = 0.0, pf_s = 0.0;
+                    if (F32 && LAT && status == 1 && sl < 2) {
+                        const uint32_t gA = ws.gidx[myA];
+                        pf_p = sl ? B.py[gA] : B.px[gA];
+                        pf_c = B.q0[gA];
+                        pf_s = B.q1[gA];
+                    }
                     float4 trA = make_float4(0.f, 0.f, 0.f, 0.f);
                     double2 tpA = make_double2(0.0, 0.0);
                     if (status == 1) {
@@ -741,7 +752,47 @@ k_set2d(Dev dv, Shape2 sh, int nxt, int sigma, const uint32_t* __restrict__ item
 
                     HPMC_STAMP(dv, wid, first, lane, 7 + 3 * (int)k);
                     // ---- accept or reject (one lane per cell)
-                    if (sl == 0 && status != 0) {
+                    if constexpr (F32 && LAT) {
+                        // contract update split over lanes 0 (x', c') and 1 (y',
+                        // s') of the cell: each FP64 instruction then serves both
+                        // components (identical operations; s1 = c sd - (-s) cd
+                        // rounds as c sd + s cd)
+                        const bool acc = status == 1 && !((ws.ovmask >> grp) & 1u);
+                        if (sl == 0 && status != 0) {
+                            if (status == 2) c_rbd += 1;
+                            else if (acc) c_acc += 1;
+                            else c_rov += 1;
+                        }
+                        const bool upd = acc && sl < 2;
+                        const unsigned um = __ballot_sync(FULL, upd);
+                        if (upd) {
+                            const int eA = ws.eA[grp];
+                            const uint32_t gA = ws.gidx[eA];
+                            const MoveData& m = ws.mv[jc][k - k0];
+                            const double pn = wrap_pos_bits(pf_p + (sl ? m.dy : m.dx), rp.L[sl]);
+                            const double v = sl ? m.sd : m.cd, z = sl ? m.cd : m.sd;
+                            const double wv = sl ? -pf_s : pf_s;
+                            const double q1 = pf_c * v - wv * z;
+                            const double sq = q1 * q1;
+                            const double n2 = sq + __shfl_xor_sync(um, sq, 1);
+                            const double f = 1.5 - 0.5 * n2;
+                            const double qn = q1 * f;
+                            const float rel = (float)(cell_coord_bits(pn, sl ? shy : shx, rp.L[sl]) - (sl ? iwy : iwx));
+                            const float fq = (float)qn;
+                            const float rel_o = __shfl_xor_sync(um, rel, 1);
+                            const float fq_o = __shfl_xor_sync(um, fq, 1);
+                            if (sl == 0) {
+                                B.px[gA] = pn;
+                                B.q0[gA] = qn;
+                                const float4 nf = make_float4(rel, rel_o, fq, fq_o);
+                                B.f4a[gA] = nf;
+                                ws.ent[eA] = nf;
+                            } else {
+                                B.py[gA] = pn;
+                                B.q1[gA] = qn;
+                            }
+                        }
+                    } else if (sl == 0 && status != 0) {
                         if (status == 2) {
                             c_rbd += 1;
                         } else if ((ws.ovmask >> grp) & 1u) {
@@ -752,9 +803,8 @@ k_set2d(Dev dv, Shape2 sh, int nxt, int sigma, const uint32_t* __restrict__ item
                             const uint32_t gA = ws.gidx[eA];
                             Trial2 t2;
                             if (F32) {
-                                if (LAT) t2 = apply64(rp, ax64, ay64, ac64, as64, ws.mv[jc][k - k0]);
-                                else t2 = propose2d(rp, ax64, ay64, ac64, as64, ws.rw[grp][0], ws.rw[grp][1],
-                                                    ws.rw[grp][2], ws.rw[grp][3], ws.rw[grp][4], ws.rw[grp][5]);
+                                t2 = propose2d(rp, ax64, ay64, ac64, as64, ws.rw[grp][0], ws.rw[grp][1],
+                                               ws.rw[grp][2], ws.rw[grp][3], ws.rw[grp][4], ws.rw[grp][5]);
                             } else {
                                 t2.x = tpA.x; t2.y = tpA.y;
                                 t2.c = ws.tz[grp].x; t2.s = ws.tz[grp].y;
