@@ -391,6 +391,16 @@ def run_profile(args):
                                   "max": float((ex[okx] - ent[okx]).max())}
             out["kernel_span_ns"] = float(ex[okx].max() - e0)
         out["total_cycles_median"] = float(np.median(tr[:, 30] - tr[:, 0])) if (tr[:, 30] != 0).any() else None
+        # 3D kernel: point 31 holds the traced item's FP64 re-check count
+        rc = tr[:, 31]
+        if rc.any() and okx.any():
+            run = (ex - ent).astype(float)
+            w0, w1 = okx & (rc == 0), okx & (rc > 0)
+            out["rechecks_per_traced_item"] = {
+                "mean": float(rc.mean()), "frac_items_with": float((rc > 0).mean()),
+                "run_ns_p50_without": float(np.median(run[w0])) if w0.any() else None,
+                "run_ns_p50_with": float(np.median(run[w1])) if w1.any() else None,
+                "run_ns_max_without": float(run[w0].max()) if w0.any() else None}
     b.close()
     print(json.dumps(out))
 

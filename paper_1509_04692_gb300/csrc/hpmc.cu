@@ -51,6 +51,7 @@ struct hpmc_batch {
     double verts[kMaxV3 * 3] = {};
     double w_min = 0.0;
     double Rc = 0.0, rc2 = 0.0;
+    double rin = 0.0;                    // inradius about the local origin
     uint32_t R = 0, ntot = 0, ctot = 0, ntiles = 0;
     std::vector<HostRep> hr;
     std::vector<Rep> reps;
@@ -126,6 +127,7 @@ int shape_setup(hpmc_batch* h, int dim, const double* verts, uint32_t nv)
     h->dim = dim;
     h->nv = (int)nv;
     std::memcpy(h->verts, verts, sizeof(double) * nv * dim);
+    h->rin = shape_inradius(dim, verts, nv);
     return 0;
 }
 
@@ -194,6 +196,15 @@ int rep_geometry(const hpmc_batch* h, const HostRep& hr, Rep& rp)
         rp.out_hi[a] = f32_up(rp.w[a] + g.e_in);
     }
     rp.cull_keep = f32_down(h->rc2 - g.e_cull);
+    // centres closer than twice the inradius: the inscribed balls meet, so the
+    // shapes overlap at depth 2 rin - |Delta|; with the band of the certified
+    // GJK (and far above any FP64 rounding) every FP64 test answers overlap
+    {
+        const double band = 2e-9 * 2.0 * h->Rc;
+        const double r2 = 2.0 * h->rin * (1.0 - 1e-12) - band;
+        rp.ins64 = r2 > 0.0 ? r2 * r2 * (1.0 - 1e-12) : -1.0;
+        rp.ins32 = r2 > 0.0 ? f32_down(r2 * r2 - g.e_cull) : -1.0f;
+    }
     rp.cull_skip = f32_up(h->rc2 + g.e_cull);
     rp.sat_e = f32_up(g.e_sat);
     rp.e_dlt32 = f32_up(g.e_dlt);

@@ -188,21 +188,46 @@ __device__ __forceinline__ void qrot(const double q[4], const double v[3], doubl
 struct Trial3 { double x[3]; double q[4]; };
 
 // 3D translation + rotation dq = (1, v) / sqrt(1 + v.v) from words r1..r12.
-// trial orientation of the contract: q' = renorm(q (x) dq), dq = (1, v) / |(1, v)|,
+// orientation step of the contract: dq = (1, v) / sqrt(1 + v.v) with
 // v = tau (2u - 1) per component from words r[7..12]
-__device__ __forceinline__ void propose3d_orient(const Rep& rp, const double q[4], const uint32_t* r, double o[4])
+__device__ __forceinline__ void orient_step3(const Rep& rp, const uint32_t* r, double dq[4])
 {
     const double v0 = rp.tau_s * pm53(r[7], r[8]);
     const double v1 = rp.tau_s * pm53(r[9], r[10]);
     const double v2 = rp.tau_s * pm53(r[11], r[12]);
     const double vv = (v0 * v0 + v1 * v1) + v2 * v2;
     const double inv = 1.0 / sqrt(1.0 + vv);
-    const double dq[4] = { inv, v0 * inv, v1 * inv, v2 * inv };
+    dq[0] = inv; dq[1] = v0 * inv; dq[2] = v1 * inv; dq[3] = v2 * inv;
+}
+
+// trial orientation of the contract: q' = renorm(q (x) dq)
+__device__ __forceinline__ void orient_apply3(const double q[4], const double dq[4], double o[4])
+{
     double q1[4];
     qmul(q, dq, q1);
     const double n2 = ((q1[0] * q1[0] + q1[1] * q1[1]) + q1[2] * q1[2]) + q1[3] * q1[3];
     const double f = 1.5 - 0.5 * n2;
     o[0] = q1[0] * f; o[1] = q1[1] * f; o[2] = q1[2] * f; o[3] = q1[3] * f;
+}
+
+// Component i of qmul(a, b) with the contract's operations: a0 b_i first,
+// then a_j b_(i^j) for j = 1, 2, 3 in order, the sign of each term folded
+// into a_j (negation is exact, and x - y rounds as x + (-y)).
+__device__ __forceinline__ double qmul_component(const double a[4], const double* b, int i)
+{
+    const int neg = (0x2147 >> (4 * i)) & 7;          // i: 0 -> 7, 1 -> 4, 2 -> 1, 3 -> 2
+    double acc = a[0] * b[i];
+    acc = acc + ((neg & 1) ? -a[1] : a[1]) * b[i ^ 1];
+    acc = acc + ((neg & 2) ? -a[2] : a[2]) * b[i ^ 2];
+    acc = acc + ((neg & 4) ? -a[3] : a[3]) * b[i ^ 3];
+    return acc;
+}
+
+__device__ __forceinline__ void propose3d_orient(const Rep& rp, const double q[4], const uint32_t* r, double o[4])
+{
+    double dq[4];
+    orient_step3(rp, r, dq);
+    orient_apply3(q, dq, o);
 }
 
 __device__ __forceinline__ Trial3 propose3d(const Rep& rp, const double x[3], const double q[4],

@@ -84,4 +84,49 @@ inline int build_shapes(int dim, const double* verts, uint32_t nv, Shape2& s2, S
     return 0;
 }
 
+// Inradius about the local origin: the distance from the origin to the
+// nearest facet plane (2D: edge line), or 0 when the origin is not strictly
+// inside.  A ball of this radius lies inside the shape, so two shapes whose
+// centres are closer than twice it overlap whatever their orientations.
+// 3D facets are found by brute force over vertex triples (nv <= 32).
+inline double shape_inradius(int dim, const double* v, uint32_t nv)
+{
+    double best = INFINITY;
+    if (dim == 2) {
+        for (uint32_t k = 0; k < nv; ++k) {
+            const double* p0 = v + 2 * k;
+            const double* p1 = v + 2 * ((k + 1) % nv);
+            const double nx = p1[1] - p0[1], ny = p0[0] - p1[0];      // outward (CCW)
+            const double nn = std::sqrt(nx * nx + ny * ny);
+            best = std::fmin(best, (nx * p0[0] + ny * p0[1]) / nn);
+        }
+    } else {
+        double scale = 0.0;
+        for (uint32_t i = 0; i < 3 * nv; ++i) scale = std::fmax(scale, std::fabs(v[i]));
+        for (uint32_t i = 0; i < nv; ++i)
+            for (uint32_t j = i + 1; j < nv; ++j)
+                for (uint32_t k = j + 1; k < nv; ++k) {
+                    const double* a = v + 3 * i;
+                    const double* b = v + 3 * j;
+                    const double* c = v + 3 * k;
+                    const double u[3] = { b[0] - a[0], b[1] - a[1], b[2] - a[2] };
+                    const double w[3] = { c[0] - a[0], c[1] - a[1], c[2] - a[2] };
+                    double n[3] = { u[1] * w[2] - u[2] * w[1], u[2] * w[0] - u[0] * w[2], u[0] * w[1] - u[1] * w[0] };
+                    const double nn = std::sqrt(n[0] * n[0] + n[1] * n[1] + n[2] * n[2]);
+                    if (!(nn > 1e-9 * scale * scale)) continue;
+                    for (double& x : n) x /= nn;
+                    const double d0 = n[0] * a[0] + n[1] * a[1] + n[2] * a[2];
+                    int above = 0, below = 0;
+                    for (uint32_t m = 0; m < nv; ++m) {
+                        const double t = n[0] * v[3 * m] + n[1] * v[3 * m + 1] + n[2] * v[3 * m + 2] - d0;
+                        if (t > 1e-9 * scale) above += 1;
+                        if (t < -1e-9 * scale) below += 1;
+                    }
+                    if (above && below) continue;               // not a supporting plane
+                    best = std::fmin(best, std::fabs(d0) * ((above ? -d0 : d0) > 0.0 ? 1.0 : -1.0));
+                }
+    }
+    return best > 0.0 && std::isfinite(best) ? best : 0.0;
+}
+
 }  // namespace hpmc

@@ -20,6 +20,32 @@
 
 namespace hpmc {
 
+// Random words and orientation step of one select (state independent).
+struct MoveData3 {
+    double dq[4];        // (1, v) / sqrt(1 + v.v), the contract's orientation step
+    uint32_t w[12];      // words r1..r12
+    uint32_t r0;         // pick word
+    uint32_t pad;
+};
+
+__device__ __forceinline__ MoveData3 precompute_select3(const Rep& rp, uint64_t seed, uint64_t sweep,
+                                                        uint32_t sigma, uint32_t cell, uint32_t k)
+{
+    uint32_t w16[16];
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+        const uint4 bb = move_block(seed, sweep, sigma, cell, k, (uint32_t)b);
+        w16[4 * b] = bb.x; w16[4 * b + 1] = bb.y; w16[4 * b + 2] = bb.z; w16[4 * b + 3] = bb.w;
+    }
+    MoveData3 m;
+    m.r0 = w16[0];
+#pragma unroll
+    for (int q = 0; q < 12; ++q) m.w[q] = w16[q + 1];
+    orient_step3(rp, w16, m.dq);
+    m.pad = 0;
+    return m;
+}
+
 template <int G, bool F32>
 struct Warp3 {
     static constexpr int S = 32 / G;                  // cells per strip
@@ -33,6 +59,8 @@ struct Warp3 {
     double eq[F32 ? 1 : CAP][4];                      // FP64 quaternion
     uint32_t gidx[CAP];
     uint16_t sbeg[9][M + 1];
+    uint32_t rowinfo[10][4];                          // per row: offset, entries before the x wrap, starts
+
     uint16_t beg[S][27];
     uint16_t pfx[S][28];
     float4 qd[QCAP];                                  // queued Delta32
@@ -42,6 +70,7 @@ struct Warp3 {
     double tp[S][3], tq[S][4];                        // FP64 trial (FP64 form)
     uint32_t rw[S][12];                               // words r1..r12
     uint16_t eA[S];
+    MoveData3 mv[S][G];                               // selects of the current chunk
     unsigned int ovmask;
 };
 
@@ -79,8 +108,13 @@ k_set3d(Dev dv, Shape3 sh, int nxt, int sigma, const uint32_t* __restrict__ item
     const uint32_t* __restrict__ start = dv.start;
     const uint32_t nitems = item_base[dv.R];
     const uint32_t wpb = blockDim.x >> 5;
+    const uint32_t wid = blockIdx.x * wpb + (threadIdx.x >> 5);
+    HPMC_STAMP_NS(dv, wid, lane, 28);
 
-    for (uint32_t item = blockIdx.x * wpb + (threadIdx.x >> 5); item < nitems; item += gridDim.x * wpb) {
+    for (uint32_t item = wid; item < nitems; item += gridDim.x * wpb) {
+        const bool first = item == wid;
+        (void)first;
+        HPMC_STAMP(dv, wid, first, lane, 0);
         uint32_t lo = 0, hi = dv.R;
         while (hi - lo > 1) {
             const uint32_t mid = (lo + hi) >> 1;
@@ -113,18 +147,37 @@ k_set3d(Dev dv, Shape3 sh, int nxt, int sigma, const uint32_t* __restrict__ item
         }
         const double iwy = (double)iy * rp.w[1];
         const double iwz = (double)iz * rp.w[2];
+        HPMC_STAMP(dv, wid, first, lane, 1);
 
         int j0 = 0;
         while (j0 < Sv) {
-            // ---- sub-strip [j0, j1) whose nine staged rows fit CAP
+            // ---- sub-strip [j0, j1) whose nine staged rows fit CAP: every
+            // cell start of the nine rows is loaded at once (one round trip)
+            constexpr int NCH = (W::M + 31) / 32;       // 32-column chunks per row
             int j1 = Sv;
             bool skip_cell = false;
+            int xa = 0, Mp = 0;
+            uint32_t s0[9][NCH], cnt[9][NCH];
             for (;;) {
-                const int xa = ((sigma & 1) + 2 * (jfirst + j0) - 1 + nc0) % nc0;
-                const int len = 2 * (j1 - j0) + 1;
-                uint32_t cnt = 0;
-                if (lane < 9) cnt = row_count3(start, rowbase[lane], nc0, xa, len);
-                const uint32_t tot = __reduce_add_sync(FULL, cnt);
+                xa = ((sigma & 1) + 2 * (jfirst + j0) - 1 + nc0) % nc0;
+                Mp = 2 * (j1 - j0) + 1;
+                uint32_t mine = 0;
+#pragma unroll
+                for (int q = 0; q < 9; ++q)
+#pragma unroll
+                    for (int ch = 0; ch < NCH; ++ch) {
+                        const int m = ch * 32 + lane;
+                        s0[q][ch] = 0u;
+                        cnt[q][ch] = 0u;
+                        if (m < Mp) {
+                            const uint32_t c = rowbase[q] + (uint32_t)((xa + m) % nc0);
+                            const uint32_t a0 = start[c];
+                            s0[q][ch] = a0;
+                            cnt[q][ch] = start[c + 1] - a0;
+                            mine += cnt[q][ch];
+                        }
+                    }
+                const uint32_t tot = __reduce_add_sync(FULL, mine);
                 if (tot <= (uint32_t)W::CAP) break;
                 if (j1 == j0 + 1) { skip_cell = true; break; }
                 j1 = j0 + (j1 - j0) / 2;
@@ -134,51 +187,63 @@ k_set3d(Dev dv, Shape3 sh, int nxt, int sigma, const uint32_t* __restrict__ item
                 j0 += 1;
                 continue;
             }
-            const int xa = ((sigma & 1) + 2 * (jfirst + j0) - 1 + nc0) % nc0;
-            const int Mp = 2 * (j1 - j0) + 1;
-            const int mwrap = (xa + Mp > nc0) ? nc0 - xa : Mp;
-            // ---- stage the nine rows
+            const int mwrap = (xa + Mp > nc0) ? nc0 - xa : Mp;   // first column wrapped to x = 0
+            // ---- staged begin of every cell (per-row scans of the counts)
             uint32_t off = 0;
-#pragma unroll 1
+#pragma unroll
             for (int q = 0; q < 9; ++q) {
-                uint32_t run = 0;
-                for (int mb = 0; mb < Mp; mb += 32) {
-                    const int m = mb + lane;
-                    uint32_t cnt = 0;
-                    if (m < Mp) {
-                        const uint32_t c = rowbase[q] + (uint32_t)((xa + m) % nc0);
-                        cnt = start[c + 1] - start[c];
-                    }
-                    uint32_t incl = cnt;
+                uint32_t run = 0, at_wrap = 0, gb = 0;
+#pragma unroll
+                for (int ch = 0; ch < NCH; ++ch) {
+                    const int m = ch * 32 + lane;
+                    const uint32_t c = cnt[q][ch];
+                    uint32_t incl = c;
 #pragma unroll
                     for (int o = 1; o < 32; o <<= 1) {
                         const uint32_t t = __shfl_up_sync(FULL, incl, o);
                         if (lane >= o) incl += t;
                     }
-                    if (m < Mp) ws.sbeg[q][m] = (uint16_t)(off + run + incl - cnt);
+                    const uint32_t excl = run + incl - c;
+                    if (m < Mp) ws.sbeg[q][m] = (uint16_t)(off + excl);
+                    if (mwrap < Mp && mwrap >= ch * 32 && mwrap < ch * 32 + 32) {
+                        at_wrap = __shfl_sync(FULL, excl, mwrap - ch * 32);
+                        gb = __shfl_sync(FULL, s0[q][ch], mwrap - ch * 32);
+                    }
                     run += __shfl_sync(FULL, incl, 31);
                 }
-                if (lane == 0) ws.sbeg[q][Mp] = (uint16_t)(off + run);
-                __syncwarp();
-                const uint32_t gA0 = start[rowbase[q] + xa];
-                const uint32_t gB0 = start[rowbase[q]];
-                const uint32_t lenA = (mwrap < Mp) ? (uint32_t)ws.sbeg[q][mwrap] - off : run;
-                for (uint32_t t = lane; t < run; t += 32) {
-                    const uint32_t gi = t < lenA ? gA0 + t : gB0 + (t - lenA);
-                    const uint32_t si = off + t;
-                    ws.gidx[si] = gi;
-                    if (F32) {
-                        ws.ea[si] = B.f4a[gi];
-                        ws.eb[si] = B.f4b[gi];
-                    } else {
-                        ws.ep[si][0] = B.px[gi]; ws.ep[si][1] = B.py[gi]; ws.ep[si][2] = B.pz[gi];
-                        ws.eq[si][0] = B.q0[gi]; ws.eq[si][1] = B.q1[gi];
-                        ws.eq[si][2] = B.q2[gi]; ws.eq[si][3] = B.q3[gi];
-                    }
+                const uint32_t ga = __shfl_sync(FULL, s0[q][0], 0);
+                if (mwrap >= Mp) at_wrap = run;
+                if (lane == 0) {
+                    ws.sbeg[q][Mp] = (uint16_t)(off + run);
+                    ws.rowinfo[q][0] = off;
+                    ws.rowinfo[q][1] = at_wrap;
+                    ws.rowinfo[q][2] = ga;
+                    ws.rowinfo[q][3] = gb;
                 }
                 off += run;
             }
+            if (lane == 0) ws.rowinfo[9][0] = off;
             __syncwarp();
+            // ---- stage every entry of the nine rows (one pass of loads)
+            for (uint32_t t = lane; t < off; t += 32) {
+                int q = 0;
+#pragma unroll
+                for (int qq = 1; qq < 9; ++qq) q += (t >= ws.rowinfo[qq][0]) ? 1 : 0;
+                const uint32_t u = t - ws.rowinfo[q][0];
+                const uint32_t la = ws.rowinfo[q][1];
+                const uint32_t gi = u < la ? ws.rowinfo[q][2] + u : ws.rowinfo[q][3] + (u - la);
+                ws.gidx[t] = gi;
+                if (F32) {
+                    ws.ea[t] = B.f4a[gi];
+                    ws.eb[t] = B.f4b[gi];
+                } else {
+                    ws.ep[t][0] = B.px[gi]; ws.ep[t][1] = B.py[gi]; ws.ep[t][2] = B.pz[gi];
+                    ws.eq[t][0] = B.q0[gi]; ws.eq[t][1] = B.q1[gi];
+                    ws.eq[t][2] = B.q2[gi]; ws.eq[t][3] = B.q3[gi];
+                }
+            }
+            __syncwarp();
+            HPMC_STAMP(dv, wid, first, lane, 3);
             // ---- stencil tables
             const bool valid = grp < (j1 - j0);
             const int mc = 1 + 2 * grp;
@@ -205,34 +270,34 @@ k_set3d(Dev dv, Shape3 sh, int nxt, int sigma, const uint32_t* __restrict__ item
             const bool live_cell = valid && n_c > 0;
 
 #pragma unroll 1
-            for (uint32_t k = 0; k < nsel; ++k) {
+            HPMC_STAMP(dv, wid, first, lane, 4);
+#pragma unroll 1
+            for (uint32_t k0 = 0; k0 < nsel; k0 += G) {
+            // ---- Philox words and orientation steps of a chunk of selects, one
+            // (cell, select) per lane
+            {
+                const uint32_t kk = k0 + (uint32_t)sl;
+                if (live_cell && kk < nsel)
+                    ws.mv[grp][sl] = precompute_select3(rp, seed, sweep, (uint32_t)sigma, cell_local, kk);
+                __syncwarp();
+            }
+            const uint32_t kend = min(nsel, k0 + (uint32_t)G);
+#pragma unroll 1
+            for (uint32_t k = k0; k < kend; ++k) {
+                const MoveData3& m = ws.mv[grp][k - k0];
                 int status = 0;
                 if (sl == 0 && live_cell) {
                     c_moves += 1;
-                    uint32_t w16[16];
+                    const uint32_t eA = cb + __umulhi(m.r0, n_c);
 #pragma unroll
-                    for (int b = 0; b < 4; ++b) {
-                        const uint4 bb = move_block(seed, sweep, (uint32_t)sigma, cell_local, k, (uint32_t)b);
-                        w16[4 * b] = bb.x; w16[4 * b + 1] = bb.y; w16[4 * b + 2] = bb.z; w16[4 * b + 3] = bb.w;
-                    }
-                    const uint32_t eA = cb + __umulhi(w16[0], n_c);
-#pragma unroll
-                    for (int q = 0; q < 12; ++q) ws.rw[grp][q] = w16[q + 1];
+                    for (int q = 0; q < 12; ++q) ws.rw[grp][q] = m.w[q];
                     ws.eA[grp] = (uint16_t)eA;
                     if (F32) {
                         const float4 fa = ws.ea[eA];
-                        const float rx = __fadd_rn(fa.x, __fmul_rn(rp.d32, m24(w16[1])));
-                        const float ry = __fadd_rn(fa.y, __fmul_rn(rp.d32, m24(w16[3])));
-                        const float rz = __fadd_rn(fa.z, __fmul_rn(rp.d32, m24(w16[5])));
-                        // the trial orientation is the contract's FP64 one, cast:
-                        // its FP32 copy then differs by one rounding only
-                        const uint32_t gA = ws.gidx[eA];
-                        const double qp[4] = { B.q0[gA], B.q1[gA], B.q2[gA], B.q3[gA] };
-                        double qt[4];
-                        propose3d_orient(rp, qp, w16, qt);
-                        const float q0 = (float)qt[0], q1 = (float)qt[1], q2 = (float)qt[2], q3 = (float)qt[3];
-                        ws.tra[grp] = make_float4(rx, ry, rz, q0);
-                        ws.trb[grp] = make_float4(q1, q2, q3, 0.f);
+                        const float rx = __fadd_rn(fa.x, __fmul_rn(rp.d32, m24(m.w[0])));
+                        const float ry = __fadd_rn(fa.y, __fmul_rn(rp.d32, m24(m.w[2])));
+                        const float rz = __fadd_rn(fa.z, __fmul_rn(rp.d32, m24(m.w[4])));
+                        ws.tra[grp] = make_float4(rx, ry, rz, 0.f);
                         const bool out = rx < rp.out_lo || ry < rp.out_lo || rz < rp.out_lo || rx > rp.out_hi[0] ||
                                          ry > rp.out_hi[1] || rz > rp.out_hi[2];
                         const bool in = rx > rp.in_lo && ry > rp.in_lo && rz > rp.in_lo && rx < rp.in_hi[0] &&
@@ -250,21 +315,67 @@ k_set3d(Dev dv, Shape3 sh, int nxt, int sigma, const uint32_t* __restrict__ item
                             status = ok ? 1 : 2;
                         }
                     } else {
-                        const double x[3] = { ws.ep[eA][0], ws.ep[eA][1], ws.ep[eA][2] };
-                        const double qa[4] = { ws.eq[eA][0], ws.eq[eA][1], ws.eq[eA][2], ws.eq[eA][3] };
-                        const Trial3 t3 = propose3d(rp, x, qa, w16);
+                        double x[3];
+                        x[0] = wrap_pos_bits(ws.ep[eA][0] + rp.d_s * pm53(m.w[0], m.w[1]), rp.L[0]);
+                        x[1] = wrap_pos_bits(ws.ep[eA][1] + rp.d_s * pm53(m.w[2], m.w[3]), rp.L[1]);
+                        x[2] = wrap_pos_bits(ws.ep[eA][2] + rp.d_s * pm53(m.w[4], m.w[5]), rp.L[2]);
 #pragma unroll
-                        for (int a = 0; a < 3; ++a) ws.tp[grp][a] = t3.x[a];
-#pragma unroll
-                        for (int a = 0; a < 4; ++a) ws.tq[grp][a] = t3.q[a];
-                        const bool ok = cell_axis(t3.x[0], shx, rp.L[0], rp.inv_w[0], nc0) == ix &&
-                                        cell_axis(t3.x[1], shy, rp.L[1], rp.inv_w[1], nc1) == iy &&
-                                        cell_axis(t3.x[2], shz, rp.L[2], rp.inv_w[2], nc2) == iz;
+                        for (int a = 0; a < 3; ++a) ws.tp[grp][a] = x[a];
+                        const bool ok = cell_axis(x[0], shx, rp.L[0], rp.inv_w[0], nc0) == ix &&
+                                        cell_axis(x[1], shy, rp.L[1], rp.inv_w[1], nc1) == iy &&
+                                        cell_axis(x[2], shz, rp.L[2], rp.inv_w[2], nc2) == iz;
                         status = ok ? 1 : 2;
                     }
                 }
                 if (lane == 0) ws.ovmask = 0u;
                 status = __shfl_sync(FULL, status, grp * G);
+                __syncwarp();
+                // ---- trial orientation of the contract, only for moves that stay
+                // in their cell; with 4+ lanes per cell each of lanes 0..3
+                // computes one quaternion component (same operations)
+                {
+                    constexpr int NQ = G >= 4 ? 4 : 1;
+                    const bool on = status == 1 && sl < NQ;
+                    const unsigned om = __ballot_sync(FULL, on);
+                    if (on) {
+                        const int eA = ws.eA[grp];
+                        double qa[4];
+                        if (F32) {
+                            const uint32_t gA = ws.gidx[eA];
+                            qa[0] = B.q0[gA]; qa[1] = B.q1[gA]; qa[2] = B.q2[gA]; qa[3] = B.q3[gA];
+                        } else {
+#pragma unroll
+                            for (int a = 0; a < 4; ++a) qa[a] = ws.eq[eA][a];
+                        }
+                        if constexpr (NQ == 4) {
+                            const double c = qmul_component(qa, m.dq, sl);
+                            const double sq = c * c;
+                            const int base = grp * G;
+                            const double s0 = __shfl_sync(om, sq, base), s1 = __shfl_sync(om, sq, base + 1);
+                            const double s2 = __shfl_sync(om, sq, base + 2), s3 = __shfl_sync(om, sq, base + 3);
+                            const double n2 = ((s0 + s1) + s2) + s3;
+                            const double f = 1.5 - 0.5 * n2;
+                            const double o = c * f;
+                            ws.tq[grp][sl] = o;
+                            if (F32) {
+                                if (sl == 0) ws.tra[grp].w = (float)o;
+                                else if (sl == 1) ws.trb[grp].x = (float)o;
+                                else if (sl == 2) ws.trb[grp].y = (float)o;
+                                else ws.trb[grp].z = (float)o;
+                            }
+                        } else {
+                            double o[4];
+                            orient_apply3(qa, m.dq, o);
+#pragma unroll
+                            for (int a = 0; a < 4; ++a) ws.tq[grp][a] = o[a];
+                            if (F32) {
+                                ws.tra[grp].w = (float)o[0];
+                                ws.trb[grp] = make_float4((float)o[1], (float)o[2], (float)o[3], 0.f);
+                            }
+                        }
+                    }
+                }
+                if (k < 7) HPMC_STAMP(dv, wid, first, lane, 6 + 3 * (int)k);
                 __syncwarp();
                 const int myA = (status == 1) ? (int)ws.eA[grp] : -1;
                 float4 ta = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -279,7 +390,7 @@ k_set3d(Dev dv, Shape3 sh, int nxt, int sigma, const uint32_t* __restrict__ item
                 for (int it = 0;; ++it) {
                     const int t = sl + it * G;
                     const bool live = (status == 1) && t < T && !((ws.ovmask >> grp) & 1u);
-                    bool keep = false;
+                    bool keep = false, ins = false;
                     float4 dl = make_float4(0.f, 0.f, 0.f, 0.f);
                     int e = 0;
                     if (live) {
@@ -296,7 +407,9 @@ k_set3d(Dev dv, Shape3 sh, int nxt, int sigma, const uint32_t* __restrict__ item
                                 dl.y = __fsub_rn(__fadd_rn(f.y, (float)oy * rp.w32[1]), ta.y);
                                 dl.z = __fsub_rn(__fadd_rn(f.z, (float)oz * rp.w32[2]), ta.z);
                                 const float q32 = __fmaf_rn(dl.x, dl.x, __fmaf_rn(dl.y, dl.y, __fmul_rn(dl.z, dl.z)));
-                                if (q32 < rp.cull_keep) {
+                                if (q32 < rp.ins32) {
+                                    ins = true;                    // inscribed balls meet
+                                } else if (q32 < rp.cull_keep) {
                                     keep = true;
                                 } else if (q32 > rp.cull_skip) {
                                     keep = false;
@@ -313,9 +426,15 @@ k_set3d(Dev dv, Shape3 sh, int nxt, int sigma, const uint32_t* __restrict__ item
                                 const double Dx = min_image(ws.ep[e][0] - tpx, rp.L[0], rp.halfL[0]);
                                 const double Dy = min_image(ws.ep[e][1] - tpy, rp.L[1], rp.halfL[1]);
                                 const double Dz = min_image(ws.ep[e][2] - tpz, rp.L[2], rp.halfL[2]);
-                                keep = ((Dx * Dx + Dy * Dy) + Dz * Dz) <= sh.rc2;
+                                const double q2 = (Dx * Dx + Dy * Dy) + Dz * Dz;
+                                ins = q2 < rp.ins64;
+                                keep = !ins && q2 <= sh.rc2;
                             }
                         }
+                    }
+                    if (ins) {
+                        c_chk += 1;
+                        atomicOr(&ws.ovmask, 1u << grp);
                     }
                     const unsigned bal = __ballot_sync(FULL, keep);
                     if (keep) {
@@ -380,6 +499,7 @@ k_set3d(Dev dv, Shape3 sh, int nxt, int sigma, const uint32_t* __restrict__ item
                     }
                     if (!any_live && qn == 0) break;
                 }
+                if (k < 7) HPMC_STAMP(dv, wid, first, lane, 7 + 3 * (int)k);
                 // ---- accept or reject
                 if (sl == 0 && status != 0) {
                     if (status == 2) {
@@ -392,7 +512,13 @@ k_set3d(Dev dv, Shape3 sh, int nxt, int sigma, const uint32_t* __restrict__ item
                         const uint32_t gA = ws.gidx[eA];
                         Trial3 t3;
                         if (F32) {
-                            t3 = trial3_of(rp, B, gA, ws.rw[grp]);
+                            // position from the words; orientation as computed at the proposal
+                            const uint32_t* w = ws.rw[grp];
+                            t3.x[0] = wrap_pos_bits(B.px[gA] + rp.d_s * pm53(w[0], w[1]), rp.L[0]);
+                            t3.x[1] = wrap_pos_bits(B.py[gA] + rp.d_s * pm53(w[2], w[3]), rp.L[1]);
+                            t3.x[2] = wrap_pos_bits(B.pz[gA] + rp.d_s * pm53(w[4], w[5]), rp.L[2]);
+#pragma unroll
+                            for (int a = 0; a < 4; ++a) t3.q[a] = ws.tq[grp][a];
                         } else {
 #pragma unroll
                             for (int a = 0; a < 3; ++a) t3.x[a] = ws.tp[grp][a];
@@ -418,10 +544,13 @@ k_set3d(Dev dv, Shape3 sh, int nxt, int sigma, const uint32_t* __restrict__ item
                     }
                 }
                 __syncwarp();
+                if (k < 7) HPMC_STAMP(dv, wid, first, lane, 8 + 3 * (int)k);
             }
+            }   // chunks of selects
             j0 = j1;
             __syncwarp();
         }
+        HPMC_STAMP(dv, wid, first, lane, 30);
         c_moves = __reduce_add_sync(FULL, c_moves);
         c_acc = __reduce_add_sync(FULL, c_acc);
         c_rov = __reduce_add_sync(FULL, c_rov);
@@ -430,6 +559,11 @@ k_set3d(Dev dv, Shape3 sh, int nxt, int sigma, const uint32_t* __restrict__ item
         c_chk = __reduce_add_sync(FULL, c_chk);
         c_rechk = __reduce_add_sync(FULL, c_rechk);
         c_cap = __reduce_add_sync(FULL, c_cap);
+#ifdef HPMC_TRACE
+        // point 31 of the traced item: its FP64 re-checks (a count, not a stamp)
+        if (first && lane == 0 && dv.trace && wid < dv.trace_warps)
+            dv.trace[(size_t)wid * kTracePoints + 31] = c_rechk;
+#endif
         if (lane == 0) {
             unsigned long long* C = dv.counters + (size_t)r * kNumCounters;
             atomicAdd(C + CNT_MOVES, (unsigned long long)c_moves);
@@ -442,6 +576,7 @@ k_set3d(Dev dv, Shape3 sh, int nxt, int sigma, const uint32_t* __restrict__ item
             if (c_cap) atomicAdd(C + CNT_GJKCAP, (unsigned long long)c_cap);
         }
     }
+    HPMC_STAMP_NS(dv, wid, lane, 29);
 }
 
 }  // namespace hpmc
