@@ -9,7 +9,8 @@ rebuild + 4 checkerboard sets each), replayed from a CUDA graph.
 Headline `value`: FP32-filtered form (decisions identical to FP64), inputs
 resident in HBM.  `forms` reports the plain FP64 form on the same workload,
 the batched form (512 replicas of N ~ U{256..8192}, phi ~ U[0.40, 0.70]),
-32768 cubes at volume fraction 0.50 in both forms, and 2^24 pentagons at area
+32768 cubes and 32000 dodecahedra at volume fraction 0.50 in both forms, and
+2^24 pentagons at area
 fraction 0.60 on a 2048^2 cell list (FP32-filtered).
 `e2e`: the same metric through hpmc_run_host with host buffers (H2D + sweeps
 + D2H inside the timed region).  `cpu_baseline`: the C oracle on host cores.
@@ -297,6 +298,17 @@ def run_ours(args):
             forms[key] = f
             bc.close()
 
+    # ---- 3D: 32000 dodecahedra at volume fraction 0.5 (the paper's 3D shape), both forms
+    if not args.no_cubes:
+        sd = inputs.dodecahedra32000(42)
+        for prec, key in ((hpmc.HPMC_FP32_FILTERED, "dodecahedra32000_fp32_filtered"),
+                          (hpmc.HPMC_FP64, "dodecahedra32000_fp64")):
+            bd = hpmc.from_system(sd)
+            f = measure_form(bd, torch, stream, flush, prec, MELT, 50, 2)
+            f.update(workload=sd.name, N=sd.N, d=sd.d, a=sd.a, nselect=sd.nselect)
+            forms[key] = f
+            bd.close()
+
     # ---- large 2D: 2^24 pentagons on a 2048^2 cell list (state > L2)
     if not args.no_large:
         sl = inputs.large2d(42)
@@ -346,6 +358,8 @@ def run_profile(args):
         b = hpmc.from_systems(inputs.replica_systems(512))
     elif args.profile_workload == "cubes":
         b = hpmc.from_system(inputs.cubes32768(42))
+    elif args.profile_workload == "dodecahedra":
+        b = hpmc.from_system(inputs.dodecahedra32000(42))
     elif args.profile_workload == "large2d":
         b = hpmc.from_system(inputs.large2d(42, N=args.profile_n or inputs.LARGE2D_N))
     else:
@@ -410,7 +424,7 @@ def main():
     ap.add_argument("--profile-sweeps", type=int, default=0,
                     help="run the small ncu case instead of the benchmark")
     ap.add_argument("--profile-workload", default="fluid4096",
-                    choices=["fluid4096", "batched", "cubes", "large2d"])
+                    choices=["fluid4096", "batched", "cubes", "dodecahedra", "large2d"])
     ap.add_argument("--profile-fp64", action="store_true")
     ap.add_argument("--profile-n", type=int, default=0, help="N of the large2d profile case")
     ap.add_argument("--profile-melt", type=int, default=20, help="graph-replayed sweeps before profiling")

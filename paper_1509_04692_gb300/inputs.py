@@ -47,6 +47,21 @@ def polygon_area(v: np.ndarray) -> float:
     return 0.5 * float(np.sum(x * np.roll(y, -1) - np.roll(x, -1) * y))
 
 
+def dodecahedron(volume: float = 1.0) -> np.ndarray:
+    """Regular dodecahedron (20 vertices) of the given volume, centred, in the
+    standard orientation: the cube (+-1, +-1, +-1) and the cyclic
+    permutations of (0, +-1/g, +-g), g the golden ratio, scaled."""
+    g = (1.0 + math.sqrt(5.0)) / 2.0
+    v = [(x, y, z) for x in (-1.0, 1.0) for y in (-1.0, 1.0) for z in (-1.0, 1.0)]
+    for a in (-1.0, 1.0):
+        for b in (-1.0, 1.0):
+            v += [(0.0, a / g, b * g), (a / g, b * g, 0.0), (a * g, 0.0, b / g)]
+    v = np.array(v)
+    edge = 2.0 / g                                   # of the coordinates above
+    vol = (15.0 + 7.0 * math.sqrt(5.0)) / 4.0 * edge ** 3
+    return v * (volume / vol) ** (1.0 / 3.0)
+
+
 def cube_volume(edge: float) -> float:
     return edge ** 3
 
@@ -116,6 +131,21 @@ def cubic_lattice(N: int, L: float, rng: np.random.Generator):
     pos[pos >= L] = 0.0
     q = np.tile(np.array([1.0, 0.0, 0.0, 0.0]), (N, 1))
     return pos, q, a
+
+
+def fcc_lattice(n: int, a: float, rng: np.random.Generator):
+    """4 n^3 sites of a periodic face-centred cubic lattice of cubic cell a in
+    [0, n a)^3 (random global offset), identity orientations.
+    Returns (pos[4n^3, 3], quat[4n^3, 4])."""
+    g = np.arange(n) * a
+    corner = np.stack(np.meshgrid(g, g, g, indexing="ij"), axis=-1).reshape(-1, 3)
+    basis = np.array([[0.0, 0.0, 0.0], [0.0, 0.5, 0.5], [0.5, 0.0, 0.5], [0.5, 0.5, 0.0]]) * a
+    sites = (corner[:, None, :] + basis[None, :, :]).reshape(-1, 3)
+    L = n * a
+    pos = np.mod(sites + rng.uniform(0.0, L, size=3)[None, :], L)
+    pos[pos >= L] = 0.0
+    q = np.tile(np.array([1.0, 0.0, 0.0, 0.0]), (pos.shape[0], 1))
+    return pos, q
 
 
 @dataclass
@@ -234,3 +264,32 @@ def large2d(seed: int = 42, N: int = LARGE2D_N) -> System:
     """2^24 regular pentagons, area fraction 0.60, 2048^2 cells of width >= 1.99."""
     return pentagon_system(N, 0.60, seed, name=f"pentagon fluid N={N} phi=0.60 w_min=1.99",
                            d=FLUID4096_D, a=FLUID4096_A, nselect=4, w_min=LARGE2D_W_MIN)
+
+
+def dodecahedron_system(n: int = 20, phi: float = 0.50, seed: int = 42, d: float = 0.1, a: float = 0.1,
+                        nselect: int = 4) -> System:
+    """4 n^3 unit-volume regular dodecahedra at volume fraction phi, aligned in
+    the standard orientation on an FCC lattice (cubic cell (4 / phi)^(1/3);
+    at phi = 0.5 its nearest-site distance 1.414 keeps aligned shapes apart,
+    which tests check with the oracle)."""
+    v = dodecahedron(1.0)
+    cell = (4.0 / phi) ** (1.0 / 3.0)
+    rng = np.random.default_rng(seed)
+    pos, q = fcc_lattice(n, cell, rng)
+    L = n * cell
+    return System(name=f"dodecahedra N={pos.shape[0]} phi={phi}", dim=3, verts=v, L=np.array([L, L, L]),
+                  pos=pos, orient=q, phi=phi, seed=seed, d=d, a=a, nselect=nselect,
+                  notes={"init": "FCC lattice, aligned (standard orientation)"})
+
+
+# 32000 unit-volume dodecahedra at volume fraction 0.50 (the paper's 3D
+# benchmark shape and density): d = a = 0.087 gives a 30% acceptance ratio,
+# found with tune.tune_scale (d/a fixed at 1, 100-sweep pilots) after a
+# 1000-sweep melt from the FCC start at d = a = 0.1.
+DODECA_D = 0.087
+DODECA_A = 0.087
+
+
+def dodecahedra32000(seed: int = 42) -> System:
+    """32000 unit-volume regular dodecahedra, volume fraction 0.50."""
+    return dodecahedron_system(20, 0.50, seed, d=DODECA_D, a=DODECA_A, nselect=4)

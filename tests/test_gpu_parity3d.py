@@ -98,3 +98,21 @@ def test_batched_3d_replicas():
         ref = oracle_run(s, 12)
         assert_same((p, o, [c["accept"], c["reject_overlap"], c["reject_boundary"]]), ref)
     b.close()
+
+
+@pytest.mark.parametrize("mode", [F64, F32])
+def test_dodecahedra_32000_phi050(mode):
+    # 32000 regular dodecahedra (20 vertices: generic kernel) at volume
+    # fraction 0.50 from the aligned FCC start, with the tuned move sizes
+    s = inputs.dodecahedra32000(42)
+    ref = oracle_run(s, 4)
+    got = gpu_run(s, 4, mode, lanes=32, warps=4, graph=True)
+    assert_same(got, ref)
+    assert got[4] == 0
+
+
+def test_cubes_32768_tuned_moves():
+    # the benchmark's cube system and move sizes, graph-replayed as timed
+    s = inputs.cubes32768(42)
+    ref = oracle_run(s, 6)
+    assert_same(gpu_run(s, 6, F32, lanes=32, warps=4, graph=True), ref)
