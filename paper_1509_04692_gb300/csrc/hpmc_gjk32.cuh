@@ -296,6 +296,58 @@ __device__ __forceinline__ bool cert_inside(const G32* pb, const G32* va, const 
     return true;
 }
 
+// GJK stops at the first tetrahedron that encloses the origin, which may
+// have the origin next to one of its faces although the origin lies deep
+// inside B - A.  Expansion (one step of the polytope expansion used for
+// penetration depths, a few times): take the face nearest the origin, add
+// the support point w beyond it, and move to whichever of the three
+// tetrahedra (w, opposite vertex, face edge) encloses the origin; certify it.
+template <int NV>
+__device__ __noinline__ bool expand_inside(int nv, const G32* pb, const G32* va, SPt sp[4], float e_pb, float e_va,
+                                           float tau)
+{
+#pragma unroll 1
+    for (int rep = 0; rep < 4; ++rep) {
+        // face of the current tetrahedron nearest the origin (plain FP32)
+        int fbest = 0;
+        float dbest = 0.f;
+        G32 nbest = { 0.f, 0.f, 0.f };
+#pragma unroll 1
+        for (int f = 0; f < 4; ++f) {
+            const int i0 = (f == 3) ? 1 : 0, i1 = (f <= 1) ? 1 : 2, i2 = (f == 0) ? 2 : 3, i3 = 3 - f;
+            G32 n = g_cross(g_sub(sp[i1].p, sp[i0].p), g_sub(sp[i2].p, sp[i0].p));
+            if (g_dot(n, g_sub(sp[i3].p, sp[i0].p)) > 0.f) n = g_neg(n);       // outward
+            const float nn = g_dot(n, n);
+            if (!(nn > 0.f)) return false;
+            const float h = g_dot(n, sp[i0].p);                                 // > 0: origin inside
+            const float dd = h * fabsf(h) / nn;
+            if (f == 0 || dd < dbest) { dbest = dd; fbest = f; nbest = n; }
+        }
+        const int i0 = (fbest == 3) ? 1 : 0, i1 = (fbest <= 1) ? 1 : 2, i2 = (fbest == 0) ? 2 : 3, i3 = 3 - fbest;
+        const SPt w = g_support<NV>(nv, pb, va, nbest);
+        const float hw = g_dot(nbest, w.p), hf = g_dot(nbest, sp[i0].p);
+        if (!(hw > hf + 1e-6f * fabsf(hf) + 1e-30f)) return false;              // face on the boundary of B - A
+        const SPt T[3][4] = { { w, sp[i3], sp[i0], sp[i1] }, { w, sp[i3], sp[i1], sp[i2] },
+                              { w, sp[i3], sp[i2], sp[i0] } };
+        int pick = -1;
+#pragma unroll 1
+        for (int t = 0; t < 3 && pick < 0; ++t) {
+            bool in = true;
+#pragma unroll 1
+            for (int f = 0; f < 4 && in; ++f) {
+                const int j0 = (f == 3) ? 1 : 0, j1 = (f <= 1) ? 1 : 2, j2 = (f == 0) ? 2 : 3, j3 = 3 - f;
+                in = !g_outside(T[t][j0].p, T[t][j1].p, T[t][j2].p, T[t][j3].p);
+            }
+            if (in) pick = t;
+        }
+        if (pick < 0) return false;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) sp[k] = T[pick][k];
+        if (cert_inside(pb, va, sp, e_pb, e_va, tau)) return true;
+    }
+    return false;
+}
+
 // FP32 GJK + certificate for A (orientation qA) and B at Delta (orientation
 // qB), in A's frame: GJK32_SEPARATED / GJK32_OVERLAP when certified about the
 // exact shapes with margin tau (where the FP64 contract decides the same),
@@ -327,6 +379,8 @@ __device__ __noinline__ int gjk32_cert(const Shape3& sh, float dx, float dy, flo
         const G32 rr = rot(r0, r1, r2, r3, va[i]);
         pb[i] = G32{ rr.x + l.x, rr.y + l.y, rr.z + l.z };
     }
+    // the centre line first: well-separated pairs are certified without GJK
+    if (cert_separated<NV>(nv, pb, va, l, e_pb, e_va, tau)) return GJK32_SEPARATED;
     G32 d = g_neg(l);
     if (d.x == 0.f && d.y == 0.f && d.z == 0.f) d.x = -1.0f;
     SPt sp[4];
@@ -355,7 +409,10 @@ __device__ __noinline__ int gjk32_cert(const Shape3& sh, float dx, float dy, flo
         sp[n] = w;
         n += 1;
         const int rr = g_reduce(sp, n, v);
-        if (rr == 1) return cert_inside(pb, va, sp, e_pb, e_va, tau) ? GJK32_OVERLAP : GJK32_UNC_INSIDE;
+        if (rr == 1) {
+            if (cert_inside(pb, va, sp, e_pb, e_va, tau)) return GJK32_OVERLAP;
+            return expand_inside<NV>(nv, pb, va, sp, e_pb, e_va, tau) ? GJK32_OVERLAP : GJK32_UNC_INSIDE;
+        }
         if (rr == 2) return GJK32_UNC_DEGENERATE;
     }
     return GJK32_UNC_CAP;
