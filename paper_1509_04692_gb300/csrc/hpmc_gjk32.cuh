@@ -352,17 +352,19 @@ __device__ __noinline__ bool expand_inside(int nv, const G32* pb, const G32* va,
 // qB), in A's frame: GJK32_SEPARATED / GJK32_OVERLAP when certified about the
 // exact shapes with margin tau (where the FP64 contract decides the same),
 // GJK32_UNCERTAIN otherwise.
+// Quaternions as (w, x, y, z) in a float4's (x, y, z, w).
 template <int NV>
-__device__ __noinline__ int gjk32_cert(const Shape3& sh, float dx, float dy, float dz, const float qA[4],
-                                       const float qB[4], float e_pb, float e_va, float tau)
+__device__ __forceinline__ int gjk32_cert(const Shape3& sh, float dx, float dy, float dz, float4 qA, float4 qB,
+                                          float e_pb, float e_va, float tau)
 {
     const int nv = NV ? NV : sh.nv;
     // qr = conj(qA) qB, l = rot(conj(qA), Delta), pb = rot(qr, v) + l
-    const float a0 = qA[0], a1 = -qA[1], a2 = -qA[2], a3 = -qA[3];
-    const float r0 = ((a0 * qB[0] - a1 * qB[1]) - a2 * qB[2]) - a3 * qB[3];
-    const float r1 = ((a0 * qB[1] + a1 * qB[0]) + a2 * qB[3]) - a3 * qB[2];
-    const float r2 = ((a0 * qB[2] - a1 * qB[3]) + a2 * qB[0]) + a3 * qB[1];
-    const float r3 = ((a0 * qB[3] + a1 * qB[2]) - a2 * qB[1]) + a3 * qB[0];
+    const float a0 = qA.x, a1 = -qA.y, a2 = -qA.z, a3 = -qA.w;
+    const float b0 = qB.x, b1 = qB.y, b2 = qB.z, b3 = qB.w;
+    const float r0 = ((a0 * b0 - a1 * b1) - a2 * b2) - a3 * b3;
+    const float r1 = ((a0 * b1 + a1 * b0) + a2 * b3) - a3 * b2;
+    const float r2 = ((a0 * b2 - a1 * b3) + a2 * b0) + a3 * b1;
+    const float r3 = ((a0 * b3 + a1 * b2) - a2 * b1) + a3 * b0;
     auto rot = [](float w, float x, float y, float z, G32 v) {
         const float tx = 2.0f * (y * v.z - z * v.y);
         const float ty = 2.0f * (z * v.x - x * v.z);

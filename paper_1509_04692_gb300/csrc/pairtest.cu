@@ -38,8 +38,8 @@ __global__ void k_pairs3d(Shape3 sh, float e_pb, float e_va, float tau, uint32_t
     const double b[4] = { qB[4 * i], qB[4 * i + 1], qB[4 * i + 2], qB[4 * i + 3] };
     int it = 0;
     o64[i] = overlap3d64<0>(sh, d, a, b, &it) ? 1 : 0;
-    const float fa[4] = { (float)a[0], (float)a[1], (float)a[2], (float)a[3] };
-    const float fb[4] = { (float)b[0], (float)b[1], (float)b[2], (float)b[3] };
+    const float4 fa = make_float4((float)a[0], (float)a[1], (float)a[2], (float)a[3]);
+    const float4 fb = make_float4((float)b[0], (float)b[1], (float)b[2], (float)b[3]);
     const int v = gjk32_cert<0>(sh, (float)d[0], (float)d[1], (float)d[2], fa, fb, e_pb, e_va, tau);
     o32[i] = v;   // 0, 1, or the reason it is uncertain (>= 2)
 }
