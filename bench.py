@@ -45,6 +45,10 @@ SMS, FP32_LANES, MAX_MHZ = 152, 128, 2070.0
 PEAK_TFLOPS = SMS * FP32_LANES * 2 * MAX_MHZ * 1e6 / 1e12
 # algorithmic flops: move arithmetic + circumsphere culls + full SAT checks
 FLOP_MOVE, FLOP_CULL, FLOP_SAT = 30, 5, 330
+# DRAM bytes (read + write) of one set launch of this workload from ncu
+# (profiles/set2d_fluid4096.md, cold-cache replay); valid for the kernel as
+# captured there
+SET2D_FLUID_DRAM_BYTES = 224512
 
 
 def dist_env():
@@ -240,7 +244,7 @@ def run_ours(args):
     achieved = (flop_per_sweep / nsets) / (set_ms * 1e-3) / 1e12
     roofline = {"bound": "alu", "kernel": "k_set2d (checkerboard set)", "achieved": achieved,
                 "peak": PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / PEAK_TFLOPS,
-                "traffic": None,
+                "traffic": SET2D_FLUID_DRAM_BYTES,
                 "set_kernel_ms": set_ms, "rebuild_ms_per_sweep": ms_rebuild,
                 "peak_source": "152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz (nominal unit counts)",
                 "flops_per_move_model": f"{FLOP_MOVE} + {FLOP_CULL}*culls + {FLOP_SAT}*SAT checks"}
