@@ -291,8 +291,7 @@ SetKernel pick_kernel(const hpmc_batch* h)
         const bool fixed = h->nv == 5;
         return f32 ? set2d_f32_kernel(h->G, fixed) : set2d_f64_kernel(h->G, fixed);
     }
-    const bool fixed = h->nv == 8;
-    return f32 ? set3d_f32_kernel(h->G, fixed) : set3d_f64_kernel(h->G, fixed);
+    return f32 ? set3d_f32_kernel(h->G, h->nv) : set3d_f64_kernel(h->G, h->nv);
 }
 
 // enqueue the rebuild of the cell list from buffer `cur` into cur ^ 1

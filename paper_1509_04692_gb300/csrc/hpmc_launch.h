@@ -9,11 +9,14 @@ struct SetKernel {
     size_t smem_per_warp;    // dynamic shared memory per warp
 };
 
-// lanes per cell G in {1, 2, 4, 8, 16, 32}; fixed_nv: shape specialised on
-// the vertex count (5 for pentagons in 2D, 8 for cubes in 3D).
+// lanes per cell G in {1, 2, 4, 8, 16, 32}.  2D fixed_nv: specialised on 5
+// vertices (pentagons).  3D nv: specialised kernels for 8 (cubes) and 20
+// (dodecahedra) vertices, the generic one otherwise.
 SetKernel set2d_f32_kernel(int G, bool fixed_nv);
 SetKernel set2d_f64_kernel(int G, bool fixed_nv);
-SetKernel set3d_f32_kernel(int G, bool fixed_nv);
-SetKernel set3d_f64_kernel(int G, bool fixed_nv);
+SetKernel set3d_f32_kernel(int G, int nv);
+SetKernel set3d_f64_kernel(int G, int nv);
+SetKernel set3d_f32_nv20(int G);
+SetKernel set3d_f64_nv20(int G);
 
 }  // namespace hpmc

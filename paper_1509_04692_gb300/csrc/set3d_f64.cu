@@ -10,8 +10,10 @@ static SetKernel make3d()
     return { (const void*)&k_set3d<G, false, NV>, sizeof(Warp3<G, false>) };
 }
 
-SetKernel set3d_f64_kernel(int G, bool fixed_nv)
+SetKernel set3d_f64_kernel(int G, int nv)
 {
+    if (nv == 20) return set3d_f64_nv20(G);
+    const bool fixed_nv = nv == 8;
     switch (G) {
     case 1: return fixed_nv ? make3d<1, 8>() : make3d<1, 0>();
     case 2: return fixed_nv ? make3d<2, 8>() : make3d<2, 0>();
