@@ -28,7 +28,9 @@
  *
  * Parity status: every function here is pinned by the CPU tests (Philox
  * known-answer vectors, brute-force polygon/polyhedron predicates, SAT-15 for
- * boxes, ideal-gas closed form, move distributions, O(N^2) no-overlap).
+ * boxes, ideal-gas closed form, move distributions, O(N^2) no-overlap; for
+ * disks/spheres the contact definition and lattice closed forms of the
+ * scale-distribution histogram).
  */
 #include <math.h>
 #include <stdint.h>
@@ -103,7 +105,7 @@ typedef struct {
     double L[3], halfL[3];      /* box lengths (orthorhombic, periodic) */
     int nc[3];                  /* cells per axis (even, >= 4) */
     double w[3], inv_w[3];      /* cell width and nc/L */
-    int nv;                     /* vertices of the (single) shape */
+    int nv;                     /* vertices of the (single) shape; 0: disk/sphere */
     double v[OR_MAXV][3];       /* local-frame vertices */
     double R;                   /* circumradius */
     double rc2;                 /* (2R)^2: circumsphere cull threshold */
@@ -122,11 +124,13 @@ size_t or_system_size(void) { return sizeof(or_system); }
 /* Cell list geometry (Sec. 2.2.1): the shortest cell side must be at least
  * d_max = 2R.  Reading: ncell = floor(L / max(2R, w_min)), made even (for the
  * 2^d colouring) and required >= 4 (unique minimum image inside a stencil). */
+/* nv = 0 selects hard disks (2D) or spheres (3D) of radius verts[0] (the
+ * paper's validation systems, Sec. 4): the shape is its own circumsphere. */
 int or_init(or_system* s, int dim, const double* L, const double* verts, int nv, double w_min)
 {
     memset(s, 0, sizeof(*s));
     if (dim != 2 && dim != 3) return -1;
-    if (nv < 3 || nv > OR_MAXV) return -1;
+    if (nv != 0 && (nv < 3 || nv > OR_MAXV)) return -1;
     s->dim = dim;
     s->nv = nv;
     for (int i = 0; i < nv; ++i)
@@ -137,7 +141,11 @@ int or_init(or_system* s, int dim, const double* L, const double* verts, int nv,
         if (dim == 3) q = q + s->v[i][2] * s->v[i][2];
         if (q > r2) r2 = q;
     }
-    s->R = sqrt(r2);
+    if (nv == 0) {
+        if (!(verts[0] > 0.0)) return -1;
+        r2 = verts[0] * verts[0];
+    }
+    s->R = nv == 0 ? verts[0] : sqrt(r2);
     double dcut = s->R + s->R;
     s->rc2 = dcut * dcut;
     double wmin = dcut > w_min ? dcut : w_min;
@@ -152,7 +160,7 @@ int or_init(or_system* s, int dim, const double* L, const double* verts, int nv,
         s->w[k] = L[k] / (double)n;
         s->inv_w[k] = (double)n / L[k];
     }
-    if (dim == 2) {
+    if (dim == 2 && nv > 0) {
         /* convex, counter-clockwise polygon: every turn must be strictly left */
         for (int i = 0; i < nv; ++i) {
             const double* p0 = s->v[i];
@@ -285,6 +293,7 @@ static int or_sat_half(const or_system* s, double cr, double sr, double lx, doub
  * Returns 1 for overlap (touching counts as overlap), 0 when separated. */
 int or_overlap_2d(const or_system* s, const double D[2], const double zA[2], const double zB[2])
 {
+    if (s->nv == 0) return (D[0] * D[0] + D[1] * D[1]) <= s->rc2;    /* disks: distance <= 2R */
     double cA = zA[0], sA = zA[1], cB = zB[0], sB = zB[1];
     double cr = cA * cB + sA * sB;
     double sr = cA * sB - sA * cB;
@@ -503,6 +512,10 @@ static int or_gjk_reduce(double sp[4][3], int* n, double v[3])
 int or_overlap_3d(const or_system* s, const double D[3], const double qA[4], const double qB[4],
                   int* iters)
 {
+    if (s->nv == 0) {                                                 /* spheres */
+        *iters = 0;
+        return ((D[0] * D[0] + D[1] * D[1]) + D[2] * D[2]) <= s->rc2;
+    }
     or_gjk_pair g;
     g.s = s;
     double qAc[4] = { qA[0], -qA[1], -qA[2], -qA[3] };
@@ -683,7 +696,9 @@ int or_sweep(or_system* s, uint32_t N, double* pos, double* orient, uint64_t swe
                                     if (dim == 3) q2 = q2 + D[2] * D[2];
                                     if (q2 > s->rc2) continue;           /* circumsphere cull */
                                     int ov;
-                                    if (dim == 2) {
+                                    if (s->nv == 0) {
+                                        ov = 1;                 /* disks/spheres: q2 <= (2R)^2 */
+                                    } else if (dim == 2) {
                                         ov = or_overlap_2d(s, D, qn, orient + (size_t)b * qd);
                                     } else {
                                         int it = 0;
@@ -721,6 +736,36 @@ void or_overlap_batch(const or_system* s, uint32_t n, const double* D, const dou
             out[p] = or_overlap_3d(s, D + 3 * (size_t)p, qA + (size_t)qd * p, qB + (size_t)qd * p, &it);
         }
     }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Pressure by the scale distribution (Sec. 4): for disks/spheres of        */
+/* diameter sigma, compressing every position by the factor (1 - x) makes a  */
+/* pair at distance r overlap for x >= x* = 1 - sigma / r.  The histogram of  */
+/* x* near 0 extrapolated to x = 0 gives beta P / rho = 1 + h(0) / (dim N),  */
+/* h the number of pairs per unit x.  Every unordered pair (all pairs,       */
+/* minimum image) with 0 <= x* < x_max adds one to bin (int)(x* nbins/x_max). */
+/* ------------------------------------------------------------------------ */
+int or_sdf_histogram(const or_system* s, uint32_t N, const double* pos, double x_max, uint32_t nbins,
+                     uint64_t* hist)
+{
+    if (s->nv != 0 || !(x_max > 0.0) || nbins == 0) return -1;
+    const int dim = s->dim;
+    const double sigma = s->R + s->R;
+    const double scale = (double)nbins / x_max;
+    for (uint32_t i = 0; i < N; ++i)
+        for (uint32_t j = i + 1; j < N; ++j) {
+            double D[3] = { 0, 0, 0 };
+            for (int k = 0; k < dim; ++k)
+                D[k] = or_min_image(pos[(size_t)j * dim + k] - pos[(size_t)i * dim + k], s->L[k], s->halfL[k]);
+            double q2 = D[0] * D[0] + D[1] * D[1];
+            if (dim == 3) q2 = q2 + D[2] * D[2];
+            const double x = 1.0 - sigma / sqrt(q2);
+            if (!(x >= 0.0) || !(x < x_max)) continue;
+            const int b = (int)(x * scale);
+            if (b < (int)nbins) hist[b] += 1;
+        }
+    return 0;
 }
 
 /* Exported geometry for tests */

@@ -74,6 +74,9 @@ def lib():
             L.or_get_geometry.argtypes = [ctypes.c_void_p, dp, dp, ctypes.POINTER(ctypes.c_int), dp, dp]
             L.or_get_tau.restype = ctypes.c_double
             L.or_get_tau.argtypes = [ctypes.c_void_p]
+            L.or_sdf_histogram.restype = ctypes.c_int
+            L.or_sdf_histogram.argtypes = [ctypes.c_void_p, ctypes.c_uint32, dp, ctypes.c_double,
+                                           ctypes.c_uint32, ctypes.POINTER(ctypes.c_uint64)]
             L.or_rsa_2d.restype = ctypes.c_int
             L.or_rsa_2d.argtypes = [ctypes.c_void_p, ctypes.c_uint32, ctypes.c_uint64,
                                     ctypes.c_uint64, dp, dp, ctypes.POINTER(ctypes.c_uint64)]
@@ -103,20 +106,37 @@ def u53(a: int, b: int) -> float:
 
 
 class OracleSystem:
-    """One periodic box with one convex shape type (the oracle's view)."""
+    """One periodic box with one convex shape type (the oracle's view).
+    ``radius`` instead of ``verts`` selects disks (2D) or spheres (3D)."""
 
-    def __init__(self, dim, L, verts, w_min=0.0):
+    def __init__(self, dim, L, verts=None, w_min=0.0, radius=None):
         self.dim = int(dim)
         self._buf = ctypes.create_string_buffer(lib().or_system_size())
         Ls = np.ascontiguousarray(np.broadcast_to(np.asarray(L, dtype=np.float64), (dim,)))
-        v = np.ascontiguousarray(verts, dtype=np.float64).reshape(-1, dim)
+        if radius is not None:
+            v = np.array([float(radius)] * dim, dtype=np.float64)
+            nv = 0
+        else:
+            v = np.ascontiguousarray(verts, dtype=np.float64).reshape(-1, dim)
+            nv = v.shape[0]
         self.verts = v.copy()
         self.L = Ls.copy()
-        rc = lib().or_init(self._buf, self.dim, _dp(Ls), _dp(v), v.shape[0], float(w_min))
+        rc = lib().or_init(self._buf, self.dim, _dp(Ls), _dp(v), nv, float(w_min))
         if rc != 0:
             raise ValueError(f"oracle or_init failed ({rc})")
         self.seed = 0
         self.nselect = 0
+
+    def sdf_histogram(self, pos, x_max, nbins):
+        """Counts of pair scale factors x* = 1 - sigma / r in [0, x_max), nbins
+        bins, every unordered pair once (disks / spheres only)."""
+        p = np.ascontiguousarray(pos, dtype=np.float64)
+        h = np.zeros(int(nbins), dtype=np.uint64)
+        rc = lib().or_sdf_histogram(self.ptr, p.shape[0], _dp(p), float(x_max), int(nbins),
+                                    h.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)))
+        if rc != 0:
+            raise ValueError("or_sdf_histogram failed")
+        return h
 
     @property
     def ptr(self):

@@ -1,0 +1,67 @@
+"""Oracle pins for round particles (hard disks and spheres, the paper's
+validation systems) and the scale-distribution pressure histogram.
+
+Pins: the contact definition (touching counts as overlap), an O(N^2) numpy
+distance check of sweeps, and closed forms of the histogram on lattices
+whose pair distances are known exactly."""
+import math
+
+import numpy as np
+
+from oracle import oracle as orc
+from paper_1509_04692_gb300 import inputs
+
+
+def test_disk_and_sphere_contact():
+    d2 = orc.OracleSystem(2, [20.0, 20.0], radius=0.5)
+    z = np.tile([1.0, 0.0], (4, 1))
+    D = np.array([[1.0, 0.0], [0.0, -1.0], [np.nextafter(1.0, 2.0), 0.0], [0.6, 0.8]])
+    assert list(d2.overlap(D, z, z)) == [1, 1, 0, 1]      # 0.6^2 + 0.8^2 rounds to exactly 1
+    d3 = orc.OracleSystem(3, [20.0] * 3, radius=0.25)
+    q = np.tile([1.0, 0.0, 0.0, 0.0], (3, 1))
+    D3 = np.array([[0.5, 0.0, 0.0], [0.3, 0.3, 0.3], [0.3, 0.3, 0.2]])
+    assert list(d3.overlap(D3, q, q)) == [1, 0, 1]         # 0.27 > 0.25, 0.22 < 0.25
+
+
+def test_disk_sweeps_never_overlap():
+    rng = np.random.default_rng(3)
+    N, phi = 400, 0.60
+    L = math.sqrt(N * math.pi * 0.25 / phi)
+    pos, ori, dmin = inputs.triangular_lattice(N, L, rng)
+    assert dmin >= 1.0
+    o = orc.OracleSystem(2, [L, L], radius=0.5)
+    o.set_moves(0.15, 0.0, 4, 11)
+    c = o.sweep(pos, ori, 0, 60)
+    assert c[0] > 0 and c[1] > 0
+    D = pos[:, None, :] - pos[None, :, :]
+    D -= L * np.round(D / L)
+    r2 = (D ** 2).sum(-1) + np.eye(N) * 10.0
+    assert r2.min() > 1.0                                   # no pair at or inside contact
+
+
+def test_sdf_triangular_lattice_closed_form():
+    # perfect triangular lattice, spacing a: 3N nearest-neighbour pairs at
+    # distance a (x* = 1 - sigma / a), the next shell at sqrt(3) a is beyond x_max
+    nx, ny, a = 16, 16, 1.04
+    L = np.array([nx * a, ny * a * math.sqrt(3.0) / 2.0])
+    j, i = np.divmod(np.arange(nx * ny), nx)
+    pos = np.stack([(i + 0.5 * (j % 2)) * a, j * a * math.sqrt(3.0) / 2.0], 1)
+    o = orc.OracleSystem(2, L, radius=0.5)
+    x_max, nbins = 0.1, 50
+    h = o.sdf_histogram(pos, x_max, nbins)
+    xs = 1.0 - 1.0 / a
+    b = int(xs * (nbins / x_max))
+    assert h[b] == 3 * nx * ny and h.sum() == 3 * nx * ny
+
+
+def test_sdf_pairs_and_spheres():
+    o = orc.OracleSystem(3, [10.0] * 3, radius=0.5)
+    # three spheres: pair distances 1.01, 1.05 and beyond range
+    pos = np.array([[1.0, 1.0, 1.0], [2.01, 1.0, 1.0], [1.0, 2.05, 1.0]])
+    h = o.sdf_histogram(pos, 0.1, 100)
+    expect = np.zeros(100, dtype=np.uint64)
+    for r in (1.01, 1.05):
+        expect[int((1.0 - 1.0 / r) * 1000.0)] += 1
+    r3 = math.hypot(1.01, 1.05)
+    assert 1.0 - 1.0 / r3 > 0.1
+    assert np.array_equal(h, expect)
