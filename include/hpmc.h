@@ -80,7 +80,10 @@ typedef struct {
  *   dim       2 or 3.
  *   verts     nv*dim doubles, the shape in its local frame (2D: convex and
  *             counter-clockwise; 3D: the vertices of a convex polyhedron).
- *   nv        3..16 (2D) or 4..32 (3D).
+ *   nv        3..16 (2D) or 4..32 (3D); or 0: hard disks (2D) / spheres
+ *             (3D) of radius verts[0] (the paper's validation systems,
+ *             Sec. 4), which overlap when their centres are at most one
+ *             diameter apart.
  *   w_min     floor on the cell width (0 = the circumdiameter, the paper's
  *             minimum, Sec. 2.2.1).
  *   reps      R replica descriptors (see above).
@@ -192,6 +195,22 @@ int hpmc_profile_sweeps(hpmc_t h, uint32_t n, void* stream, double* ms_rebuild, 
  * Returns HPMC_ERR_NOT_READY in ordinary builds.  Synchronous.
  */
 int hpmc_trace_read(hpmc_t h, uint64_t* out, uint32_t max_warps, uint32_t* n_points);
+
+/*
+ * hpmc_sdf -- pressure sampling by the scale distribution (Sec. 4; disks and
+ * spheres, nv = 0): for every pair of replica r (r = -1: all replicas) whose
+ * scale factor x* = 1 - 2R/|D| (the uniform compression of positions by
+ * 1 - x that makes the pair touch) lies in [0, x_max), adds one to
+ * hist[(int)(x* * nbins / x_max)].  hist is a caller-owned host array of
+ * nbins uint64 that is accumulated, not cleared, so successive samples add
+ * up.  beta P / rho = 1 + h(0) / (dim N), h(x) the pair count per unit x
+ * per configuration extrapolated to x = 0.  Requires 0 < x_max < 1,
+ * 1 <= nbins <= 2^20 and 2R / (1 - x_max) <= the cell width on every axis
+ * (w_min at creation sets it); INVALID_ARG otherwise, and for shaped
+ * particles.  Rebuilds the cell list (the trajectory is unaffected).
+ * Synchronous.
+ */
+int hpmc_sdf(hpmc_t h, int32_t r, double x_max, uint32_t nbins, uint64_t* hist);
 
 /*
  * hpmc_pair_test -- evaluate the overlap test on n independent pairs on the

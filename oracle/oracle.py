@@ -113,6 +113,8 @@ class OracleSystem:
         self.dim = int(dim)
         self._buf = ctypes.create_string_buffer(lib().or_system_size())
         Ls = np.ascontiguousarray(np.broadcast_to(np.asarray(L, dtype=np.float64), (dim,)))
+        if radius is None and verts is not None and np.ndim(verts) == 0:
+            radius = float(verts)              # a scalar is the radius of disks / spheres
         if radius is not None:
             v = np.array([float(radius)] * dim, dtype=np.float64)
             nv = 0

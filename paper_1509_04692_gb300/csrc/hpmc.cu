@@ -52,6 +52,8 @@ struct hpmc_batch {
     double w_min = 0.0;
     double Rc = 0.0, rc2 = 0.0;
     double rin = 0.0;                    // inradius about the local origin
+    unsigned long long* sdf_hist = nullptr;   // device histogram of hpmc_sdf
+    uint32_t sdf_cap = 0;
     uint32_t R = 0, ntot = 0, ctot = 0, ntiles = 0;
     std::vector<HostRep> hr;
     std::vector<Rep> reps;
@@ -613,6 +615,7 @@ int hpmc_destroy(hpmc_t h)
     invalidate_graph(h);
     if (h->graph_stream) cudaStreamDestroy(h->graph_stream);
     for (void* p : h->allocs) cudaFree(p);
+    if (h->sdf_hist) cudaFree(h->sdf_hist);
     delete h;
     return 0;
 }
@@ -771,6 +774,42 @@ int hpmc_check_overlaps(hpmc_t h, int32_t r, uint64_t* n_pairs)
     unsigned long long n = 0;
     CK(cudaMemcpy(&n, h->check_out, sizeof(n), cudaMemcpyDeviceToHost));
     *n_pairs = n;
+    return read_error(h);
+}
+
+int hpmc_sdf(hpmc_t h, int32_t r, double x_max, uint32_t nbins, uint64_t* hist)
+{
+    if (!h || !hist || r < -1 || r >= (int32_t)h->R) return HPMC_ERR_INVALID_ARG;
+    if (h->nv != 0 || !(x_max > 0.0) || !(x_max < 1.0) || nbins == 0 || nbins > (1u << 20))
+        return HPMC_ERR_INVALID_ARG;
+    const double sigma = h->Rc + h->Rc;
+    const double rmax = sigma / (1.0 - x_max);
+    for (uint32_t q = 0; q < h->R; ++q) {
+        if (r >= 0 && (uint32_t)r != q) continue;
+        for (int a = 0; a < h->dim; ++a)
+            if (rmax > h->reps[q].w[a]) return HPMC_ERR_INVALID_ARG;
+    }
+    CK(cudaDeviceSynchronize());
+    if (h->sdf_cap < nbins) {
+        if (h->sdf_hist) cudaFree(h->sdf_hist);
+        h->sdf_hist = nullptr;
+        h->sdf_cap = 0;
+        CK(cudaMalloc(&h->sdf_hist, sizeof(unsigned long long) * nbins));
+        h->sdf_cap = nbins;
+    }
+    // a cell list with a zero shift, then every pair of stencil neighbours
+    CK(cudaMemset(h->dv.shift, 0, sizeof(double) * 3 * h->R));
+    int rc = enqueue_rebuild(h, 0, false);
+    if (rc) return rc;
+    h->cur ^= 1;
+    CK(cudaMemset(h->sdf_hist, 0, sizeof(unsigned long long) * nbins));
+    const int T = 128;
+    k_sdf<<<(h->ntot + T - 1) / T, T>>>(h->dv, h->cur, sigma, x_max, (double)nbins / x_max, nbins, r,
+                                        h->sdf_hist);
+    CK(cudaGetLastError());
+    std::vector<unsigned long long> got(nbins);
+    CK(cudaMemcpy(got.data(), h->sdf_hist, sizeof(unsigned long long) * nbins, cudaMemcpyDeviceToHost));
+    for (uint32_t b = 0; b < nbins; ++b) hist[b] += got[b];
     return read_error(h);
 }
 

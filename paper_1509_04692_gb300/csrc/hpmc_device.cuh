@@ -311,6 +311,7 @@ template <int NV>
 __device__ __forceinline__ bool overlap2d64(const Shape2& sh, double Dx, double Dy,
                                             double cA, double sA, double cB, double sB)
 {
+    if (NV == 0 && sh.round) return (Dx * Dx + Dy * Dy) <= sh.rc2;      // disks
     const double cr = cA * cB + sA * sB;
     const double sr = cA * sB - sA * cB;
     const double lx = cA * Dx + sA * Dy;
@@ -501,6 +502,10 @@ template <int NV>
 __device__ __noinline__ bool overlap3d64(const Shape3& sh, const double D[3], const double qA[4],
                                          const double qB[4], int* iters)
 {
+    if (NV == 0 && sh.round) {                                          // spheres
+        *iters = 0;
+        return ((D[0] * D[0] + D[1] * D[1]) + D[2] * D[2]) <= sh.rc2;
+    }
     const double qAc[4] = { qA[0], -qA[1], -qA[2], -qA[3] };
     double qr[4], l[3];
     qmul(qAc, qB, qr);

@@ -223,6 +223,50 @@ __global__ void k_place(Dev dv, int cur)
     place_at(dv, cur, i, t, dv.rep_of[i], c, b + rank);
 }
 
+// ------------------------------------------------ pressure (disks, spheres)
+// Scale-distribution histogram (Sec. 4): every unordered pair of stencil
+// neighbours (the higher tag counts it) with 0 <= x* = 1 - sigma / r < x_max
+// adds one to bin (int)(x* * scale), scale = nbins / x_max.  The host checks
+// that sigma / (1 - x_max) fits in a cell, so the stencil holds every such pair.
+__global__ void k_sdf(Dev dv, int b, double sigma, double x_max, double scale, uint32_t nbins, int32_t only_r,
+                      unsigned long long* hist)
+{
+    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= dv.ntot) return;
+    const uint32_t r = dv.rep_of[i];
+    if (only_r >= 0 && (int32_t)r != only_r) return;
+    const Rep& rp = dv.reps[r];
+    const Bufs& B = dv.buf[b];
+    const int d3 = dv.dim == 3;
+    const int ix = cell_axis(B.px[i], dv.shift[3 * r], rp.L[0], rp.inv_w[0], rp.nc[0]);
+    const int iy = cell_axis(B.py[i], dv.shift[3 * r + 1], rp.L[1], rp.inv_w[1], rp.nc[1]);
+    const int iz = d3 ? cell_axis(B.pz[i], dv.shift[3 * r + 2], rp.L[2], rp.inv_w[2], rp.nc[2]) : 0;
+    const uint32_t ti = B.tag[i];
+    for (int oz = -d3; oz <= d3; ++oz)
+        for (int oy = -1; oy <= 1; ++oy)
+            for (int ox = -1; ox <= 1; ++ox) {
+                const int jx = (ix + ox + rp.nc[0]) % rp.nc[0];
+                const int jy = (iy + oy + rp.nc[1]) % rp.nc[1];
+                const int jz = d3 ? (iz + oz + rp.nc[2]) % rp.nc[2] : 0;
+                const uint32_t cc = rp.cbase + (uint32_t)jx +
+                                    (uint32_t)rp.nc[0] * ((uint32_t)jy + (uint32_t)rp.nc[1] * (uint32_t)jz);
+                for (uint32_t e = dv.start[cc]; e < dv.start[cc + 1]; ++e) {
+                    if (B.tag[e] <= ti) continue;
+                    const double Dx = min_image(B.px[e] - B.px[i], rp.L[0], rp.halfL[0]);
+                    const double Dy = min_image(B.py[e] - B.py[i], rp.L[1], rp.halfL[1]);
+                    double q2 = Dx * Dx + Dy * Dy;
+                    if (d3) {
+                        const double Dz = min_image(B.pz[e] - B.pz[i], rp.L[2], rp.halfL[2]);
+                        q2 = q2 + Dz * Dz;
+                    }
+                    const double x = 1.0 - sigma / sqrt(q2);
+                    if (!(x >= 0.0) || !(x < x_max)) continue;
+                    const int bin = (int)(x * scale);
+                    if (bin < (int)nbins) atomicAdd(hist + bin, 1ull);
+                }
+            }
+}
+
 // ---------------------------------------------------------------- checks
 // Count overlapping pairs (each unordered pair once: the lower tag counts
 // it) of the sorted buffer `b` with the FP64 contract predicate.

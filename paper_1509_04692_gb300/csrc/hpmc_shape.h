@@ -17,6 +17,19 @@ inline int build_shapes(int dim, const double* verts, uint32_t nv, Shape2& s2, S
                         double& rc2)
 {
     if (dim != 2 && dim != 3) return HPMC_ERR_INVALID_ARG;
+    if (nv == 0) {
+        // disks / spheres of radius verts[0]: the shape is its circumsphere
+        if (!verts || !std::isfinite(verts[0]) || !(verts[0] > 0.0)) return HPMC_ERR_INVALID_ARG;
+        Rc = verts[0];
+        const double dcut = Rc + Rc;
+        rc2 = dcut * dcut;
+        s2 = Shape2{};
+        s3 = Shape3{};
+        s2.round = s3.round = 1;
+        s2.rc2 = s3.rc2 = rc2;
+        s2.frc2 = s3.frc2 = (float)rc2;
+        return 0;
+    }
     if (dim == 2 && (nv < 3 || nv > (uint32_t)kMaxV2)) return HPMC_ERR_INVALID_ARG;
     if (dim == 3 && (nv < 4 || nv > (uint32_t)kMaxV3)) return HPMC_ERR_INVALID_ARG;
     if (!verts) return HPMC_ERR_INVALID_ARG;
@@ -91,6 +104,7 @@ inline int build_shapes(int dim, const double* verts, uint32_t nv, Shape2& s2, S
 // 3D facets are found by brute force over vertex triples (nv <= 32).
 inline double shape_inradius(int dim, const double* v, uint32_t nv)
 {
+    if (nv == 0) return v[0];                 // disk / sphere
     double best = INFINITY;
     if (dim == 2) {
         for (uint32_t k = 0; k < nv; ++k) {

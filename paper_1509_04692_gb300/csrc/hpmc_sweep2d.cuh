@@ -467,7 +467,7 @@ k_set2d(Dev dv, Shape2 sh, int nxt, int sigma, const uint32_t* __restrict__ item
                     // arrive by shuffles from the survivor's lane
                     bool ovl = false;
                     if (status == 1) {
-                        const int seg = 2 * nvv;
+                        const int seg = nvv > 0 ? 2 * nvv : 2;
                         const int ppr = 32 / seg;
                         const int p = lane / seg, wi = lane - (lane / seg) * seg;
                         const int hf = wi / nvv, axk = wi - hf * nvv;
@@ -515,6 +515,10 @@ k_set2d(Dev dv, Shape2 sh, int nxt, int sigma, const uint32_t* __restrict__ item
                                     }
                                 }
                             }
+                            // disks: a kept pair (|D|^2 <= (2R)^2) is the overlap
+                            const bool rov = NV == 0 && sh.round && keep;
+                            if (rov) { keep = false; c_chk += 1; }
+                            if (__any_sync(FULL, rov)) ovl = true;
                             unsigned bal = __ballot_sync(FULL, keep);
 #pragma unroll 1
                             while (bal != 0u && !ovl) {
@@ -626,6 +630,11 @@ k_set2d(Dev dv, Shape2 sh, int nxt, int sigma, const uint32_t* __restrict__ item
                                 }
                             }
                         }
+                        if (NV == 0 && sh.round && keep) {       // disks: kept = overlap
+                            keep = false;
+                            c_chk += 1;
+                            atomicOr(&ws.ovmask, 1u << grp);
+                        }
                         const unsigned bal = __ballot_sync(FULL, keep);
                         if (keep) {
                             const int pos = qn + __popc(bal & ((1u << lane) - 1u));
@@ -636,12 +645,12 @@ k_set2d(Dev dv, Shape2 sh, int nxt, int sigma, const uint32_t* __restrict__ item
                         qn += __popc(bal);
                         const bool any_live = __any_sync(FULL, live) != 0;
                         __syncwarp();
-                        const int per_round = (LAT && F32) ? 32 / (2 * nvv) : 32;
+                        const int per_round = (LAT && F32) ? 32 / (nvv > 0 ? 2 * nvv : 2) : 32;
                         while (qn >= 32 || (!any_live && qn > 0)) {
                             const int np = qn < per_round ? qn : per_round;
                             if (LAT && F32) {
                                 // one separating axis of one pair per lane
-                                const int seg = 2 * nvv;
+                                const int seg = nvv > 0 ? 2 * nvv : 2;
                                 const int p = lane / seg;
                                 const int wi = lane - p * seg;
                                 const int hf = wi / nvv, axk = wi - hf * nvv;

@@ -436,6 +436,10 @@ k_set3d(Dev dv, Shape3 sh, int nxt, int sigma, const uint32_t* __restrict__ item
                             }
                         }
                     }
+                    if (NV == 0 && sh.round && keep) {           // spheres: kept = overlap
+                        keep = false;
+                        ins = true;
+                    }
                     if (ins) {
                         c_chk += 1;
                         atomicOr(&ws.ovmask, 1u << grp);

@@ -75,6 +75,7 @@ struct Rep {
 // Polygon constants (kernel parameter, passed by value).
 struct Shape2 {
     int nv;
+    int round;               // 1: hard disk (nv = 0), overlap iff |D|^2 <= rc2
     double vx[kMaxV2], vy[kMaxV2];
     double nx[kMaxV2], ny[kMaxV2];
     double alo[kMaxV2], ahi[kMaxV2];
@@ -86,6 +87,7 @@ struct Shape2 {
 // Polyhedron constants (kernel parameter, passed by value).
 struct Shape3 {
     int nv;
+    int round;               // 1: hard sphere (nv = 0), overlap iff |D|^2 <= rc2
     double v[kMaxV3][3];
     float fv[kMaxV3][3];
     double rc2;

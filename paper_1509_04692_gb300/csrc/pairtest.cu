@@ -24,6 +24,7 @@ __global__ void k_pairs2d(Shape2 sh, float E, uint32_t n, const double* D, const
     const double dx = D[2 * i], dy = D[2 * i + 1];
     const double ca = qA[2 * i], sa = qA[2 * i + 1], cb = qB[2 * i], sb = qB[2 * i + 1];
     o64[i] = overlap2d64<0>(sh, dx, dy, ca, sa, cb, sb) ? 1 : 0;
+    if (sh.round) { o32[i] = 2; return; }            // disks: the set kernels' cull decides
     const int v = sat32<0>(sh, E, (float)dx, (float)dy, (float)ca, (float)sa, (float)cb, (float)sb);
     o32[i] = v == 1 ? 1 : (v == 0 ? 0 : 2);
 }
@@ -38,6 +39,7 @@ __global__ void k_pairs3d(Shape3 sh, float e_pb, float e_va, float tau, uint32_t
     const double b[4] = { qB[4 * i], qB[4 * i + 1], qB[4 * i + 2], qB[4 * i + 3] };
     int it = 0;
     o64[i] = overlap3d64<0>(sh, d, a, b, &it) ? 1 : 0;
+    if (sh.round) { o32[i] = 2; return; }            // spheres: the set kernels' cull decides
     const float4 fa = make_float4((float)a[0], (float)a[1], (float)a[2], (float)a[3]);
     const float4 fb = make_float4((float)b[0], (float)b[1], (float)b[2], (float)b[3]);
     const int v = gjk32_cert<0>(sh, (float)d[0], (float)d[1], (float)d[2], fa, fb, e_pb, e_va, tau);

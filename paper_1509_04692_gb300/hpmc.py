@@ -31,7 +31,7 @@ EXPORTS = [
     "hpmc_reset_counters", "hpmc_check_overlaps", "hpmc_get_state", "hpmc_set_state",
     "hpmc_run_host", "hpmc_autotune", "hpmc_geometry", "hpmc_launches_per_sweep",
     "hpmc_filter_margins", "hpmc_strerror", "hpmc_profile_sweeps", "hpmc_count_overlaps_noalloc",
-    "hpmc_trace_read", "hpmc_pair_test",
+    "hpmc_trace_read", "hpmc_pair_test", "hpmc_sdf",
 ]
 
 
@@ -92,6 +92,7 @@ def _load():
         "hpmc_trace_read": [vp, ctypes.POINTER(u64), u32, ctypes.POINTER(u32)],
         "hpmc_pair_test": [ctypes.c_int, dp, u32, u32, dp, dp, dp, ctypes.POINTER(ctypes.c_int32),
                            ctypes.POINTER(ctypes.c_int32)],
+        "hpmc_sdf": [ctypes.c_void_p, ctypes.c_int32, ctypes.c_double, u32, ctypes.POINTER(ctypes.c_uint64)],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -132,7 +133,10 @@ class Batch:
         """replicas: list of dicts with keys N, box, pos, orient, seed, d, a, nselect."""
         self.dim = int(dim)
         self.qd = 2 if self.dim == 2 else 4
-        v = _c64(verts).reshape(-1, self.dim)
+        # a scalar is the radius of disks (2D) / spheres (3D): nv = 0
+        round_ = np.ndim(verts) == 0
+        v = np.array([float(verts)]) if round_ else _c64(verts).reshape(-1, self.dim)
+        nv = 0 if round_ else v.shape[0]
         self._keep = []
         descs = (ReplicaDesc * len(replicas))()
         self.N = []
@@ -151,7 +155,7 @@ class Batch:
             descs[i].nselect = int(r.get("nselect", 4))
             self.N.append(pos.shape[0])
         h = ctypes.c_void_p()
-        _ck(_lib.hpmc_batch_create(self.dim, _dp(v), v.shape[0], float(w_min), len(replicas), descs,
+        _ck(_lib.hpmc_batch_create(self.dim, _dp(v), nv, float(w_min), len(replicas), descs,
                                    ctypes.byref(h)), "hpmc_batch_create")
         self.h = h
         self.R = len(replicas)
@@ -229,6 +233,15 @@ class Batch:
                                ctypes.byref(c), ctypes.c_void_p(int(stream) if stream else None)),
             "hpmc_run_host")
         return c.as_dict()
+
+    def sdf(self, x_max, nbins, r=-1, hist=None):
+        """Add the current configuration's scale-factor histogram (disks /
+        spheres) to ``hist`` (uint64[nbins], created when None); returns it."""
+        if hist is None:
+            hist = np.zeros(int(nbins), dtype=np.uint64)
+        _ck(_lib.hpmc_sdf(self.h, int(r), float(x_max), int(nbins),
+                          hist.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64))), "hpmc_sdf")
+        return hist
 
     def autotune(self, n_trial=8):
         g = ctypes.c_int()

@@ -293,3 +293,35 @@ DODECA_A = 0.087
 def dodecahedra32000(seed: int = 42) -> System:
     """32000 unit-volume regular dodecahedra, volume fraction 0.50."""
     return dodecahedron_system(20, 0.50, seed, d=DODECA_D, a=DODECA_A, nselect=4)
+
+
+def disk_system(N: int, phi: float, seed: int, sigma: float = 1.0, d: float = 0.1, nselect: int = 4,
+                w_min: float = 0.0) -> System:
+    """N hard disks of diameter sigma at area fraction phi on a triangular
+    lattice (site distance >= sigma up to phi = 0.9069); orientations (1, 0)
+    (carried, irrelevant to the overlap).  verts is the radius (a scalar)."""
+    area = math.pi * 0.25 * sigma * sigma
+    L = box_length(N, area, phi, 2)
+    rng = np.random.default_rng(seed)
+    pos, ori, dmin = triangular_lattice(N, L, rng, aligned=True)
+    if dmin < sigma:
+        raise ValueError(f"phi={phi} too dense for an overlap-free lattice start")
+    return System(name=f"disks N={N} phi={phi}", dim=2, verts=np.array(0.5 * sigma), L=np.array([L, L]),
+                  pos=pos, orient=ori, phi=phi, seed=seed, d=d, a=0.0, nselect=nselect, w_min=w_min,
+                  notes={"init": "triangular lattice", "site_distance": dmin})
+
+
+def sphere_system(n: int, phi: float, seed: int, sigma: float = 1.0, d: float = 0.1, nselect: int = 4,
+                  w_min: float = 0.0) -> System:
+    """4 n^3 hard spheres of diameter sigma at volume fraction phi on an FCC
+    lattice (nearest-site distance >= sigma up to phi = 0.7405)."""
+    vol = math.pi / 6.0 * sigma ** 3
+    cell = (4.0 * vol / phi) ** (1.0 / 3.0)
+    if cell / math.sqrt(2.0) < sigma:
+        raise ValueError(f"phi={phi} too dense for an overlap-free FCC start")
+    rng = np.random.default_rng(seed)
+    pos, q = fcc_lattice(n, cell, rng)
+    L = n * cell
+    return System(name=f"spheres N={pos.shape[0]} phi={phi}", dim=3, verts=np.array(0.5 * sigma),
+                  L=np.array([L, L, L]), pos=pos, orient=q, phi=phi, seed=seed, d=d, a=0.0,
+                  nselect=nselect, w_min=w_min, notes={"init": "FCC lattice"})

@@ -1,0 +1,94 @@
+"""Hard disks and spheres (the paper's validation systems, Sec. 4) on the
+GPU: trajectories bit for bit against the oracle in both precision forms,
+the scale-distribution histogram count for count, and the pressure of a
+dilute disk fluid against the virial series."""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import oracle as orc
+from paper_1509_04692_gb300 import inputs, pressure
+
+pytestmark = pytest.mark.gpu
+
+hpmc = pytest.importorskip("paper_1509_04692_gb300.hpmc")
+
+
+def _oracle(s, n):
+    o = orc.OracleSystem(s.dim, s.L, s.verts, w_min=s.w_min)
+    o.set_moves(s.d, s.a, s.nselect, s.seed)
+    p, q = s.pos.copy(), s.orient.copy()
+    c = o.sweep(p, q, 0, n)
+    return o, p, q, [int(x) for x in c[:3]]
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+@pytest.mark.parametrize("lanes", [1, 8, 32])
+def test_disks_bit_exact(mode, lanes):
+    s = inputs.disk_system(1024, 0.60, 5, d=0.12, w_min=1.06)
+    _, rp, rq, rc = _oracle(s, 30)
+    b = hpmc.from_system(s)
+    b.set_precision(mode)
+    b.set_group_size(lanes, 2)
+    b.sweep(30, graph=True)
+    c = b.counters()
+    p, q, sw = b.get_state()
+    assert [c["accept"], c["reject_overlap"], c["reject_boundary"]] == rc
+    assert np.array_equal(p, rp) and np.array_equal(q, rq)
+    assert b.check_overlaps() == 0
+    b.close()
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_spheres_bit_exact(mode):
+    s = inputs.sphere_system(6, 0.40, 7, d=0.15)
+    _, rp, rq, rc = _oracle(s, 20)
+    b = hpmc.from_system(s)
+    b.set_precision(mode)
+    b.set_group_size(8, 2)
+    b.sweep(20)
+    c = b.counters()
+    p, q, sw = b.get_state()
+    assert [c["accept"], c["reject_overlap"], c["reject_boundary"]] == rc
+    assert np.array_equal(p, rp) and np.array_equal(q, rq)
+    b.close()
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_sdf_histogram_matches_oracle(dim):
+    s = (inputs.disk_system(2048, 0.65, 9, d=0.1, w_min=1.06) if dim == 2
+         else inputs.sphere_system(8, 0.45, 9, d=0.1, w_min=1.06))
+    b = hpmc.from_system(s)
+    b.sweep(25, graph=True)
+    p, q, sw = b.get_state()
+    h = b.sdf(0.05, 40)
+    o = orc.OracleSystem(dim, s.L, s.verts, w_min=s.w_min)
+    ref = o.sdf_histogram(p, 0.05, 40)
+    assert h.sum() > 0 and np.array_equal(h, ref)
+    # sampling leaves the trajectory unchanged
+    b2 = hpmc.from_system(s)
+    b2.sweep(25, graph=True)
+    b2.sweep(10, graph=True)
+    b.sweep(10, graph=True)
+    assert np.array_equal(b.get_state()[0], b2.get_state()[0])
+    b.close()
+    b2.close()
+
+
+def test_dilute_disk_pressure_matches_virial_series():
+    # beta P / rho = 1 + 2 eta + 3.1280 eta^2 + 4.2579 eta^3 + 5.3369 eta^4 (hard-disk virial
+    # coefficients in units of the area fraction eta); at eta = 0.1 the series is converged
+    eta = 0.10
+    s = inputs.disk_system(4096, eta, 3, d=0.5, w_min=1.06)
+    b = hpmc.from_system(s)
+    b.sweep(500, graph=True)                              # melt the lattice
+    hist, n = None, 0
+    for _ in range(400):
+        b.sweep(5, graph=True)
+        hist = b.sdf(0.05, 25, hist=hist)
+        n += 1
+    out = pressure.pressure(hist, n, 0.05, s.N, float(s.L[0] * s.L[1]), 2, deg=2)
+    ref = 1 + 2 * eta + 3.1280 * eta ** 2 + 4.2579 * eta ** 3 + 5.3369 * eta ** 4
+    assert abs(out["beta_P_over_rho"] - ref) < max(0.012, 4 * out["beta_P_over_rho_err"]), (out, ref)
+    b.close()
