@@ -423,6 +423,65 @@ def run_profile(args):
     print(json.dumps(out))
 
 
+def run_validate_pressure(args):
+    """Hard disks at area fraction 0.698 (N = 65536), the paper's NVT
+    validation state point (Sec. 4: P* = beta P sigma^2 = 9.1707(2)): melt
+    the lattice, then sample the scale distribution every `--sample-every`
+    sweeps and extrapolate the pressure (block averages show the drift)."""
+    import torch
+    from paper_1509_04692_gb300 import hpmc, pressure, tune
+    torch.cuda.set_device(0)
+    x_max, nbins = 0.05, 25
+    s = inputs.disk_system(65536, 0.698, 42, d=0.05, w_min=1.06)
+    b = hpmc.from_system(s)
+    b.set_precision(hpmc.HPMC_FP32_FILTERED)
+    t0 = time.time()
+    b.sweep(2000, graph=True)
+    p0, q0, sw0 = b.get_state()
+
+    def pilot(d, a):
+        b.set_state(p0, q0, sw0)
+        b.set_moves(d, 0.0, 4)
+        b.reset_counters()
+        b.sweep(50, graph=True)
+        c = b.counters()
+        return c["accept"] / c["moves"]
+    d, _, acc = tune.tune_scale(pilot, 0.05, 0.05, 0.30, lo=0.1, hi=10.0, iters=10)
+    b.set_state(p0, q0, sw0)
+    b.set_moves(d, 0.0, 4)
+    b.reset_counters()
+    te = time.time()
+    b.sweep(args.validate_pressure, graph=True)              # equilibration
+    b.sync()
+    eq_s = time.time() - te
+    blocks = []
+    hist_all = np.zeros(nbins, dtype=np.uint64)
+    n_all = 0
+    per_block = max(1, args.validate_samples // 5)
+    ts = time.time()
+    for blk in range(5):
+        h = np.zeros(nbins, dtype=np.uint64)
+        for _ in range(per_block):
+            b.sweep(args.sample_every, graph=True)
+            b.sdf(x_max, nbins, hist=h)
+        hist_all += h
+        n_all += per_block
+        blocks.append(pressure.pressure(h, per_block, x_max, s.N, float(s.L[0] * s.L[1]), 2)["P_star"])
+    samp_s = time.time() - ts
+    out = pressure.pressure(hist_all, n_all, x_max, s.N, float(s.L[0] * s.L[1]), 2)
+    c = b.counters()
+    bm = np.array(blocks)
+    print(json.dumps({
+        "validate": "hard disks N=65536 phi=0.698 (paper Sec. 4: P* = 9.1707(2))",
+        "P_star": out["P_star"], "P_star_fit_err": out["P_star_err"],
+        "P_star_blocks": blocks, "P_star_block_sem": float(bm.std(ddof=1) / np.sqrt(len(bm))),
+        "d": d, "acceptance": c["accept"] / max(1, c["moves"]),
+        "equilibration_sweeps": args.validate_pressure, "samples": n_all, "sample_every": args.sample_every,
+        "moves_per_s": c["moves"] / (eq_s + samp_s), "seconds": time.time() - t0,
+        "fp64_rechecks": c["fp64_rechecks"], "overlaps_after": b.check_overlaps()}))
+    b.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--profile-sweeps", type=int, default=0,
@@ -443,11 +502,17 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-cubes", action="store_true")
+    ap.add_argument("--validate-pressure", type=int, default=0,
+                    help="hard-disk pressure validation: equilibration sweeps (then sampling)")
+    ap.add_argument("--validate-samples", type=int, default=2000)
+    ap.add_argument("--sample-every", type=int, default=50)
     ap.add_argument("--no-large", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
-    if args.profile_sweeps:
+    if args.validate_pressure:
+        run_validate_pressure(args)
+    elif args.profile_sweeps:
         run_profile(args)
     elif args.impl == "reference":
         run_reference(args)

@@ -92,3 +92,20 @@ def test_dilute_disk_pressure_matches_virial_series():
     ref = 1 + 2 * eta + 3.1280 * eta ** 2 + 4.2579 * eta ** 3 + 5.3369 * eta ** 4
     assert abs(out["beta_P_over_rho"] - ref) < max(0.012, 4 * out["beta_P_over_rho_err"]), (out, ref)
     b.close()
+
+
+def test_disk_pressure_at_the_papers_state_point():
+    # Sec. 4 / Table 2: 65536 hard disks at area fraction 0.698 have
+    # P* = beta P sigma^2 = 9.1707(2).  A short run (20000 + 10000 sweeps)
+    # gives it to about 0.1%; the tolerance is a few block standard errors.
+    s = inputs.disk_system(65536, 0.698, 42, d=0.143, w_min=1.06)
+    b = hpmc.from_system(s)
+    b.sweep(20000, graph=True)
+    hist = None
+    for _ in range(500):
+        b.sweep(20, graph=True)
+        hist = b.sdf(0.05, 25, hist=hist)
+    out = pressure.pressure(hist, 500, 0.05, s.N, float(s.L[0] * s.L[1]), 2)
+    assert abs(out["P_star"] - 9.1707) < 0.04, out
+    assert b.check_overlaps() == 0
+    b.close()
