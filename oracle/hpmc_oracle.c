@@ -105,6 +105,7 @@ typedef struct {
     double L[3], halfL[3];      /* box lengths (orthorhombic, periodic) */
     int nc[3];                  /* cells per axis (even, >= 4) */
     double w[3], inv_w[3];      /* cell width and nc/L */
+    double wcell_min;           /* max(2R, w_min): the narrowest allowed cell */
     int nv;                     /* vertices of the (single) shape; 0: disk/sphere */
     double v[OR_MAXV][3];       /* local-frame vertices */
     double R;                   /* circumradius */
@@ -149,6 +150,7 @@ int or_init(or_system* s, int dim, const double* L, const double* verts, int nv,
     double dcut = s->R + s->R;
     s->rc2 = dcut * dcut;
     double wmin = dcut > w_min ? dcut : w_min;
+    s->wcell_min = wmin;
     for (int k = 0; k < dim; ++k) {
         if (!(L[k] > 0.0)) return -1;
         s->L[k] = L[k];
@@ -766,6 +768,86 @@ int or_sdf_histogram(const or_system* s, uint32_t N, const double* pos, double x
             if (b < (int)nbins) hist[b] += 1;
         }
     return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Isotropic volume move (NPT ensemble, which the paper runs following      */
+/* Frenkel & Smit).  Readings: one trial V' = V + dV_max (2u - 1); every    */
+/* box length and position scaled by f = (V'/V)^(1/dim) (sqrt / cbrt), a    */
+/* position that rounds onto L' wraps to 0; the cell grid of the trial box */
+/* follows the creation rule (nc = floor(L'/max(2R, w_min)), even, a trial  */
+/* with fewer than 4 cells on an axis is rejected); any overlapping pair    */
+/* rejects; otherwise accept                                                */
+/* when u' < exp(-beta_P (V' - V) + N log(V'/V)).  Stream: key = seed,      */
+/* ctr = (lo32(m), hi32(m), 0, 4 << 24) for the m-th move attempt; u from   */
+/* words (0, 1), u' from words (2, 3).  Returns 1 when accepted.            */
+/* ------------------------------------------------------------------------ */
+int or_box_move(or_system* s, uint32_t N, double* pos, const double* orient, double beta_P, double dV_max,
+                uint64_t m)
+{
+    const int dim = s->dim, qd = (dim == 2) ? 2 : 4;
+    uint32_t key[2] = { (uint32_t)s->seed, (uint32_t)(s->seed >> 32) };
+    uint32_t ctr[4] = { (uint32_t)m, (uint32_t)(m >> 32), 0u, 4u << 24 };
+    uint32_t w[4];
+    or_philox4x32_10(ctr, key, w);
+    const double u1 = or_u53(w[0], w[1]), u2 = or_u53(w[2], w[3]);
+    double V = s->L[0] * s->L[1];
+    if (dim == 3) V = V * s->L[2];
+    const double dV = dV_max * (2.0 * u1 - 1.0);
+    const double Vn = V + dV;
+    if (!(Vn > 0.0)) return 0;
+    const double ratio = Vn / V;
+    const double f = (dim == 2) ? sqrt(ratio) : cbrt(ratio);
+    or_system t = *s;
+    for (int k = 0; k < dim; ++k) {
+        t.L[k] = s->L[k] * f;
+        t.halfL[k] = 0.5 * t.L[k];
+        int n = (int)floor(t.L[k] / s->wcell_min);
+        if (n % 2) n -= 1;
+        if (n < 4) return 0;
+        t.nc[k] = n;
+        t.w[k] = t.L[k] / (double)n;
+        t.inv_w[k] = (double)n / t.L[k];
+    }
+    double* np = (double*)malloc(sizeof(double) * (size_t)N * dim + 8);
+    if (!np) return -3;
+    for (uint32_t i = 0; i < N; ++i)
+        for (int k = 0; k < dim; ++k) {
+            double x = pos[(size_t)i * dim + k] * f;
+            if (x >= t.L[k]) x = x - t.L[k];
+            np[(size_t)i * dim + k] = x;
+        }
+    int overlap = 0;
+    for (uint32_t i = 0; i < N && !overlap; ++i)
+        for (uint32_t j = i + 1; j < N && !overlap; ++j) {
+            double D[3] = { 0, 0, 0 };
+            for (int k = 0; k < dim; ++k)
+                D[k] = or_min_image(np[(size_t)j * dim + k] - np[(size_t)i * dim + k], t.L[k], t.halfL[k]);
+            double q2 = D[0] * D[0] + D[1] * D[1];
+            if (dim == 3) q2 = q2 + D[2] * D[2];
+            if (q2 > t.rc2) continue;
+            if (dim == 2) overlap = or_overlap_2d(&t, D, orient + (size_t)i * qd, orient + (size_t)j * qd);
+            else {
+                int it = 0;
+                overlap = or_overlap_3d(&t, D, orient + (size_t)i * qd, orient + (size_t)j * qd, &it);
+            }
+        }
+    int acc = 0;
+    if (!overlap) {
+        const double arg = -beta_P * dV + (double)N * log(ratio);
+        if (u2 < exp(arg)) acc = 1;
+    }
+    if (acc) {
+        memcpy(pos, np, sizeof(double) * (size_t)N * dim);
+        *s = t;
+    }
+    free(np);
+    return acc;
+}
+
+void or_get_box(const or_system* s, double* L)
+{
+    for (int k = 0; k < 3; ++k) L[k] = s->L[k];
 }
 
 /* Exported geometry for tests */

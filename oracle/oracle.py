@@ -74,6 +74,10 @@ def lib():
             L.or_get_geometry.argtypes = [ctypes.c_void_p, dp, dp, ctypes.POINTER(ctypes.c_int), dp, dp]
             L.or_get_tau.restype = ctypes.c_double
             L.or_get_tau.argtypes = [ctypes.c_void_p]
+            L.or_get_box.argtypes = [ctypes.c_void_p, dp]
+            L.or_box_move.restype = ctypes.c_int
+            L.or_box_move.argtypes = [ctypes.c_void_p, ctypes.c_uint32, dp, dp, ctypes.c_double,
+                                      ctypes.c_double, ctypes.c_uint64]
             L.or_sdf_histogram.restype = ctypes.c_int
             L.or_sdf_histogram.argtypes = [ctypes.c_void_p, ctypes.c_uint32, dp, ctypes.c_double,
                                            ctypes.c_uint32, ctypes.POINTER(ctypes.c_uint64)]
@@ -128,6 +132,22 @@ class OracleSystem:
             raise ValueError(f"oracle or_init failed ({rc})")
         self.seed = 0
         self.nselect = 0
+
+    def box_move(self, pos, orient, beta_P, dV_max, m):
+        """One isotropic volume move (attempt number m) in place; returns 1
+        when accepted (pos and the box are then scaled)."""
+        assert pos.dtype == np.float64 and pos.flags.c_contiguous
+        o = np.ascontiguousarray(orient, dtype=np.float64)
+        rc = lib().or_box_move(self.ptr, pos.shape[0], _dp(pos), _dp(o), float(beta_P), float(dV_max), int(m))
+        if rc < 0:
+            raise RuntimeError("or_box_move failed")
+        return rc
+
+    @property
+    def box(self):
+        L = np.zeros(3)
+        lib().or_get_box(self.ptr, _dp(L))
+        return L[: self.dim].copy()
 
     def sdf_histogram(self, pos, x_max, nbins):
         """Counts of pair scale factors x* = 1 - sigma / r in [0, x_max), nbins
