@@ -197,6 +197,23 @@ int hpmc_profile_sweeps(hpmc_t h, uint32_t n, void* stream, double* ms_rebuild, 
 int hpmc_trace_read(hpmc_t h, uint64_t* out, uint32_t max_warps, uint32_t* n_points);
 
 /*
+ * hpmc_box_move -- one isotropic volume move of replica r (the NPT ensemble,
+ * which the paper runs following Frenkel & Smit): V' = V + dV_max (2u - 1)
+ * with u from the replica's volume-move stream (Philox key = the replica's
+ * seed, counter (lo32(m), hi32(m), 0, 4 << 24) for its m-th attempt; u from
+ * words 0-1, u' from words 2-3); every box length and position scaled by
+ * f = (V'/V)^(1/dim) (a position that rounds onto L' wraps to 0); the cell
+ * grid follows the creation rule for the new box (a trial with fewer than 4
+ * cells on an axis is rejected).  Any overlapping pair rejects; otherwise
+ * the move is accepted when u' < exp(-beta_P (V' - V) + N log(V'/V)) (host
+ * libm).  *accepted receives 1 or 0.  dV_max >= 0.  Synchronous.
+ */
+int hpmc_box_move(hpmc_t h, int32_t r, double beta_P, double dV_max, int* accepted);
+
+/* hpmc_get_box -- the current box lengths of replica r (box[3]; 0 beyond dim). */
+int hpmc_get_box(hpmc_t h, int32_t r, double* box);
+
+/*
  * hpmc_sdf -- pressure sampling by the scale distribution (Sec. 4; disks and
  * spheres, nv = 0): for every pair of replica r (r = -1: all replicas) whose
  * scale factor x* = 1 - 2R/|D| (the uniform compression of positions by

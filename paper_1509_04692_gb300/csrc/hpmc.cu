@@ -41,7 +41,27 @@ struct HostRep {
     uint64_t seed;
     double d, a;
     uint32_t nselect;
+    uint64_t box_moves = 0;   // volume-move attempts (counter of their Philox stream)
 };
+
+// Philox4x32-10 on the host (the volume move draws its two numbers here; the
+// device version is in hpmc_device.cuh): same rounds and Weyl key bumps.
+void philox_host(uint32_t c[4], uint32_t k0, uint32_t k1)
+{
+    for (int r = 0; r < 10; ++r) {
+        if (r) { k0 += 0x9E3779B9u; k1 += 0xBB67AE85u; }
+        const uint64_t p0 = (uint64_t)0xD2511F53u * c[0], p1 = (uint64_t)0xCD9E8D57u * c[2];
+        const uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
+        const uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
+        const uint32_t n0 = hi1 ^ c[1] ^ k0, n2 = hi0 ^ c[3] ^ k1;
+        c[0] = n0; c[1] = lo1; c[2] = n2; c[3] = lo0;
+    }
+}
+
+double u53_host(uint32_t a, uint32_t b)
+{
+    return (double)((((uint64_t)a << 32) | b) >> 11) * 0x1.0p-53;
+}
 
 }  // namespace
 
@@ -52,6 +72,8 @@ struct hpmc_batch {
     double w_min = 0.0;
     double Rc = 0.0, rc2 = 0.0;
     double rin = 0.0;                    // inradius about the local origin
+    uint32_t ctot_cap = 0;               // cells the count / start arrays hold
+    double* bak[3] = { nullptr, nullptr, nullptr };   // positions saved by a volume move
     unsigned long long* sdf_hist = nullptr;   // device histogram of hpmc_sdf
     uint32_t sdf_cap = 0;
     uint32_t R = 0, ntot = 0, ctot = 0, ntiles = 0;
@@ -544,6 +566,7 @@ int hpmc_batch_create(int dim, const double* verts, uint32_t nv, double w_min, u
                 return fail(rc);
         }
     }
+    h->ctot_cap = h->ctot;
     if ((rc = dalloc(h, &dv.count, h->ctot)) || (rc = dalloc(h, &dv.start, (size_t)h->ctot + 1)) ||
         (rc = dalloc(h, &dv.tile_sums, h->ntiles)) || (rc = dalloc(h, &dv.cellid, h->ntot)) ||
         (rc = dalloc(h, &dv.slot, h->ntot)) || (rc = dalloc(h, &dv.tmp_tag, h->ntot)) ||
@@ -811,6 +834,137 @@ int hpmc_sdf(hpmc_t h, int32_t r, double x_max, uint32_t nbins, uint64_t* hist)
     CK(cudaMemcpy(got.data(), h->sdf_hist, sizeof(unsigned long long) * nbins, cudaMemcpyDeviceToHost));
     for (uint32_t b = 0; b < nbins; ++b) hist[b] += got[b];
     return read_error(h);
+}
+
+// Cell offsets, scan tiles and work-item tables after a replica's cell grid
+// changed (volume moves); the count / start arrays grow by doubling.
+int relayout(hpmc_batch* h)
+{
+    uint64_t ctot = 0;
+    for (uint32_t r = 0; r < h->R; ++r) {
+        h->reps[r].cbase = (uint32_t)ctot;
+        ctot += h->reps[r].ncell;
+    }
+    if (ctot > 0x7fffffffull) return HPMC_ERR_INVALID_ARG;
+    Dev& dv = h->dv;
+    if (ctot > h->ctot_cap) {
+        const uint32_t cap = (uint32_t)std::min<uint64_t>(std::max<uint64_t>(ctot, 2ull * h->ctot_cap), 0x7fffffffull);
+        const uint32_t nt = (cap + kScanTile - 1) / kScanTile;
+        int rc;
+        if ((rc = dalloc(h, &dv.count, cap)) || (rc = dalloc(h, &dv.start, (size_t)cap + 1)) ||
+            (rc = dalloc(h, &dv.tile_sums, nt)))
+            return rc;
+        h->ctot_cap = cap;
+    }
+    h->ctot = (uint32_t)ctot;
+    h->ntiles = (h->ctot + kScanTile - 1) / kScanTile;
+    dv.ctot = h->ctot;
+    std::vector<uint32_t> tab;
+    build_item_tables(h, tab);
+    const uint32_t nt = h->ntot;
+    CK(cudaMemcpy(h->item_base_dev, tab.data(), sizeof(uint32_t) * tab.size(), cudaMemcpyHostToDevice));
+    CK(cudaMemset(dv.count, 0, sizeof(uint32_t) * h->ctot));
+    CK(cudaMemcpy(dv.start + h->ctot, &nt, sizeof(uint32_t), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy((void*)dv.reps, h->reps.data(), sizeof(Rep) * h->R, cudaMemcpyHostToDevice));
+    invalidate_graph(h);
+    return 0;
+}
+
+// Positions of replica r (slots [pbase, pbase + n) of buffer b) scaled by f,
+// wrapped onto [0, L') when the product rounds onto L'.
+__global__ void k_scale(Dev dv, int b, uint32_t pbase, uint32_t n, double f, double L0, double L1, double L2)
+{
+    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const Bufs& B = dv.buf[b];
+    const uint32_t k = pbase + i;
+    double x = B.px[k] * f;
+    if (x >= L0) x = x - L0;
+    B.px[k] = x;
+    double y = B.py[k] * f;
+    if (y >= L1) y = y - L1;
+    B.py[k] = y;
+    if (dv.dim == 3) {
+        double z = B.pz[k] * f;
+        if (z >= L2) z = z - L2;
+        B.pz[k] = z;
+    }
+}
+
+int hpmc_box_move(hpmc_t h, int32_t r, double beta_P, double dV_max, int* accepted)
+{
+    if (!h || !accepted || r < 0 || r >= (int32_t)h->R) return HPMC_ERR_INVALID_ARG;
+    if (!is_finite(beta_P) || !is_finite(dV_max) || dV_max < 0.0) return HPMC_ERR_INVALID_ARG;
+    *accepted = 0;
+    CK(cudaDeviceSynchronize());
+    HostRep& hr = h->hr[r];
+    const int dim = h->dim;
+    // the two numbers of attempt m: key = seed, ctr = (lo32(m), hi32(m), 0, 4 << 24)
+    const uint64_t m = hr.box_moves++;
+    uint32_t c[4] = { (uint32_t)m, (uint32_t)(m >> 32), 0u, 4u << 24 };
+    philox_host(c, (uint32_t)hr.seed, (uint32_t)(hr.seed >> 32));
+    const double u1 = u53_host(c[0], c[1]), u2 = u53_host(c[2], c[3]);
+    double V = hr.L[0] * hr.L[1];
+    if (dim == 3) V = V * hr.L[2];
+    const double dV = dV_max * (2.0 * u1 - 1.0);
+    const double Vn = V + dV;
+    if (!(Vn > 0.0)) return 0;
+    const double ratio = Vn / V;
+    const double f = dim == 2 ? std::sqrt(ratio) : std::cbrt(ratio);
+    HostRep trial = hr;
+    for (int a = 0; a < dim; ++a) trial.L[a] = hr.L[a] * f;
+    Rep rp_old = h->reps[r], rp_new = rp_old;
+    if (rep_geometry(h, trial, rp_new)) return 0;      // fewer than 4 cells: rejected
+    rp_new.pbase = rp_old.pbase;
+    const bool grid_changed = rp_new.ncell != rp_old.ncell || rp_new.nc[0] != rp_old.nc[0] ||
+                              rp_new.nc[1] != rp_old.nc[1] || rp_new.nc[2] != rp_old.nc[2];
+    // save the replica's positions, scale them, switch to the trial geometry
+    const uint32_t pb = rp_old.pbase, n = hr.N;
+    const int cur0 = h->cur;
+    Bufs& B = h->dv.buf[cur0];
+    double* src[3] = { B.px, B.py, B.pz };
+    for (int a = 0; a < dim; ++a) {
+        if (!h->bak[a]) {
+            int rc = dalloc(h, &h->bak[a], h->ntot);
+            if (rc) return rc;
+        }
+        CK(cudaMemcpy(h->bak[a] + pb, src[a] + pb, sizeof(double) * n, cudaMemcpyDeviceToDevice));
+    }
+    k_scale<<<(n + 255) / 256, 256>>>(h->dv, cur0, pb, n, f, rp_new.L[0], rp_new.L[1], rp_new.L[2]);
+    CK(cudaGetLastError());
+    h->reps[r] = rp_new;
+    int rc = grid_changed ? relayout(h) : upload_reps(h, 0);
+    if (rc) return rc;
+    // any overlapping pair of the replica rejects (FP64 contract, cell list of the trial box)
+    uint64_t n_ov = 0;
+    rc = hpmc_check_overlaps(h, r, &n_ov);
+    if (rc) return rc;
+    bool acc = false;
+    if (n_ov == 0) {
+        const double arg = -beta_P * dV + (double)n * std::log(ratio);
+        acc = u2 < std::exp(arg);
+    }
+    if (acc) {
+        hr.L[0] = trial.L[0]; hr.L[1] = trial.L[1]; hr.L[2] = trial.L[2];
+        *accepted = 1;
+        return 0;
+    }
+    // rejected: the old buffer (untouched but for the scaled positions) and geometry
+    h->cur = cur0;
+    for (int a = 0; a < dim; ++a)
+        CK(cudaMemcpy(src[a] + pb, h->bak[a] + pb, sizeof(double) * n, cudaMemcpyDeviceToDevice));
+    h->reps[r] = rp_old;
+    rc = grid_changed ? relayout(h) : upload_reps(h, 0);
+    if (rc) return rc;
+    CK(cudaDeviceSynchronize());      // (the next sweep rebuilds the cell list and mirrors)
+    return read_error(h);
+}
+
+int hpmc_get_box(hpmc_t h, int32_t r, double* box)
+{
+    if (!h || !box || r < 0 || r >= (int32_t)h->R) return HPMC_ERR_INVALID_ARG;
+    for (int a = 0; a < 3; ++a) box[a] = a < h->dim ? h->hr[r].L[a] : 0.0;
+    return 0;
 }
 
 int hpmc_get_state(hpmc_t h, int32_t r, double* pos, double* orient, uint64_t* sweep)

@@ -31,7 +31,7 @@ EXPORTS = [
     "hpmc_reset_counters", "hpmc_check_overlaps", "hpmc_get_state", "hpmc_set_state",
     "hpmc_run_host", "hpmc_autotune", "hpmc_geometry", "hpmc_launches_per_sweep",
     "hpmc_filter_margins", "hpmc_strerror", "hpmc_profile_sweeps", "hpmc_count_overlaps_noalloc",
-    "hpmc_trace_read", "hpmc_pair_test", "hpmc_sdf",
+    "hpmc_trace_read", "hpmc_pair_test", "hpmc_sdf", "hpmc_box_move", "hpmc_get_box",
 ]
 
 
@@ -93,6 +93,9 @@ def _load():
         "hpmc_pair_test": [ctypes.c_int, dp, u32, u32, dp, dp, dp, ctypes.POINTER(ctypes.c_int32),
                            ctypes.POINTER(ctypes.c_int32)],
         "hpmc_sdf": [ctypes.c_void_p, ctypes.c_int32, ctypes.c_double, u32, ctypes.POINTER(ctypes.c_uint64)],
+        "hpmc_box_move": [ctypes.c_void_p, ctypes.c_int32, ctypes.c_double, ctypes.c_double,
+                          ctypes.POINTER(ctypes.c_int)],
+        "hpmc_get_box": [ctypes.c_void_p, ctypes.c_int32, dp],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -233,6 +236,18 @@ class Batch:
                                ctypes.byref(c), ctypes.c_void_p(int(stream) if stream else None)),
             "hpmc_run_host")
         return c.as_dict()
+
+    def box_move(self, beta_P, dV_max, r=0):
+        """One isotropic volume move of replica r; True when accepted."""
+        acc = ctypes.c_int()
+        _ck(_lib.hpmc_box_move(self.h, int(r), float(beta_P), float(dV_max), ctypes.byref(acc)),
+            "hpmc_box_move")
+        return bool(acc.value)
+
+    def box(self, r=0):
+        L = np.zeros(3)
+        _ck(_lib.hpmc_get_box(self.h, int(r), _dp(L)), "hpmc_get_box")
+        return L[: self.dim].copy()
 
     def sdf(self, x_max, nbins, r=-1, hist=None):
         """Add the current configuration's scale-factor histogram (disks /
