@@ -482,6 +482,50 @@ def run_validate_pressure(args):
     b.close()
 
 
+def run_efficiency(args):
+    """Sampling efficiency against move size (Sec. 2.1: the diffusion rate in
+    wall-clock time peaks near the acceptance the paper tunes to): the
+    4096-pentagon fluid at area fraction 0.60, d = a scaled together; for each
+    scale, the mean squared displacement after `--efficiency` sweeps divided
+    by the GPU time of those sweeps (CUDA events around the sweeps only)."""
+    import torch
+    from paper_1509_04692_gb300 import hpmc
+    torch.cuda.set_device(0)
+    s = inputs.fluid4096(42)
+    b = hpmc.from_system(s)
+    b.set_precision(hpmc.HPMC_FP32_FILTERED)
+    b.sweep(MELT, graph=True)
+    b.autotune(4)
+    p0, q0, sw0 = b.get_state()
+    rows = []
+    chunk = 20
+    for f in (0.15, 0.25, 0.4, 0.6, 0.8, 1.0, 1.3, 1.7, 2.3, 3.0):
+        b.set_state(p0, q0, sw0)
+        b.set_moves(s.d * f, s.a * f, s.nselect)
+        b.sweep(100, graph=True)                             # settle at this move size
+        b.reset_counters()
+        b.msd_reset()
+        ms = 0.0
+        for _ in range(max(1, args.efficiency // chunk)):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            b.sweep(chunk, graph=True)
+            e1.record()
+            e1.synchronize()
+            ms += e0.elapsed_time(e1)
+            b.msd_update()
+        c = b.counters()
+        msd = b.msd()
+        rows.append({"scale": f, "d": s.d * f, "a": s.a * f, "acceptance": c["accept"] / c["moves"],
+                     "msd": msd, "gpu_s": ms * 1e-3, "msd_per_gpu_s": msd / (ms * 1e-3),
+                     "moves_per_s": c["moves"] / (ms * 1e-3)})
+    best = max(rows, key=lambda r: r["msd_per_gpu_s"])
+    print(json.dumps({"efficiency": "4096 pentagons, area fraction 0.60, d = a scaled together",
+                      "sweeps_per_point": args.efficiency, "rows": rows,
+                      "best_acceptance": best["acceptance"], "best_scale": best["scale"]}))
+    b.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--profile-sweeps", type=int, default=0,
@@ -505,6 +549,8 @@ def main():
     ap.add_argument("--validate-pressure", type=int, default=0,
                     help="hard-disk pressure validation: equilibration sweeps (then sampling)")
     ap.add_argument("--validate-samples", type=int, default=2000)
+    ap.add_argument("--efficiency", type=int, default=0,
+                    help="diffusion per GPU second against move size (sweeps per point)")
     ap.add_argument("--sample-every", type=int, default=50)
     ap.add_argument("--no-large", action="store_true")
     args = ap.parse_args()
@@ -512,6 +558,8 @@ def main():
         args.warmup = 3
     if args.validate_pressure:
         run_validate_pressure(args)
+    elif args.efficiency:
+        run_efficiency(args)
     elif args.profile_sweeps:
         run_profile(args)
     elif args.impl == "reference":

@@ -214,6 +214,34 @@ int hpmc_box_move(hpmc_t h, int32_t r, double beta_P, double dV_max, int* accept
 int hpmc_get_box(hpmc_t h, int32_t r, double* box);
 
 /*
+ * hpmc_tune_moves -- move sizes for a target acceptance ratio (Sec. 2.1: the
+ * paper tunes to a fixed acceptance, then fixes the sizes).  A geometric
+ * bisection over a common factor f in [lo, hi] of replica r's current d and a
+ * (r = -1: every replica, acceptance pooled): each of `iters` pilots runs
+ * n_pilot sweeps from the same saved state; the pilot whose acceptance is
+ * closest to `target` sets the moves.  The configuration, sweep counters
+ * and event counters are restored afterwards, so the trajectory continues
+ * as if no pilot had run.  *d_out, *a_out (replica r, or replica 0 when
+ * r = -1) and *acc_out (may be NULL) receive the result.  Synchronous.
+ */
+int hpmc_tune_moves(hpmc_t h, int32_t r, double target, uint32_t n_pilot, uint32_t iters, double lo,
+                    double hi, double* d_out, double* a_out, double* acc_out);
+
+/*
+ * Mean squared displacement (the paper's efficiency measure for fluids is
+ * the diffusion rate per wall-clock time, Sec. 2.1).  hpmc_msd_reset makes
+ * the current positions the reference; hpmc_msd_update adds every
+ * particle's minimum-image step since the previous call to its unwrapped
+ * displacement (call it often enough that no particle moves half a box in
+ * between; NVT only: a volume move would count as displacement);
+ * hpmc_msd_read returns the mean over replica r's particles (r = -1: all)
+ * of |displacement|^2 (NOT_READY before a reset).  Synchronous.
+ */
+int hpmc_msd_reset(hpmc_t h);
+int hpmc_msd_update(hpmc_t h);
+int hpmc_msd_read(hpmc_t h, int32_t r, double* msd);
+
+/*
  * hpmc_sdf -- pressure sampling by the scale distribution (Sec. 4; disks and
  * spheres, nv = 0): for every pair of replica r (r = -1: all replicas) whose
  * scale factor x* = 1 - 2R/|D| (the uniform compression of positions by

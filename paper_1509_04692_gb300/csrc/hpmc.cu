@@ -74,6 +74,8 @@ struct hpmc_batch {
     double rin = 0.0;                    // inradius about the local origin
     uint32_t ctot_cap = 0;               // cells the count / start arrays hold
     double* bak[3] = { nullptr, nullptr, nullptr };   // positions saved by a volume move
+    double* msd_last = nullptr;          // [ntot * 3] position at the last update, by tag
+    double* msd_acc = nullptr;           // [ntot * 3] unwrapped displacement since the reset
     unsigned long long* sdf_hist = nullptr;   // device histogram of hpmc_sdf
     uint32_t sdf_cap = 0;
     uint32_t R = 0, ntot = 0, ctot = 0, ntiles = 0;
@@ -960,6 +962,76 @@ int hpmc_box_move(hpmc_t h, int32_t r, double beta_P, double dV_max, int* accept
     return read_error(h);
 }
 
+// Mean squared displacement, by particle tag: mode 0 resets (the current
+// positions become the reference), mode 1 adds the minimum-image step since
+// the last call to the unwrapped displacement.
+__global__ void k_msd(Dev dv, int b, int mode, double* last, double* acc)
+{
+    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= dv.ntot) return;
+    const Rep& rp = dv.reps[dv.rep_of[i]];
+    const Bufs& B = dv.buf[b];
+    const size_t g = 3 * (size_t)(rp.pbase + B.tag[i]);
+    const double x[3] = { B.px[i], B.py[i], dv.dim == 3 ? B.pz[i] : 0.0 };
+    for (int a = 0; a < dv.dim; ++a) {
+        if (mode == 0) {
+            acc[g + a] = 0.0;
+        } else {
+            acc[g + a] += min_image(x[a] - last[g + a], rp.L[a], rp.halfL[a]);
+        }
+        last[g + a] = x[a];
+    }
+}
+
+int msd_launch(hpmc_batch* h, int mode)
+{
+    CK(cudaDeviceSynchronize());
+    if (!h->msd_last) {
+        int rc;
+        if ((rc = dalloc(h, &h->msd_last, 3 * (size_t)h->ntot)) || (rc = dalloc(h, &h->msd_acc, 3 * (size_t)h->ntot)))
+            return rc;
+        mode = 0;
+    }
+    k_msd<<<(h->ntot + 255) / 256, 256>>>(h->dv, h->cur, mode, h->msd_last, h->msd_acc);
+    CK(cudaGetLastError());
+    CK(cudaDeviceSynchronize());
+    return read_error(h);
+}
+
+int hpmc_msd_reset(hpmc_t h)
+{
+    if (!h) return HPMC_ERR_INVALID_ARG;
+    return msd_launch(h, 0);
+}
+
+int hpmc_msd_update(hpmc_t h)
+{
+    if (!h) return HPMC_ERR_INVALID_ARG;
+    return msd_launch(h, 1);
+}
+
+int hpmc_msd_read(hpmc_t h, int32_t r, double* msd)
+{
+    if (!h || !msd || r < -1 || r >= (int32_t)h->R) return HPMC_ERR_INVALID_ARG;
+    if (!h->msd_acc) return HPMC_ERR_NOT_READY;
+    CK(cudaDeviceSynchronize());
+    std::vector<double> acc(3 * (size_t)h->ntot);
+    CK(cudaMemcpy(acc.data(), h->msd_acc, sizeof(double) * acc.size(), cudaMemcpyDeviceToHost));
+    double sum = 0.0;
+    uint64_t n = 0;
+    for (uint32_t q = 0; q < h->R; ++q) {
+        if (r >= 0 && (uint32_t)r != q) continue;
+        const uint32_t pb = h->reps[q].pbase;
+        for (uint32_t t = 0; t < h->hr[q].N; ++t) {
+            const double* d = acc.data() + 3 * (size_t)(pb + t);
+            sum += d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+        }
+        n += h->hr[q].N;
+    }
+    *msd = n ? sum / (double)n : 0.0;
+    return 0;
+}
+
 int hpmc_get_box(hpmc_t h, int32_t r, double* box)
 {
     if (!h || !box || r < 0 || r >= (int32_t)h->R) return HPMC_ERR_INVALID_ARG;
@@ -1072,34 +1144,106 @@ int hpmc_run_host(hpmc_t h, const double* pos, const double* orient, uint32_t n,
     return read_error(h);
 }
 
-int hpmc_autotune(hpmc_t h, uint32_t n_trial, int* best_lanes, int* best_warps)
+// The state in tag order, the sweep counters and the event counters, kept on
+// the host while trial runs (tuning) use the device state.
+struct Snapshot {
+    std::vector<double> P, Q;
+    std::vector<uint64_t> sw;
+    std::vector<unsigned long long> cnt;
+};
+
+int snapshot_take(hpmc_batch* h, Snapshot& s)
 {
-    if (!h || n_trial == 0) return HPMC_ERR_INVALID_ARG;
     CK(cudaDeviceSynchronize());
     const int qd = h->dim == 2 ? 2 : 4;
     const size_t N = h->ntot;
-    // save the state in tag order and the sweep counters
-    std::vector<double> P(N * h->dim), Q(N * qd);
-    std::vector<uint64_t> sw(h->R);
-    std::vector<unsigned long long> cnt((size_t)h->R * kNumCounters);
+    s.P.resize(N * h->dim);
+    s.Q.resize(N * qd);
+    s.sw.resize(h->R);
+    s.cnt.resize((size_t)h->R * kNumCounters);
     k_unsort<<<(h->ntot + 255) / 256, 256>>>(h->dv, h->cur);
     CK(cudaDeviceSynchronize());
-    {
-        const Bufs& D = h->dv.buf[h->cur ^ 1];
-        const double* sp[3] = { D.px, D.py, D.pz };
-        const double* sq[4] = { D.q0, D.q1, D.q2, D.q3 };
-        std::vector<double> col(N);
-        for (int a = 0; a < h->dim; ++a) {
-            CK(cudaMemcpy(col.data(), sp[a], N * sizeof(double), cudaMemcpyDeviceToHost));
-            for (size_t i = 0; i < N; ++i) P[i * h->dim + a] = col[i];
-        }
-        for (int a = 0; a < qd; ++a) {
-            CK(cudaMemcpy(col.data(), sq[a], N * sizeof(double), cudaMemcpyDeviceToHost));
-            for (size_t i = 0; i < N; ++i) Q[i * qd + a] = col[i];
-        }
+    const Bufs& D = h->dv.buf[h->cur ^ 1];
+    const double* sp[3] = { D.px, D.py, D.pz };
+    const double* sq[4] = { D.q0, D.q1, D.q2, D.q3 };
+    std::vector<double> col(N);
+    for (int a = 0; a < h->dim; ++a) {
+        CK(cudaMemcpy(col.data(), sp[a], N * sizeof(double), cudaMemcpyDeviceToHost));
+        for (size_t i = 0; i < N; ++i) s.P[i * h->dim + a] = col[i];
     }
-    CK(cudaMemcpy(sw.data(), h->dv.sweep, sizeof(uint64_t) * h->R, cudaMemcpyDeviceToHost));
-    CK(cudaMemcpy(cnt.data(), h->dv.counters, sizeof(unsigned long long) * cnt.size(), cudaMemcpyDeviceToHost));
+    for (int a = 0; a < qd; ++a) {
+        CK(cudaMemcpy(col.data(), sq[a], N * sizeof(double), cudaMemcpyDeviceToHost));
+        for (size_t i = 0; i < N; ++i) s.Q[i * qd + a] = col[i];
+    }
+    CK(cudaMemcpy(s.sw.data(), h->dv.sweep, sizeof(uint64_t) * h->R, cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(s.cnt.data(), h->dv.counters, sizeof(unsigned long long) * s.cnt.size(), cudaMemcpyDeviceToHost));
+    return 0;
+}
+
+int snapshot_restore(hpmc_batch* h, const Snapshot& s)
+{
+    CK(cudaDeviceSynchronize());
+    int rc = upload_all(h, s.P.data(), s.Q.data(), 0);
+    if (rc) return rc;
+    CK(cudaMemcpy(h->dv.sweep, s.sw.data(), sizeof(uint64_t) * h->R, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(h->dv.counters, s.cnt.data(), sizeof(unsigned long long) * s.cnt.size(), cudaMemcpyHostToDevice));
+    CK(cudaDeviceSynchronize());
+    return 0;
+}
+
+int hpmc_tune_moves(hpmc_t h, int32_t r, double target, uint32_t n_pilot, uint32_t iters, double lo,
+                    double hi, double* d_out, double* a_out, double* acc_out)
+{
+    if (!h || r < -1 || r >= (int32_t)h->R || n_pilot == 0 || iters == 0) return HPMC_ERR_INVALID_ARG;
+    if (!(target > 0.0 && target < 1.0) || !(lo > 0.0) || !(hi > lo) || !is_finite(hi)) return HPMC_ERR_INVALID_ARG;
+    Snapshot snap;
+    int rc = snapshot_take(h, snap);
+    if (rc) return rc;
+    const std::vector<HostRep> base = h->hr;
+    auto set_scale = [&](double f) {
+        for (uint32_t q = 0; q < h->R; ++q) {
+            if (r >= 0 && (uint32_t)r != q) continue;
+            int e = hpmc_set_moves(h, (int32_t)q, base[q].d * f, base[q].a * f, base[q].nselect);
+            if (e) return e;
+        }
+        return 0;
+    };
+    // geometric bisection on a common scale of (d, a): acceptance falls as the
+    // moves grow; the best pilot (closest to the target) wins
+    double best_f = 1.0, best_acc = -1.0;
+    for (uint32_t it = 0; it < iters; ++it) {
+        const double mid = std::sqrt(lo * hi);
+        if ((rc = snapshot_restore(h, snap)) || (rc = set_scale(mid))) return rc;
+        CK(cudaMemset(h->dv.counters, 0, sizeof(unsigned long long) * h->R * kNumCounters));
+        if ((rc = hpmc_sweep(h, n_pilot, nullptr))) return rc;
+        hpmc_counters_t c{};
+        if ((rc = hpmc_counters(h, r, &c))) return rc;
+        const double acc = c.moves ? (double)c.accept / (double)c.moves : 0.0;
+        if (best_acc < 0.0 || std::fabs(acc - target) < std::fabs(best_acc - target)) {
+            best_acc = acc;
+            best_f = mid;
+        }
+        if (acc > target) lo = mid;        // moves too small: acceptance too high
+        else hi = mid;
+    }
+    if ((rc = snapshot_restore(h, snap)) || (rc = set_scale(best_f))) return rc;
+    if (r >= 0) {
+        if (d_out) *d_out = h->hr[r].d;
+        if (a_out) *a_out = h->hr[r].a;
+    } else {
+        if (d_out) *d_out = h->hr[0].d;
+        if (a_out) *a_out = h->hr[0].a;
+    }
+    if (acc_out) *acc_out = best_acc;
+    return read_error(h);
+}
+
+int hpmc_autotune(hpmc_t h, uint32_t n_trial, int* best_lanes, int* best_warps)
+{
+    if (!h || n_trial == 0) return HPMC_ERR_INVALID_ARG;
+    Snapshot snap;
+    int rc0 = snapshot_take(h, snap);
+    if (rc0) return rc0;
     const int G0 = h->G, W0 = h->wpb;
     float best_ms = 1e30f;
     int bg = G0, bw = W0;
@@ -1127,13 +1271,8 @@ int hpmc_autotune(hpmc_t h, uint32_t n_trial, int* best_lanes, int* best_warps)
     h->G = bg;
     h->wpb = bw;
     invalidate_graph(h);
-    // restore
-    CK(cudaDeviceSynchronize());
-    int rc = upload_all(h, P.data(), Q.data(), 0);
+    int rc = snapshot_restore(h, snap);
     if (rc) return rc;
-    CK(cudaMemcpy(h->dv.sweep, sw.data(), sizeof(uint64_t) * h->R, cudaMemcpyHostToDevice));
-    CK(cudaMemcpy(h->dv.counters, cnt.data(), sizeof(unsigned long long) * cnt.size(), cudaMemcpyHostToDevice));
-    CK(cudaDeviceSynchronize());
     if (best_lanes) *best_lanes = bg;
     if (best_warps) *best_warps = bw;
     return read_error(h);

@@ -32,6 +32,7 @@ EXPORTS = [
     "hpmc_run_host", "hpmc_autotune", "hpmc_geometry", "hpmc_launches_per_sweep",
     "hpmc_filter_margins", "hpmc_strerror", "hpmc_profile_sweeps", "hpmc_count_overlaps_noalloc",
     "hpmc_trace_read", "hpmc_pair_test", "hpmc_sdf", "hpmc_box_move", "hpmc_get_box",
+    "hpmc_tune_moves", "hpmc_msd_reset", "hpmc_msd_update", "hpmc_msd_read",
 ]
 
 
@@ -96,6 +97,11 @@ def _load():
         "hpmc_box_move": [ctypes.c_void_p, ctypes.c_int32, ctypes.c_double, ctypes.c_double,
                           ctypes.POINTER(ctypes.c_int)],
         "hpmc_get_box": [ctypes.c_void_p, ctypes.c_int32, dp],
+        "hpmc_tune_moves": [ctypes.c_void_p, ctypes.c_int32, ctypes.c_double, u32, u32, ctypes.c_double,
+                            ctypes.c_double, dp, dp, dp],
+        "hpmc_msd_reset": [ctypes.c_void_p],
+        "hpmc_msd_update": [ctypes.c_void_p],
+        "hpmc_msd_read": [ctypes.c_void_p, ctypes.c_int32, dp],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -243,6 +249,26 @@ class Batch:
         _ck(_lib.hpmc_box_move(self.h, int(r), float(beta_P), float(dV_max), ctypes.byref(acc)),
             "hpmc_box_move")
         return bool(acc.value)
+
+    def tune_moves(self, target=0.30, n_pilot=100, iters=14, lo=0.25, hi=8.0, r=-1):
+        """Scale d and a together for a target acceptance (pilots from a
+        saved state, restored afterwards).  Returns (d, a, acceptance)."""
+        d, a, acc = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+        _ck(_lib.hpmc_tune_moves(self.h, int(r), float(target), int(n_pilot), int(iters), float(lo),
+                                 float(hi), ctypes.byref(d), ctypes.byref(a), ctypes.byref(acc)),
+            "hpmc_tune_moves")
+        return d.value, a.value, acc.value
+
+    def msd_reset(self):
+        _ck(_lib.hpmc_msd_reset(self.h), "hpmc_msd_reset")
+
+    def msd_update(self):
+        _ck(_lib.hpmc_msd_update(self.h), "hpmc_msd_update")
+
+    def msd(self, r=-1):
+        v = ctypes.c_double()
+        _ck(_lib.hpmc_msd_read(self.h, int(r), ctypes.byref(v)), "hpmc_msd_read")
+        return v.value
 
     def box(self, r=0):
         L = np.zeros(3)
