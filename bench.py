@@ -51,6 +51,20 @@ FLOP_MOVE, FLOP_CULL, FLOP_SAT = 30, 5, 330
 SET2D_FLUID_DRAM_BYTES = 224512
 
 
+def job_totals(torch, ms, moves, device):
+    """Whole-job time and work over the ranks of an initialised process
+    group: the slowest rank's time, the sum of the ranks' moves (one
+    independent replica per rank: weak scaling).  One process: unchanged."""
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(ms), float(moves)
+    t = torch.tensor([float(ms), float(moves)], dtype=torch.float64, device=device)
+    tmax = t.clone()
+    dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(tmax[0]), float(t[1])
+
+
 def dist_env():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -218,14 +232,7 @@ def run_ours(args):
     ms, cnt = time_steps(b, torch, stream, args.steps, args.warmup, flush)
     clocks = sampler.stop() if sampler else None
     moves = cnt["moves"]
-    if ws > 1:
-        t = torch.tensor([ms, float(moves)], dtype=torch.float64, device="cuda")
-        tmax = t.clone()
-        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
-        dist.all_reduce(t, op=dist.ReduceOp.SUM)
-        ms_job, moves_job = float(tmax[0]), float(t[1])
-    else:
-        ms_job, moves_job = ms, float(moves)
+    ms_job, moves_job = job_totals(torch, ms, moves, "cuda")
     value = moves_job / (ms_job * 1e-3)
     if rank != 0:
         b.close()
