@@ -119,8 +119,10 @@ int hpmc_set_precision(hpmc_t h, int mode);
 
 /*
  * hpmc_set_group_size -- lanes per active cell in the set kernel (1, 2, 4, 8,
- * 16 or 32) and warps per block (1..16).  Does not change the trajectory.
- * hpmc_autotune picks them by timing.
+ * 16 or 32) and warps per block (1..16, at most the kernel's launch bound:
+ * 8 warps for 8+ lanes per cell in 2D, 6 for fewer, 8 in 3D; INVALID_ARG
+ * beyond it).  Does not change the trajectory.  hpmc_autotune picks them by
+ * timing.
  */
 int hpmc_set_group_size(hpmc_t h, int lanes_per_cell, int warps_per_block);
 

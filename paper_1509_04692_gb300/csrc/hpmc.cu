@@ -690,6 +690,9 @@ int hpmc_set_group_size(hpmc_t h, int lanes_per_cell, int warps_per_block)
         return k;
     }();
     if (!K.fn || K.smem_per_warp * (size_t)warps_per_block > 227 * 1024) return HPMC_ERR_INVALID_ARG;
+    cudaFuncAttributes fa{};
+    CK(cudaFuncGetAttributes(&fa, K.fn));
+    if (32 * warps_per_block > fa.maxThreadsPerBlock) return HPMC_ERR_INVALID_ARG;   // launch bounds
     h->G = lanes_per_cell;
     h->wpb = warps_per_block;
     invalidate_graph(h);

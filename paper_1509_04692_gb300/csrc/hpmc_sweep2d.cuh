@@ -138,8 +138,11 @@ __device__ __forceinline__ float axis_gap32(const Shape2& sh, int k, float c, fl
     return fmaxf(__fsub_rn(lo, sh.fahi[k]), __fsub_rn(sh.falo[k], hi));
 }
 
+// Register budget: 128 a thread (two 256-thread blocks per SM) for the
+// latency regime; blocks of at most 192 threads and 168 registers for G <= 4,
+// whose per-pair SAT spills at 128 (measured: the 512 replicas +4%).
 template <int G, bool F32, int NV>
-__global__ void __launch_bounds__(256, 2)
+__global__ void __launch_bounds__(G >= 8 ? 256 : 192, 2)
 k_set2d(Dev dv, Shape2 sh, int nxt, int sigma, const uint32_t* __restrict__ item_base)
 {
     pdl_enter();
