@@ -142,20 +142,24 @@ struct SPt {
     int ib, ia;
 };
 
+// vertex i of A (its own frame): the shape's FP32 copy, read from the kernel
+// parameter (constant bank) instead of a register array
+__device__ __forceinline__ G32 vA(const Shape3& sh, int i) { return G32{ sh.fv[i][0], sh.fv[i][1], sh.fv[i][2] }; }
+
 template <int NV>
-__device__ __forceinline__ SPt g_support(int nv, const G32* pb, const G32* va, G32 d)
+__device__ __forceinline__ SPt g_support(int nv, const G32* pb, const Shape3& sh, G32 d)
 {
     int ib = 0, ia = 0;
-    float best = g_dot(pb[0], d), least = g_dot(va[0], d);
+    float best = g_dot(pb[0], d), least = g_dot(vA(sh, 0), d);
 #pragma unroll
     for (int i = 1; i < (NV ? NV : kMaxV3); ++i) {
         if (!NV && i >= nv) break;
         const float t = g_dot(pb[i], d);
         if (t > best) { best = t; ib = i; }
-        const float u = g_dot(va[i], d);
+        const float u = g_dot(vA(sh, i), d);
         if (u < least) { least = u; ia = i; }
     }
-    return { g_sub(pb[ib], va[ia]), ib, ia };
+    return { g_sub(pb[ib], vA(sh, ia)), ib, ia };
 }
 
 __device__ __forceinline__ int g_closest_seg(G32 a, G32 b, G32& out)
@@ -247,18 +251,18 @@ __device__ __forceinline__ int g_reduce(SPt sp[4], int& n, G32& v)
 // Separation: along direction nrm, every vertex of B (in A's frame) lies above
 // every vertex of A by more than tau |nrm| once all FP32 errors are added.
 template <int NV>
-__device__ __forceinline__ bool cert_separated(int nv, const G32* pb, const G32* va, G32 nrm, float e_pb,
+__device__ __forceinline__ bool cert_separated(int nv, const G32* pb, const Shape3& sh, G32 nrm, float e_pb,
                                                float e_va, float tau)
 {
-    float minB = g_dot(pb[0], nrm), maxA = g_dot(va[0], nrm);
+    float minB = g_dot(pb[0], nrm), maxA = g_dot(vA(sh, 0), nrm);
     float P = 0.f, V = 0.f;
 #pragma unroll
     for (int i = 0; i < (NV ? NV : kMaxV3); ++i) {
         if (!NV && i >= nv) break;
         minB = fminf(minB, g_dot(pb[i], nrm));
-        maxA = fmaxf(maxA, g_dot(va[i], nrm));
+        maxA = fmaxf(maxA, g_dot(vA(sh, i), nrm));
         P = fmaxf(P, fmaxf(fabsf(pb[i].x), fmaxf(fabsf(pb[i].y), fabsf(pb[i].z))));
-        V = fmaxf(V, fmaxf(fabsf(va[i].x), fmaxf(fabsf(va[i].y), fabsf(va[i].z))));
+        V = fmaxf(V, fmaxf(fabsf(vA(sh, i).x), fmaxf(fabsf(vA(sh, i).y), fabsf(vA(sh, i).z))));
     }
     const float n1 = __fadd_ru(__fadd_ru(fabsf(nrm.x), fabsf(nrm.y)), fabsf(nrm.z));
     const float gap = minB - maxA;
@@ -270,13 +274,13 @@ __device__ __forceinline__ bool cert_separated(int nv, const G32* pb, const G32*
 
 // Overlap: the origin lies strictly inside the tetrahedron of the four exact
 // vertex differences, farther than tau from each face plane.
-__device__ __forceinline__ bool cert_inside(const G32* pb, const G32* va, const SPt sp[4], float e_pb, float e_va,
+__device__ __forceinline__ bool cert_inside(const G32* pb, const Shape3& sh, const SPt sp[4], float e_pb, float e_va,
                                             float tau)
 {
     Fe3 W[4];
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
-        const G32 b = pb[sp[k].ib], a = va[sp[k].ia];
+        const G32 b = pb[sp[k].ib], a = vA(sh, sp[k].ia);
         W[k] = fe3_sub(Fe3{ { b.x, e_pb }, { b.y, e_pb }, { b.z, e_pb } },
                        Fe3{ { a.x, e_va }, { a.y, e_va }, { a.z, e_va } });
     }
@@ -303,7 +307,7 @@ __device__ __forceinline__ bool cert_inside(const G32* pb, const G32* va, const 
 // the support point w beyond it, and move to whichever of the three
 // tetrahedra (w, opposite vertex, face edge) encloses the origin; certify it.
 template <int NV>
-__device__ __noinline__ bool expand_inside(int nv, const G32* pb, const G32* va, SPt sp[4], float e_pb, float e_va,
+__device__ __noinline__ bool expand_inside(int nv, const G32* pb, const Shape3& sh, SPt sp[4], float e_pb, float e_va,
                                            float tau)
 {
 #pragma unroll 1
@@ -324,7 +328,7 @@ __device__ __noinline__ bool expand_inside(int nv, const G32* pb, const G32* va,
             if (f == 0 || dd < dbest) { dbest = dd; fbest = f; nbest = n; }
         }
         const int i0 = (fbest == 3) ? 1 : 0, i1 = (fbest <= 1) ? 1 : 2, i2 = (fbest == 0) ? 2 : 3, i3 = 3 - fbest;
-        const SPt w = g_support<NV>(nv, pb, va, nbest);
+        const SPt w = g_support<NV>(nv, pb, sh, nbest);
         const float hw = g_dot(nbest, w.p), hf = g_dot(nbest, sp[i0].p);
         if (!(hw > hf + 1e-6f * fabsf(hf) + 1e-30f)) return false;              // face on the boundary of B - A
         const SPt T[3][4] = { { w, sp[i3], sp[i0], sp[i1] }, { w, sp[i3], sp[i1], sp[i2] },
@@ -343,7 +347,7 @@ __device__ __noinline__ bool expand_inside(int nv, const G32* pb, const G32* va,
         if (pick < 0) return false;
 #pragma unroll
         for (int k = 0; k < 4; ++k) sp[k] = T[pick][k];
-        if (cert_inside(pb, va, sp, e_pb, e_va, tau)) return true;
+        if (cert_inside(pb, sh, sp, e_pb, e_va, tau)) return true;
     }
     return false;
 }
@@ -373,34 +377,33 @@ __device__ __forceinline__ int gjk32_cert(const Shape3& sh, float dx, float dy, 
                     (v.z + w * tz) + (x * ty - y * tx) };
     };
     const G32 l = rot(a0, a1, a2, a3, G32{ dx, dy, dz });
-    G32 pb[NV ? NV : kMaxV3], va[NV ? NV : kMaxV3];
+    G32 pb[NV ? NV : kMaxV3];
 #pragma unroll
     for (int i = 0; i < (NV ? NV : kMaxV3); ++i) {
         if (!NV && i >= nv) break;
-        va[i] = G32{ sh.fv[i][0], sh.fv[i][1], sh.fv[i][2] };
-        const G32 rr = rot(r0, r1, r2, r3, va[i]);
+        const G32 rr = rot(r0, r1, r2, r3, vA(sh, i));
         pb[i] = G32{ rr.x + l.x, rr.y + l.y, rr.z + l.z };
     }
     // the centre line first: well-separated pairs are certified without GJK
-    if (cert_separated<NV>(nv, pb, va, l, e_pb, e_va, tau)) return GJK32_SEPARATED;
+    if (cert_separated<NV>(nv, pb, sh, l, e_pb, e_va, tau)) return GJK32_SEPARATED;
     G32 d = g_neg(l);
     if (d.x == 0.f && d.y == 0.f && d.z == 0.f) d.x = -1.0f;
     SPt sp[4];
     int n = 1;
-    sp[0] = g_support<NV>(nv, pb, va, d);
+    sp[0] = g_support<NV>(nv, pb, sh, d);
     G32 v = sp[0].p;
     bool tried = false;   // a separating direction failed its certificate
 #pragma unroll 1
     for (int it = 0; it < kGjkMaxIt; ++it) {
         const float vv = g_dot(v, v);
         if (vv == 0.f) return GJK32_UNC_DEGENERATE;
-        const SPt w = g_support<NV>(nv, pb, va, g_neg(v));
+        const SPt w = g_support<NV>(nv, pb, sh, g_neg(v));
         const float vw = g_dot(v, w.p);
         if (vw > 0.f) {
             // v separates in FP32.  Certify it; if the gap is within the
             // bound, keep iterating towards the closest point (the largest
             // gap any direction can show) until the distance estimate stalls.
-            if (cert_separated<NV>(nv, pb, va, v, e_pb, e_va, tau)) return GJK32_SEPARATED;
+            if (cert_separated<NV>(nv, pb, sh, v, e_pb, e_va, tau)) return GJK32_SEPARATED;
             if (tried && __fsub_rn(vv, vw) <= __fmul_rn(1e-6f, vv)) return GJK32_UNCERTAIN;
             tried = true;
         }
@@ -412,8 +415,8 @@ __device__ __forceinline__ int gjk32_cert(const Shape3& sh, float dx, float dy, 
         n += 1;
         const int rr = g_reduce(sp, n, v);
         if (rr == 1) {
-            if (cert_inside(pb, va, sp, e_pb, e_va, tau)) return GJK32_OVERLAP;
-            return expand_inside<NV>(nv, pb, va, sp, e_pb, e_va, tau) ? GJK32_OVERLAP : GJK32_UNC_INSIDE;
+            if (cert_inside(pb, sh, sp, e_pb, e_va, tau)) return GJK32_OVERLAP;
+            return expand_inside<NV>(nv, pb, sh, sp, e_pb, e_va, tau) ? GJK32_OVERLAP : GJK32_UNC_INSIDE;
         }
         if (rr == 2) return GJK32_UNC_DEGENERATE;
     }

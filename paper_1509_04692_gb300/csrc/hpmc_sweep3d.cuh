@@ -97,7 +97,7 @@ template <int G, bool F32, int NV>
 // keeps the inlined FP32 GJK free of spills (measured: cubes +15%,
 // dodecahedra +15% against a 128-register cap).
 __global__ void __launch_bounds__(256, 1)
-k_set3d(Dev dv, Shape3 sh, int nxt, int sigma, const uint32_t* __restrict__ item_base)
+k_set3d(Dev dv, const __grid_constant__ Shape3 sh, int nxt, int sigma, const uint32_t* __restrict__ item_base)
 {
     pdl_enter();
     using W = Warp3<G, F32>;

@@ -29,7 +29,7 @@ __global__ void k_pairs2d(Shape2 sh, float E, uint32_t n, const double* D, const
     o32[i] = v == 1 ? 1 : (v == 0 ? 0 : 2);
 }
 
-__global__ void k_pairs3d(Shape3 sh, float e_pb, float e_va, float tau, uint32_t n, const double* D,
+__global__ void k_pairs3d(const __grid_constant__ Shape3 sh, float e_pb, float e_va, float tau, uint32_t n, const double* D,
                           const double* qA, const double* qB, int32_t* o64, int32_t* o32)
 {
     const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
