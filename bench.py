@@ -430,16 +430,28 @@ def run_profile(args):
     print(json.dumps(out))
 
 
+VALIDATION = {
+    # the paper's NVT validation state points (Sec. 4, Table 2)
+    "disks": ("hard disks N=65536 phi=0.698 (paper Sec. 4: P* = beta P sigma^2 = 9.1707(2))",
+              lambda: inputs.disk_system(65536, 0.698, 42, d=0.05, w_min=1.06)),
+    "spheres": ("hard spheres N=131072 phi=0.60, FCC (paper Sec. 4: P* = beta P v0 = 9.3135(4))",
+                lambda: inputs.sphere_system(32, 0.60, 42, d=0.05, w_min=1.06)),
+}
+
+
 def run_validate_pressure(args):
-    """Hard disks at area fraction 0.698 (N = 65536), the paper's NVT
-    validation state point (Sec. 4: P* = beta P sigma^2 = 9.1707(2)): melt
-    the lattice, then sample the scale distribution every `--sample-every`
-    sweeps and extrapolate the pressure (block averages show the drift)."""
+    """A state point of the paper's NVT validation (Sec. 4): hard disks at
+    area fraction 0.698 (65536, P* = 9.1707(2)) or hard spheres at volume
+    fraction 0.60 on their FCC lattice (131072, P* = 9.3135(4)): equilibrate
+    from the lattice, then sample the scale distribution every
+    `--sample-every` sweeps and extrapolate the pressure (block averages show
+    the drift)."""
     import torch
     from paper_1509_04692_gb300 import hpmc, pressure, tune
     torch.cuda.set_device(0)
     x_max, nbins = 0.05, 25
-    s = inputs.disk_system(65536, 0.698, 42, d=0.05, w_min=1.06)
+    label, make = VALIDATION[args.validate_system]
+    s = make()
     b = hpmc.from_system(s)
     b.set_precision(hpmc.HPMC_FP32_FILTERED)
     t0 = time.time()
@@ -473,13 +485,20 @@ def run_validate_pressure(args):
             b.sdf(x_max, nbins, hist=h)
         hist_all += h
         n_all += per_block
-        blocks.append(pressure.pressure(h, per_block, x_max, s.N, float(s.L[0] * s.L[1]), 2)["P_star"])
+        blocks.append(pressure.pressure(h, per_block, x_max, s.N, float(np.prod(s.L)), s.dim)["P_star"])
     samp_s = time.time() - ts
-    out = pressure.pressure(hist_all, n_all, x_max, s.N, float(s.L[0] * s.L[1]), 2)
+    vol = float(np.prod(s.L))
+    out = pressure.pressure(hist_all, n_all, x_max, s.N, vol, s.dim)
     c = b.counters()
     bm = np.array(blocks)
+    # sensitivity of the extrapolation: polynomial degree and fitted range
+    variants = {}
+    for deg, nb in ((1, 10), (2, 25), (3, 25), (2, 12)):
+        v = pressure.pressure(hist_all[:nb], n_all, x_max * nb / nbins, s.N, vol, s.dim, deg=deg)
+        variants[f"deg{deg}_x{x_max * nb / nbins:.3f}"] = v["P_star"]
     print(json.dumps({
-        "validate": "hard disks N=65536 phi=0.698 (paper Sec. 4: P* = 9.1707(2))",
+        "P_star_fit_variants": variants,
+        "validate": label,
         "P_star": out["P_star"], "P_star_fit_err": out["P_star_err"],
         "P_star_blocks": blocks, "P_star_block_sem": float(bm.std(ddof=1) / np.sqrt(len(bm))),
         "d": d, "acceptance": c["accept"] / max(1, c["moves"]),
@@ -556,6 +575,7 @@ def main():
     ap.add_argument("--validate-pressure", type=int, default=0,
                     help="hard-disk pressure validation: equilibration sweeps (then sampling)")
     ap.add_argument("--validate-samples", type=int, default=2000)
+    ap.add_argument("--validate-system", default="disks", choices=sorted(VALIDATION))
     ap.add_argument("--efficiency", type=int, default=0,
                     help="diffusion per GPU second against move size (sweeps per point)")
     ap.add_argument("--sample-every", type=int, default=50)
