@@ -748,11 +748,57 @@ void or_overlap_batch(const or_system* s, uint32_t n, const double* D, const dou
 /* h the number of pairs per unit x.  Every unordered pair (all pairs,       */
 /* minimum image) with 0 <= x* < x_max adds one to bin (int)(x* nbins/x_max). */
 /* ------------------------------------------------------------------------ */
-int or_sdf_histogram(const or_system* s, uint32_t N, const double* pos, double x_max, uint32_t nbins,
-                     uint64_t* hist)
+/* Shaped particles (volume perturbation for particles with shape, Sec. 4):
+ * with positions compressed by (1 - x) and the shapes unchanged, a pair at D
+ * overlaps from x* on (overlap(lambda D) is monotone in lambda for convex
+ * shapes containing their centres).  Reading: the bin of x* is found with
+ * the overlap contract at the bin edges e_k = k h, h = x_max / nbins, by
+ * bisection: if the pair overlaps at e_nbins, the smallest overlapping edge
+ * index k (lo = 0, hi = nbins; while hi - lo > 1: mid = (lo + hi) / 2,
+ * overlap at e_mid ? hi = mid : lo = mid) gives bin hi - 1; the scaled
+ * separation is D_a * (1 - e_k) per axis. */
+static int or_sdf_shaped_bin(const or_system* s, const double D[3], const double* qi, const double* qj,
+                             double h, uint32_t nbins)
 {
-    if (s->nv != 0 || !(x_max > 0.0) || nbins == 0) return -1;
     const int dim = s->dim;
+    #define OR_OVERLAP_AT(k, out)                                                 \
+        do {                                                                      \
+            const double sc = 1.0 - (double)(k) * h;                              \
+            double Ds[3] = { D[0] * sc, D[1] * sc, dim == 3 ? D[2] * sc : 0.0 };  \
+            if (dim == 2) out = or_overlap_2d(s, Ds, qi, qj);                     \
+            else { int it_ = 0; out = or_overlap_3d(s, Ds, qi, qj, &it_); }       \
+        } while (0)
+    int top = 0;
+    OR_OVERLAP_AT(nbins, top);
+    if (!top) return -1;
+    uint32_t lo = 0, hi = nbins;
+    while (hi - lo > 1) {
+        const uint32_t mid = (lo + hi) / 2;
+        int ov = 0;
+        OR_OVERLAP_AT(mid, ov);
+        if (ov) hi = mid; else lo = mid;
+    }
+    #undef OR_OVERLAP_AT
+    return (int)lo;
+}
+
+int or_sdf_histogram(const or_system* s, uint32_t N, const double* pos, const double* orient, double x_max,
+                     uint32_t nbins, uint64_t* hist)
+{
+    if (!(x_max > 0.0) || !(x_max < 1.0) || nbins == 0) return -1;
+    const int dim = s->dim, qd = (dim == 2) ? 2 : 4;
+    if (s->nv != 0) {
+        const double h = x_max / (double)nbins;
+        for (uint32_t i = 0; i < N; ++i)
+            for (uint32_t j = i + 1; j < N; ++j) {
+                double D[3] = { 0, 0, 0 };
+                for (int k = 0; k < dim; ++k)
+                    D[k] = or_min_image(pos[(size_t)j * dim + k] - pos[(size_t)i * dim + k], s->L[k], s->halfL[k]);
+                const int b = or_sdf_shaped_bin(s, D, orient + (size_t)i * qd, orient + (size_t)j * qd, h, nbins);
+                if (b >= 0) hist[b] += 1;
+            }
+        return 0;
+    }
     const double sigma = s->R + s->R;
     const double scale = (double)nbins / x_max;
     for (uint32_t i = 0; i < N; ++i)

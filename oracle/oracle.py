@@ -79,7 +79,7 @@ def lib():
             L.or_box_move.argtypes = [ctypes.c_void_p, ctypes.c_uint32, dp, dp, ctypes.c_double,
                                       ctypes.c_double, ctypes.c_uint64]
             L.or_sdf_histogram.restype = ctypes.c_int
-            L.or_sdf_histogram.argtypes = [ctypes.c_void_p, ctypes.c_uint32, dp, ctypes.c_double,
+            L.or_sdf_histogram.argtypes = [ctypes.c_void_p, ctypes.c_uint32, dp, dp, ctypes.c_double,
                                            ctypes.c_uint32, ctypes.POINTER(ctypes.c_uint64)]
             L.or_rsa_2d.restype = ctypes.c_int
             L.or_rsa_2d.argtypes = [ctypes.c_void_p, ctypes.c_uint32, ctypes.c_uint64,
@@ -149,12 +149,16 @@ class OracleSystem:
         lib().or_get_box(self.ptr, _dp(L))
         return L[: self.dim].copy()
 
-    def sdf_histogram(self, pos, x_max, nbins):
-        """Counts of pair scale factors x* = 1 - sigma / r in [0, x_max), nbins
-        bins, every unordered pair once (disks / spheres only)."""
+    def sdf_histogram(self, pos, x_max, nbins, orient=None):
+        """Counts of pair compression factors x* in [0, x_max), nbins bins,
+        every unordered pair once (disks / spheres: x* = 1 - sigma / r;
+        shaped particles: bisection over the bin edges, orientations needed)."""
         p = np.ascontiguousarray(pos, dtype=np.float64)
+        qd = 2 if self.dim == 2 else 4
+        o = (np.zeros((p.shape[0], qd)) if orient is None
+             else np.ascontiguousarray(orient, dtype=np.float64))
         h = np.zeros(int(nbins), dtype=np.uint64)
-        rc = lib().or_sdf_histogram(self.ptr, p.shape[0], _dp(p), float(x_max), int(nbins),
+        rc = lib().or_sdf_histogram(self.ptr, p.shape[0], _dp(p), _dp(o), float(x_max), int(nbins),
                                     h.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)))
         if rc != 0:
             raise ValueError("or_sdf_histogram failed")

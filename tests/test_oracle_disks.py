@@ -65,3 +65,39 @@ def test_sdf_pairs_and_spheres():
     r3 = math.hypot(1.01, 1.05)
     assert 1.0 - 1.0 / r3 > 0.1
     assert np.array_equal(h, expect)
+
+
+def test_sdf_shaped_face_to_face_closed_form():
+    # aligned squares (2D) and cubes (3D) of side a, centres d apart along x:
+    # compressing by (1 - x) makes them touch at x* = 1 - a / d exactly
+    a, x_max, nbins = 0.8, 0.1, 40
+    h = x_max / nbins
+    sq = np.array([[0.4, -0.4], [0.4, 0.4], [-0.4, 0.4], [-0.4, -0.4]])
+    o2 = orc.OracleSystem(2, [20.0, 20.0], sq)
+    cube = inputs.cube(a)
+    o3 = orc.OracleSystem(3, [20.0] * 3, cube)
+    for d in (0.8123, 0.8457, 0.8801, 0.95):
+        xs = 1.0 - a / d
+        expect = np.zeros(nbins, dtype=np.uint64)
+        if xs < x_max:
+            expect[int(xs / h)] = 1
+        p2 = np.array([[5.0, 5.0], [5.0 + d, 5.0]])
+        z2 = np.tile([1.0, 0.0], (2, 1))
+        assert np.array_equal(o2.sdf_histogram(p2, x_max, nbins, z2), expect), d
+        p3 = np.array([[5.0, 5.0, 5.0], [5.0 + d, 5.0, 5.0]])
+        q3 = np.tile([1.0, 0.0, 0.0, 0.0], (2, 1))
+        assert np.array_equal(o3.sdf_histogram(p3, x_max, nbins, q3), expect), d
+
+
+def test_sdf_shaped_rotated_square_contact():
+    # a square rotated by 45 degrees meets an aligned one corner-to-face at
+    # centre distance a/2 + a/sqrt(2) along x
+    a, x_max, nbins = 1.0, 0.2, 50
+    sq = 0.5 * a * np.array([[1, -1], [1, 1], [-1, 1], [-1, -1]], float)
+    o = orc.OracleSystem(2, [20.0, 20.0], sq)
+    contact = 0.5 * a + a / math.sqrt(2.0)
+    d = contact / (1.0 - 0.0731)
+    pos = np.array([[5.0, 5.0], [5.0 + d, 5.0]])
+    z = np.array([[1.0, 0.0], [math.cos(math.pi / 4), math.sin(math.pi / 4)]])
+    h = o.sdf_histogram(pos, x_max, nbins, z)
+    assert h.sum() == 1 and h[int(0.0731 / (x_max / nbins))] == 1
