@@ -244,17 +244,20 @@ int hpmc_msd_update(hpmc_t h);
 int hpmc_msd_read(hpmc_t h, int32_t r, double* msd);
 
 /*
- * hpmc_sdf -- pressure sampling by the scale distribution (Sec. 4; disks and
- * spheres, nv = 0): for every pair of replica r (r = -1: all replicas) whose
- * scale factor x* = 1 - 2R/|D| (the uniform compression of positions by
- * 1 - x that makes the pair touch) lies in [0, x_max), adds one to
- * hist[(int)(x* * nbins / x_max)].  hist is a caller-owned host array of
+ * hpmc_sdf -- pressure sampling by the scale distribution (Sec. 4): for
+ * every pair of replica r (r = -1: all replicas) whose compression factor x*
+ * (the uniform compression of positions by 1 - x, shapes unchanged, that
+ * makes the pair touch) lies in [0, x_max), adds one to the bin of x*.
+ * Disks / spheres (nv = 0): x* = 1 - 2R/|D|, bin (int)(x* * nbins / x_max).
+ * Shaped particles: the bin by bisection over the bin edges e_k = k h,
+ * h = x_max / nbins, with the overlap test along D (1 - e_k): the smallest
+ * overlapping edge k gives bin k - 1.  hist is a caller-owned host array of
  * nbins uint64 that is accumulated, not cleared, so successive samples add
  * up.  beta P / rho = 1 + h(0) / (dim N), h(x) the pair count per unit x
  * per configuration extrapolated to x = 0.  Requires 0 < x_max < 1,
  * 1 <= nbins <= 2^20 and 2R / (1 - x_max) <= the cell width on every axis
- * (w_min at creation sets it); INVALID_ARG otherwise, and for shaped
- * particles.  Rebuilds the cell list (the trajectory is unaffected).
+ * (w_min at creation sets it); INVALID_ARG otherwise.  Rebuilds the cell
+ * list (the trajectory is unaffected).
  * Synchronous.
  */
 int hpmc_sdf(hpmc_t h, int32_t r, double x_max, uint32_t nbins, uint64_t* hist);

@@ -808,8 +808,7 @@ int hpmc_check_overlaps(hpmc_t h, int32_t r, uint64_t* n_pairs)
 int hpmc_sdf(hpmc_t h, int32_t r, double x_max, uint32_t nbins, uint64_t* hist)
 {
     if (!h || !hist || r < -1 || r >= (int32_t)h->R) return HPMC_ERR_INVALID_ARG;
-    if (h->nv != 0 || !(x_max > 0.0) || !(x_max < 1.0) || nbins == 0 || nbins > (1u << 20))
-        return HPMC_ERR_INVALID_ARG;
+    if (!(x_max > 0.0) || !(x_max < 1.0) || nbins == 0 || nbins > (1u << 20)) return HPMC_ERR_INVALID_ARG;
     const double sigma = h->Rc + h->Rc;
     const double rmax = sigma / (1.0 - x_max);
     for (uint32_t q = 0; q < h->R; ++q) {
@@ -832,8 +831,12 @@ int hpmc_sdf(hpmc_t h, int32_t r, double x_max, uint32_t nbins, uint64_t* hist)
     h->cur ^= 1;
     CK(cudaMemset(h->sdf_hist, 0, sizeof(unsigned long long) * nbins));
     const int T = 128;
-    k_sdf<<<(h->ntot + T - 1) / T, T>>>(h->dv, h->cur, sigma, x_max, (double)nbins / x_max, nbins, r,
-                                        h->sdf_hist);
+    if (h->nv == 0)
+        k_sdf<<<(h->ntot + T - 1) / T, T>>>(h->dv, h->cur, sigma, x_max, (double)nbins / x_max, nbins, r,
+                                            h->sdf_hist);
+    else
+        k_sdf_shaped<<<(h->ntot + T - 1) / T, T>>>(h->dv, h->cur, h->sh2, h->sh3, x_max / (double)nbins, nbins, r,
+                                                   h->sdf_hist);
     CK(cudaGetLastError());
     std::vector<unsigned long long> got(nbins);
     CK(cudaMemcpy(got.data(), h->sdf_hist, sizeof(unsigned long long) * nbins, cudaMemcpyDeviceToHost));

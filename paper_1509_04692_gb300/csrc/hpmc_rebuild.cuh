@@ -240,6 +240,68 @@ __global__ void k_place(Dev dv, int cur, int advance)
 // neighbours (the higher tag counts it) with 0 <= x* = 1 - sigma / r < x_max
 // adds one to bin (int)(x* * scale), scale = nbins / x_max.  The host checks
 // that sigma / (1 - x_max) fits in a cell, so the stencil holds every such pair.
+// Shaped particles: the bin of the pair's compression factor by bisection
+// over the bin edges e_k = k h with the FP64 overlap contract along the
+// scaled separation D (1 - e_k) (overlap is monotone along it for convex
+// shapes containing their centres); -1 when the pair does not overlap at
+// the last edge.
+template <int DIM>
+__device__ int sdf_shaped_bin(const Shape2& s2, const Shape3& s3, const double D[3], const double* qi,
+                              const double* qj, double h, uint32_t nbins)
+{
+    auto overlap_at = [&](uint32_t k) {
+        const double sc = 1.0 - (double)k * h;
+        if (DIM == 2) return overlap2d64<0>(s2, D[0] * sc, D[1] * sc, qi[0], qi[1], qj[0], qj[1]);
+        const double Ds[3] = { D[0] * sc, D[1] * sc, D[2] * sc };
+        int it = 0;
+        return overlap3d64<0>(s3, Ds, qi, qj, &it);
+    };
+    if (!overlap_at(nbins)) return -1;
+    uint32_t lo = 0, hi = nbins;
+    while (hi - lo > 1) {
+        const uint32_t mid = (lo + hi) / 2;
+        if (overlap_at(mid)) hi = mid;
+        else lo = mid;
+    }
+    return (int)lo;
+}
+
+__global__ void k_sdf_shaped(Dev dv, int b, const __grid_constant__ Shape2 s2, const __grid_constant__ Shape3 s3,
+                             double h, uint32_t nbins, int32_t only_r, unsigned long long* hist)
+{
+    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= dv.ntot) return;
+    const uint32_t r = dv.rep_of[i];
+    if (only_r >= 0 && (int32_t)r != only_r) return;
+    const Rep& rp = dv.reps[r];
+    const Bufs& B = dv.buf[b];
+    const int d3 = dv.dim == 3;
+    const int ix = cell_axis(B.px[i], dv.shift[3 * r], rp.L[0], rp.inv_w[0], rp.nc[0]);
+    const int iy = cell_axis(B.py[i], dv.shift[3 * r + 1], rp.L[1], rp.inv_w[1], rp.nc[1]);
+    const int iz = d3 ? cell_axis(B.pz[i], dv.shift[3 * r + 2], rp.L[2], rp.inv_w[2], rp.nc[2]) : 0;
+    const uint32_t ti = B.tag[i];
+    const double qi[4] = { B.q0[i], B.q1[i], d3 ? B.q2[i] : 0.0, d3 ? B.q3[i] : 0.0 };
+    for (int oz = -d3; oz <= d3; ++oz)
+        for (int oy = -1; oy <= 1; ++oy)
+            for (int ox = -1; ox <= 1; ++ox) {
+                const int jx = (ix + ox + rp.nc[0]) % rp.nc[0];
+                const int jy = (iy + oy + rp.nc[1]) % rp.nc[1];
+                const int jz = d3 ? (iz + oz + rp.nc[2]) % rp.nc[2] : 0;
+                const uint32_t cc = rp.cbase + (uint32_t)jx +
+                                    (uint32_t)rp.nc[0] * ((uint32_t)jy + (uint32_t)rp.nc[1] * (uint32_t)jz);
+                for (uint32_t e = dv.start[cc]; e < dv.start[cc + 1]; ++e) {
+                    if (B.tag[e] <= ti) continue;
+                    const double D[3] = { min_image(B.px[e] - B.px[i], rp.L[0], rp.halfL[0]),
+                                          min_image(B.py[e] - B.py[i], rp.L[1], rp.halfL[1]),
+                                          d3 ? min_image(B.pz[e] - B.pz[i], rp.L[2], rp.halfL[2]) : 0.0 };
+                    const double qj[4] = { B.q0[e], B.q1[e], d3 ? B.q2[e] : 0.0, d3 ? B.q3[e] : 0.0 };
+                    const int bin = d3 ? sdf_shaped_bin<3>(s2, s3, D, qi, qj, h, nbins)
+                                       : sdf_shaped_bin<2>(s2, s3, D, qi, qj, h, nbins);
+                    if (bin >= 0) atomicAdd(hist + bin, 1ull);
+                }
+            }
+}
+
 __global__ void k_sdf(Dev dv, int b, double sigma, double x_max, double scale, uint32_t nbins, int32_t only_r,
                       unsigned long long* hist)
 {

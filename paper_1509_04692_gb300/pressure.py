@@ -1,8 +1,9 @@
-"""Pressure of hard disks / spheres from the scale-distribution histogram
-(Sec. 4 of Anderson, Irrgang & Glotzer).
+"""Pressure of hard particles from the scale-distribution histogram (Sec. 4
+of Anderson, Irrgang & Glotzer; the volume perturbation that extends it to
+particles with shape).
 
-Compressing every position by the factor (1 - x) makes a pair at distance
-r touch at x* = 1 - sigma / r.  With h(x) the number of pairs per unit x
+Compressing every position by the factor (1 - x), shapes unchanged, makes a
+pair touch at some x* (disks / spheres: x* = 1 - sigma / r).  With h(x) the number of pairs per unit x
 (per configuration) whose x* lies just above x, the volume-perturbation
 argument gives beta P / rho = 1 + h(0) / (dim N): the probability that a
 compression by x creates an overlap is h(0) x for small x, and the volume
@@ -42,8 +43,8 @@ def extrapolate_h0(hist, n_samples: int, x_max: float, deg: int = 3):
 def pressure(hist, n_samples: int, x_max: float, N: int, volume: float, dim: int, sigma: float = 1.0,
              deg: int = 3) -> dict:
     """Reduced pressure from an accumulated histogram: beta P / rho, and P*
-    as the paper reports it (2D: beta P sigma^2; 3D: beta P v0 with v0 the
-    particle volume)."""
+    as the paper reports it for disks / spheres of diameter sigma (2D:
+    beta P sigma^2; 3D: beta P v0 with v0 the sphere volume)."""
     h0, dh0 = extrapolate_h0(hist, n_samples, x_max, deg)
     bpr = 1.0 + h0 / (dim * N)
     rho = N / volume

@@ -109,3 +109,42 @@ def test_disk_pressure_at_the_papers_state_point():
     assert abs(out["P_star"] - 9.1707) < 0.04, out
     assert b.check_overlaps() == 0
     b.close()
+
+
+@pytest.mark.parametrize("shape", ["pentagons", "cubes"])
+def test_sdf_shaped_matches_oracle(shape):
+    s = (inputs.pentagon_system(1024, 0.55, 41, d=0.1, a=0.2, w_min=1.06) if shape == "pentagons"
+         else inputs.cube_system(512, 0.40, 42, d=0.1, a=0.2))
+    if shape == "cubes":
+        s.w_min = 2.0 * inputs.circumradius(s.verts) / (1.0 - 0.05) + 1e-9
+    b = hpmc.from_system(s)
+    b.sweep(20, graph=True)
+    p, q, sw = b.get_state()
+    h = b.sdf(0.05, 20)
+    ref = orc.OracleSystem(s.dim, s.L, s.verts, w_min=s.w_min).sdf_histogram(p, 0.05, 20, q)
+    assert h.sum() > 0 and np.array_equal(h, ref)
+    b.close()
+
+
+def test_dilute_pentagon_pressure_matches_second_virial():
+    # hard convex 2D bodies: B2 = A + P^2 / (4 pi) (area A, perimeter P); for
+    # the regular pentagon of circumradius 0.5, B2 / A = 2.15637.  At area
+    # fraction 0.05 the third term (B3 / A^2 ~ 3.6 for near-round shapes)
+    # adds ~0.009 +- 0.002.
+    eta = 0.05
+    v = inputs.regular_polygon(5, 0.5)
+    A = inputs.polygon_area(v)
+    P = 5 * np.linalg.norm(v[1] - v[0])
+    b2 = (A + P * P / (4 * math.pi)) / A
+    s = inputs.pentagon_system(4096, eta, 43, d=0.5, a=0.8, w_min=1.06)
+    b = hpmc.from_system(s)
+    b.sweep(500, graph=True)
+    hist, n = None, 0
+    for _ in range(400):
+        b.sweep(5, graph=True)
+        hist = b.sdf(0.05, 25, hist=hist)
+        n += 1
+    out = pressure.pressure(hist, n, 0.05, s.N, float(s.L[0] * s.L[1]), 2)
+    ref = 1 + b2 * eta + 3.6 * eta ** 2
+    assert abs(out["beta_P_over_rho"] - ref) < 0.006, (out, ref, b2)
+    b.close()
