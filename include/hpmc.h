@@ -212,6 +212,15 @@ int hpmc_trace_read(hpmc_t h, uint64_t* out, uint32_t max_warps, uint32_t* n_poi
  */
 int hpmc_box_move(hpmc_t h, int32_t r, double beta_P, double dV_max, int* accepted);
 
+/*
+ * hpmc_debug_fail_alloc -- fault injection for tests: the n-th device
+ * allocation the library makes from now on (n = 0: the next one) fails as
+ * if the device were out of memory; the call that made it returns
+ * HPMC_ERR_OOM and releases what it had allocated.  n < 0 disables it.
+ * Host-side only: nothing runs on or faults the device.
+ */
+int hpmc_debug_fail_alloc(int32_t n);
+
 /* hpmc_get_box -- the current box lengths of replica r (box[3]; 0 beyond dim). */
 int hpmc_get_box(hpmc_t h, int32_t r, double* box);
 

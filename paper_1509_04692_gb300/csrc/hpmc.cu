@@ -118,10 +118,16 @@ int cuda_fail(cudaError_t e)
         if (e_ != cudaSuccess) return cuda_fail(e_); \
     } while (0)
 
+// Fault injection for tests (hpmc_debug_fail_alloc): when non-negative, the
+// allocation with this index (counting from the call) fails as if the device
+// were out of memory.  Host-side only; the device is never faulted.
+int g_fail_alloc = -1;
+
 template <typename T>
 int dalloc(hpmc_batch* h, T** p, size_t n)
 {
     void* q = nullptr;
+    if (g_fail_alloc >= 0 && g_fail_alloc-- == 0) return HPMC_ERR_OOM;
     cudaError_t e = cudaMalloc(&q, std::max<size_t>(n, 1) * sizeof(T));
     if (e != cudaSuccess) return cuda_fail(e);
     h->allocs.push_back(q);
@@ -1035,6 +1041,12 @@ int hpmc_msd_read(hpmc_t h, int32_t r, double* msd)
         n += h->hr[q].N;
     }
     *msd = n ? sum / (double)n : 0.0;
+    return 0;
+}
+
+int hpmc_debug_fail_alloc(int32_t n)
+{
+    g_fail_alloc = n < 0 ? -1 : n;
     return 0;
 }
 

@@ -32,7 +32,7 @@ EXPORTS = [
     "hpmc_run_host", "hpmc_autotune", "hpmc_geometry", "hpmc_launches_per_sweep",
     "hpmc_filter_margins", "hpmc_strerror", "hpmc_profile_sweeps", "hpmc_count_overlaps_noalloc",
     "hpmc_trace_read", "hpmc_pair_test", "hpmc_sdf", "hpmc_box_move", "hpmc_get_box",
-    "hpmc_tune_moves", "hpmc_msd_reset", "hpmc_msd_update", "hpmc_msd_read",
+    "hpmc_tune_moves", "hpmc_msd_reset", "hpmc_msd_update", "hpmc_msd_read", "hpmc_debug_fail_alloc",
 ]
 
 
@@ -102,6 +102,7 @@ def _load():
         "hpmc_msd_reset": [ctypes.c_void_p],
         "hpmc_msd_update": [ctypes.c_void_p],
         "hpmc_msd_read": [ctypes.c_void_p, ctypes.c_int32, dp],
+        "hpmc_debug_fail_alloc": [ctypes.c_int32],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -354,3 +355,9 @@ def from_systems(systems):
     reps = [dict(box=s.L, pos=s.pos, orient=s.orient, seed=s.seed, d=s.d, a=s.a, nselect=s.nselect)
             for s in systems]
     return Batch(s0.dim, s0.verts, reps, w_min=s0.w_min)
+
+
+def debug_fail_alloc(n):
+    """Fault injection for tests: the n-th device allocation from now fails
+    as out-of-memory (n < 0 disables)."""
+    _ck(_lib.hpmc_debug_fail_alloc(int(n)), "hpmc_debug_fail_alloc")
