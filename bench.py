@@ -45,6 +45,9 @@ SMS, FP32_LANES, MAX_MHZ = 152, 128, 2070.0
 PEAK_TFLOPS = SMS * FP32_LANES * 2 * MAX_MHZ * 1e6 / 1e12
 # algorithmic flops: move arithmetic + circumsphere culls + full SAT checks
 FLOP_MOVE, FLOP_CULL, FLOP_SAT = 30, 5, 330
+# per dimension: (move, cull candidate, full overlap test); 3D: the cube GJK
+# estimate (B's vertices into A's frame ~300, ~5 iterations of ~130)
+FLOPS = {2: (FLOP_MOVE, FLOP_CULL, FLOP_SAT), 3: (80, 8, 1000)}
 # DRAM bytes (read + write) of one set launch of this workload from ncu
 # (profiles/set2d_fluid4096.md, cold-cache replay); valid for the kernel as
 # captured there
@@ -196,7 +199,17 @@ def measure_form(b, torch, stream, flush, precision, melt, sweeps, steps, n_tune
         b.sweep(melt, stream=stream.cuda_stream, graph=True)
     lanes, warps = b.autotune(n_tune)
     ms, c = time_steps(b, torch, stream, steps, 1, flush, sweeps)
+    # the set kernels' ALU roofline fraction under the same flop model as the
+    # headline (per move, per cull candidate, per full overlap test)
+    b.reset_counters()
+    n_prof = max(1, sweeps // 2)
+    _, ms_sets = b.profile_sweeps(n_prof, stream=stream.cuda_stream)
+    cp = b.counters()
+    fm, fc, ft = FLOPS[b.dim]
+    flop = fm * cp["moves"] + fc * cp["cull_pairs"] + ft * cp["overlap_checks"]
+    achieved = flop / (ms_sets * n_prof * 1e-3) / 1e12
     return {"value": c["moves"] / (ms * 1e-3),
+            "roofline_frac_alu": achieved / PEAK_TFLOPS, "set_kernels_tflops": achieved,
             "precision": "FP64" if precision == hpmc.HPMC_FP64 else "FP32_FILTERED",
             "lanes_per_cell": lanes, "warps_per_block": warps, "ms_per_step": ms / steps,
             "sweeps_per_step": sweeps, "steps": steps, "melt_sweeps": melt,

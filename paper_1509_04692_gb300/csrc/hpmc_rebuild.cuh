@@ -63,16 +63,7 @@ __global__ void k_count(Dev dv, int cur, int with_shift)
     }
     const uint32_t c = rp.cbase + local_cell(dv, rp, dv.buf[cur], i, sh);
     dv.cellid[i] = c;
-    // lanes of a warp that land in the same cell (neighbours in the previous
-    // cell order mostly do) take their arrival slots with one atomic
-    const unsigned active = __activemask();
-    const unsigned peers = __match_any_sync(active, c);
-    const int lane = threadIdx.x & 31;
-    const int leader = __ffs(peers) - 1;
-    uint32_t base = 0;
-    if (lane == leader) base = atomicAdd(dv.count + c, (uint32_t)__popc(peers));
-    base = __shfl_sync(peers, base, leader);
-    dv.slot[i] = base + (uint32_t)__popc(peers & ((1u << lane) - 1u));
+    dv.slot[i] = atomicAdd(dv.count + c, 1u);
 }
 
 // Block-wide exclusive scan of one tile of `count` into `start`; the tile
