@@ -360,15 +360,15 @@ int enqueue_rebuild(hpmc_batch* h, cudaStream_t st, bool with_shift)
     const uint32_t T = 256;
     const dim3 gp((h->ntot + T - 1) / T), gc((h->ctot + T - 1) / T);
     const int cur = h->cur;
-    const int ws = with_shift ? 1 : 0;
-    CK(launch_pdl(k_count, gp, dim3(T), st, h->dv, cur, ws));
+    if (with_shift) CK(launch_pdl(k_shift, dim3((h->R + 127) / 128), dim3(128), st, h->dv));
+    CK(launch_pdl(k_count, gp, dim3(T), st, h->dv, cur));
     CK(launch_pdl(k_scan_tiles, dim3(h->ntiles), dim3(kScanThreads), st, h->dv));
     if (h->ntiles > 1) {
         CK(launch_pdl(k_scan_sums, dim3(1), dim3(kScanThreads), st, h->dv, h->ntiles));
         CK(launch_pdl(k_scan_add, gc, dim3(T), st, h->dv));
     }
     CK(launch_pdl(k_scatter_tags, gp, dim3(T), st, h->dv, cur));
-    CK(launch_pdl(k_place, gp, dim3(T), st, h->dv, cur, ws));
+    CK(launch_pdl(k_place, gp, dim3(T), st, h->dv, cur));
     return 0;
 }
 
@@ -1360,7 +1360,7 @@ int hpmc_geometry(hpmc_t h, int32_t r, int32_t* nc, double* w, double* R)
 int hpmc_launches_per_sweep(hpmc_t h, uint32_t* n)
 {
     if (!h || !n) return HPMC_ERR_INVALID_ARG;
-    *n = 4 + (h->ntiles > 1 ? 2 : 0) + (1u << h->dim);
+    *n = 5 + (h->ntiles > 1 ? 2 : 0) + (1u << h->dim);
     return 0;
 }
 

@@ -12,9 +12,9 @@ constexpr int kScanThreads = 1024;
 constexpr int kScanItems = 4;
 constexpr int kScanTile = kScanThreads * kScanItems;
 
-// Grid shift of the sweep about to run for replica r: Philox shift stream of
-// the replica's sweep counter (advanced by k_place once the cell list is built).
-__device__ __forceinline__ void shift_of(const Dev& dv, uint32_t r, double out[3])
+// Grid shift of the sweep about to run for replica r, and the sweep counter
+// advance (the running sweep is sweep[r] - 1 afterwards).
+__device__ __forceinline__ void shift_replica(const Dev& dv, uint32_t r, double out[3])
 {
     const Rep& rp = dv.reps[r];
     const uint64_t sweep = dv.sweep[r];
@@ -27,6 +27,19 @@ __device__ __forceinline__ void shift_of(const Dev& dv, uint32_t r, double out[3
     } else {
         out[2] = 0.0;
     }
+#pragma unroll
+    for (int a = 0; a < 3; ++a) dv.shift[3 * r + a] = out[a];
+    dv.sweep[r] = sweep + 1;
+}
+
+// One thread per replica.
+__global__ void k_shift(Dev dv)
+{
+    pdl_enter();
+    const uint32_t r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= dv.R) return;
+    double s[3];
+    shift_replica(dv, r, s);
 }
 
 // Local cell (replica-relative linear index) of particle i of buffer cur.
@@ -41,27 +54,14 @@ __device__ __forceinline__ uint32_t local_cell(const Dev& dv, const Rep& rp, con
 }
 
 // Cell of every particle of buffer `cur` and its arrival slot in the cell.
-// with_shift: each thread derives the new sweep's grid shift itself (the
-// replica's first particle publishes it); otherwise the stored shift is used.
-__global__ void k_count(Dev dv, int cur, int with_shift)
+__global__ void k_count(Dev dv, int cur)
 {
     pdl_enter();
     const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= dv.ntot) return;
     const uint32_t r = dv.rep_of[i];
     const Rep& rp = dv.reps[r];
-    double sh[3];
-    if (with_shift) {
-        shift_of(dv, r, sh);
-        if (i == rp.pbase) {
-#pragma unroll
-            for (int a = 0; a < 3; ++a) dv.shift[3 * r + a] = sh[a];
-        }
-    } else {
-#pragma unroll
-        for (int a = 0; a < 3; ++a) sh[a] = dv.shift[3 * r + a];
-    }
-    const uint32_t c = rp.cbase + local_cell(dv, rp, dv.buf[cur], i, sh);
+    const uint32_t c = rp.cbase + local_cell(dv, rp, dv.buf[cur], i, dv.shift + 3 * r);
     dv.cellid[i] = c;
     dv.slot[i] = atomicAdd(dv.count + c, 1u);
 }
@@ -209,14 +209,11 @@ __device__ __forceinline__ void place_at(const Dev& dv, int cur, uint32_t i, uin
 // Canonical placement: a particle's sorted slot is its cell's start b plus
 // the number of tags among the cell's n tags (tmp_tag[b..b+n)) below its own
 // (ascending-tag order).
-// advance: the sweep's cell list is complete, so the replica's first
-// particle advances its sweep counter (the running sweep is sweep[r] - 1)
-__global__ void k_place(Dev dv, int cur, int advance)
+__global__ void k_place(Dev dv, int cur)
 {
     pdl_enter();
     const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= dv.ntot) return;
-    if (advance && i == dv.reps[dv.rep_of[i]].pbase) dv.sweep[dv.rep_of[i]] += 1;
     const uint32_t c = dv.cellid[i];
     const uint32_t b = dv.start[c];
     const uint32_t n = dv.start[c + 1] - b;
