@@ -132,7 +132,12 @@ int hpmc_set_group_size(hpmc_t h, int lanes_per_cell, int warps_per_block);
  * every replica.  Asynchronous; the sweep counter advances on the device.
  * hpmc_sweep launches the kernels directly; hpmc_sweep_graph captures the
  * launch sequence of two sweeps once into a CUDA graph (per buffer parity)
- * and replays it.  Both give the same trajectory.
+ * and replays it.  Both give the same trajectory.  With 8 or more lanes per
+ * cell each sweep also runs one kernel on an internal second stream (the
+ * state-independent part of every select, computed beside the rebuild and
+ * joined before the first set); the first sweep after a change of group
+ * size, precision, nselect or cell grid allocates its table, so a caller
+ * that captures hpmc_sweep into a graph of its own runs one sweep first.
  */
 int hpmc_sweep(hpmc_t h, uint32_t n, void* stream);
 int hpmc_sweep_graph(hpmc_t h, uint32_t n, void* stream);
@@ -290,7 +295,8 @@ int hpmc_pair_test(int dim, const double* verts, uint32_t nv, uint32_t n, const 
 /* Geometry of replica r: cells per axis, cell width, circumradius. */
 int hpmc_geometry(hpmc_t h, int32_t r, int32_t* nc, double* w, double* R);
 
-/* Number of kernel launches one sweep enqueues (for launch accounting). */
+/* Number of kernel launches one sweep enqueues, the select-table kernel of
+ * the latency regime included (for launch accounting). */
 int hpmc_launches_per_sweep(hpmc_t h, uint32_t* n);
 
 /* FP32 filter margins of replica r (in-cell, cull, overlap), for reporting. */

@@ -102,6 +102,14 @@ struct hpmc_batch {
     size_t cfg_smem = 0;
     uint32_t cfg_grid = 0;
     unsigned long long* check_out = nullptr;
+    // select table of the latency-regime kernels (G >= 8), filled by k_selects
+    // on a second stream while the cell list is rebuilt
+    bool use_selects = false;
+    void* msel = nullptr;
+    uint64_t msel_cap = 0;               // records allocated
+    uint32_t sel_grid = 0;
+    cudaStream_t side = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
 };
 
 namespace {
@@ -360,7 +368,17 @@ int enqueue_rebuild(hpmc_batch* h, cudaStream_t st, bool with_shift)
     const uint32_t T = 256;
     const dim3 gp((h->ntot + T - 1) / T), gc((h->ctot + T - 1) / T);
     const int cur = h->cur;
-    if (with_shift) CK(launch_pdl(k_shift, dim3((h->R + 127) / 128), dim3(128), st, h->dv));
+    if (with_shift) {
+        CK(launch_pdl(k_shift, dim3((h->R + 127) / 128), dim3(128), st, h->dv));
+        if (h->use_selects) {
+            // fork: the select table of this sweep (it needs the advanced
+            // sweep counter only) alongside the rebuild; joined in enqueue_sets
+            CK(cudaEventRecord(h->ev_fork, st));
+            CK(cudaStreamWaitEvent(h->side, h->ev_fork, 0));
+            CK(launch_selects(h->dv, h->dim, h->sel_grid, h->side));
+            CK(cudaEventRecord(h->ev_join, h->side));
+        }
+    }
     CK(launch_pdl(k_count, gp, dim3(T), st, h->dv, cur));
     CK(launch_pdl(k_scan_tiles, dim3(h->ntiles), dim3(kScanThreads), st, h->dv));
     if (h->ntiles > 1) {
@@ -369,6 +387,45 @@ int enqueue_rebuild(hpmc_batch* h, cudaStream_t st, bool with_shift)
     }
     CK(launch_pdl(k_scatter_tags, gp, dim3(T), st, h->dv, cur));
     CK(launch_pdl(k_place, gp, dim3(T), st, h->dv, cur));
+    return 0;
+}
+
+// Select table for the latency-regime kernels: one record for each of the
+// first min(nselect, G) selects of every cell of every replica (the chunk in
+// which idle lanes would otherwise carry the FP64 steps), grown (never
+// shrunk) with the cell count or the stride.  Runs when the launch
+// configuration is rebuilt, outside any stream capture of this library.
+int prepare_selects(hpmc_batch* h)
+{
+    h->use_selects = h->G >= 8;
+    if (!h->use_selects) return 0;
+    uint32_t stride = 1;
+    for (const HostRep& r : h->hr) stride = std::max(stride, r.nselect);
+    stride = std::min<uint32_t>(stride, (uint32_t)h->G);
+    const uint64_t need = (uint64_t)h->ctot * stride;
+    const size_t rec = select_record_bytes(h->dim);
+    if (need > h->msel_cap) {
+        if (h->msel) {
+            CK(cudaDeviceSynchronize());
+            h->allocs.erase(std::find(h->allocs.begin(), h->allocs.end(), h->msel));
+            cudaFree(h->msel);
+            h->msel = nullptr;
+            h->msel_cap = 0;
+        }
+        uint4* p = nullptr;
+        const int rc = dalloc(h, &p, need * rec / sizeof(uint4));
+        if (rc) return rc;
+        h->msel = p;
+        h->msel_cap = need;
+    }
+    if (!h->side) CK(cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking));
+    if (!h->ev_fork) CK(cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming));
+    if (!h->ev_join) CK(cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming));
+    h->dv.msel = h->msel;
+    h->dv.msel_stride = stride;
+    h->dv.msel_n = h->msel_cap;
+    const uint64_t blocks = (need + 255) / 256;
+    h->sel_grid = (uint32_t)std::max<uint64_t>(1, std::min<uint64_t>(blocks, (uint64_t)h->num_sms * 8));
     return 0;
 }
 
@@ -388,16 +445,16 @@ int prepare_set(hpmc_batch* h)
     h->cfg_fn = K.fn;
     h->cfg_smem = smem;
     h->cfg_grid = std::max<uint32_t>(1, std::min<uint32_t>(blocks_needed, (uint32_t)(per_sm * h->num_sms)));
+    int rc = prepare_selects(h);
+    if (rc) return rc;
     h->cfg_valid = true;
     return 0;
 }
 
-int enqueue_sweep(hpmc_batch* h, cudaStream_t st)
+// the set kernels of one sweep (after its rebuild) into buffer cur ^ 1
+int enqueue_sets(hpmc_batch* h, cudaStream_t st)
 {
-    int rc = prepare_set(h);
-    if (rc) return rc;
-    rc = enqueue_rebuild(h, st, true);
-    if (rc) return rc;
+    if (h->use_selects) CK(cudaStreamWaitEvent(st, h->ev_join, 0));   // join the select table
     const int nxt = h->cur ^ 1;
     const int gi = gidx_of(h->G);
     const uint32_t* ib = h->item_base_dev + (size_t)gi * (h->R + 1);
@@ -417,6 +474,15 @@ int enqueue_sweep(hpmc_batch* h, cudaStream_t st)
     }
     h->cur = nxt;
     return 0;
+}
+
+int enqueue_sweep(hpmc_batch* h, cudaStream_t st)
+{
+    int rc = prepare_set(h);
+    if (rc) return rc;
+    rc = enqueue_rebuild(h, st, true);
+    if (rc) return rc;
+    return enqueue_sets(h, st);
 }
 
 // unsorted copy of the state (tag order) into buffer cur ^ 1
@@ -645,6 +711,9 @@ int hpmc_destroy(hpmc_t h)
     cudaDeviceSynchronize();
     invalidate_graph(h);
     if (h->graph_stream) cudaStreamDestroy(h->graph_stream);
+    if (h->side) cudaStreamDestroy(h->side);
+    if (h->ev_fork) cudaEventDestroy(h->ev_fork);
+    if (h->ev_join) cudaEventDestroy(h->ev_join);
     for (void* p : h->allocs) cudaFree(p);
     if (h->sdf_hist) cudaFree(h->sdf_hist);
     delete h;
@@ -1309,25 +1378,11 @@ int hpmc_profile_sweeps(hpmc_t h, uint32_t n, void* stream, double* ms_rebuild, 
         CK(cudaEventRecord(ev[3 * s], st));
         rc = enqueue_rebuild(h, st, true);
         if (rc) break;
+        // the rebuild's time includes the select table made alongside it
+        if (h->use_selects) CK(cudaStreamWaitEvent(st, h->ev_join, 0));
         CK(cudaEventRecord(ev[3 * s + 1], st));
-        // the set kernels of enqueue_sweep, without its rebuild
-        const int nxt = h->cur ^ 1;
-        const int gi = gidx_of(h->G);
-        const uint32_t* ib = h->item_base_dev + (size_t)gi * (h->R + 1);
-        for (int sigma = 0; sigma < (1 << h->dim); ++sigma) {
-            void* args[5];
-            int nx = nxt, sg = sigma;
-            args[0] = &h->dv;
-            args[1] = h->dim == 2 ? (void*)&h->sh2 : (void*)&h->sh3;
-            args[2] = &nx;
-            args[3] = &sg;
-            args[4] = (void*)&ib;
-            // The set kernels keep the full stream dependency: launched early,
-        // their waiting blocks cost more than the saved latency (measured on
-        // the 4096-pentagon fluid: -8% moves/s, plain FP64 form -19%).
-        CK(cudaLaunchKernel(h->cfg_fn, dim3(h->cfg_grid), dim3(32 * h->wpb), args, h->cfg_smem, st));
-        }
-        h->cur = nxt;
+        rc = enqueue_sets(h, st);
+        if (rc) break;
         CK(cudaEventRecord(ev[3 * s + 2], st));
     }
     CK(cudaStreamSynchronize(st));
@@ -1360,7 +1415,7 @@ int hpmc_geometry(hpmc_t h, int32_t r, int32_t* nc, double* w, double* R)
 int hpmc_launches_per_sweep(hpmc_t h, uint32_t* n)
 {
     if (!h || !n) return HPMC_ERR_INVALID_ARG;
-    *n = 5 + (h->ntiles > 1 ? 2 : 0) + (1u << h->dim);
+    *n = 5 + (h->ntiles > 1 ? 2 : 0) + (1u << h->dim) + (h->G >= 8 ? 1 : 0);
     return 0;
 }
 

@@ -1,6 +1,9 @@
 // hpmc_launch.h -- host-side table of the set-kernel instantiations.
 #pragma once
 #include <cstddef>
+#include <cuda_runtime.h>
+
+#include "hpmc_types.h"
 
 namespace hpmc {
 
@@ -18,5 +21,10 @@ SetKernel set3d_f32_kernel(int G, int nv);
 SetKernel set3d_f64_kernel(int G, int nv);
 SetKernel set3d_f32_nv20(int G);
 SetKernel set3d_f64_nv20(int G);
+
+// select table of the latency-regime set kernels (selects.cu): bytes of one
+// record, and the kernel that fills dv.msel for the running sweep
+size_t select_record_bytes(int dim);
+cudaError_t launch_selects(const Dev& dv, int dim, uint32_t grid, cudaStream_t st);
 
 }  // namespace hpmc

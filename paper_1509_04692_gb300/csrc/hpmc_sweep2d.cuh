@@ -16,10 +16,11 @@
 // Two regimes, chosen by G:
 //  * throughput (G < 8): one lane per queued pair runs the whole
 //    separating-axis test with early exit; moves are generated on the fly.
-//  * latency (G >= 8): the random words, picks and move deltas (FP32 and the
-//    FP64 contract's) of every select are computed up front, one select per
-//    lane; each queued pair is spread over 2*nv lanes, one separating axis
-//    each, reduced with ballots.
+//  * latency (G >= 8): the picks and move deltas (FP32 and the FP64
+//    contract's) of the first G selects of a cell come from the table
+//    k_selects wrote for the sweep (selects.cu), later chunks are computed
+//    here, one select per lane; each queued pair is spread over 2*nv lanes,
+//    one separating axis each, reduced with ballots.
 //
 // F32 = true : every decision is first taken in FP32 with the certified
 //              margins of Rep (hpmc_bounds.h); FP64 only for accepted moves
@@ -30,16 +31,16 @@
 
 namespace hpmc {
 
-// Precomputed data of one select (latency regime).
-struct MoveData {
+// Precomputed data of one select (latency regime): written for every select
+// of the sweep by k_selects, loaded by the set kernel.
+struct __align__(16) MoveData {
     double dx, dy, cd, sd;      // FP64 contract: translation and Cayley rotation
     float fdx, fdy, fcd, fsd;   // FP32 versions
-    uint32_t w[6];              // words r1..r6 (FP64 re-derivation on rare paths)
     uint32_t r0;                // pick word (entry = cell begin + r0 * n_c / 2^32)
-    uint32_t pad;
+    uint32_t pad[3];
 };
 
-// Random words and move deltas of select k of a cell (state independent).
+// Move deltas and pick word of select k of a cell (state independent).
 __device__ __forceinline__ MoveData precompute_select(const Rep& rp, uint64_t seed, uint64_t sweep,
                                                       uint32_t sigma, uint32_t cell, uint32_t k)
 {
@@ -47,8 +48,6 @@ __device__ __forceinline__ MoveData precompute_select(const Rep& rp, uint64_t se
     const uint4 b1 = move_block(seed, sweep, sigma, cell, k, 1);
     MoveData m;
     m.r0 = b0.x;
-    m.w[0] = b0.y; m.w[1] = b0.z; m.w[2] = b0.w;
-    m.w[3] = b1.x; m.w[4] = b1.y; m.w[5] = b1.z;
     m.dx = rp.d_s * pm53(b0.y, b0.z);
     m.dy = rp.d_s * pm53(b0.w, b1.x);
     const double t = rp.tau_s * pm53(b1.y, b1.z);
@@ -63,7 +62,7 @@ __device__ __forceinline__ MoveData precompute_select(const Rep& rp, uint64_t se
     const float finv = __frcp_rn(__fadd_rn(1.0f, ftt));
     m.fcd = __fmul_rn(__fsub_rn(1.0f, ftt), finv);
     m.fsd = __fmul_rn(__fadd_rn(ft, ft), finv);
-    m.pad = 0;
+    m.pad[0] = m.pad[1] = m.pad[2] = 0u;
     return m;
 }
 
@@ -160,6 +159,8 @@ k_set2d(Dev dv, Shape2 sh, int nxt, int sigma, const uint32_t* __restrict__ item
     const uint32_t nitems = item_base[dv.R];
     const uint32_t wpb = blockDim.x >> 5;
     const int nvv = NV ? NV : sh.nv;
+    const MoveData* __restrict__ msel = static_cast<const MoveData*>(dv.msel);
+    const uint32_t mstride = dv.msel_stride;
     HPMC_STAMP_NS(dv, blockIdx.x * wpb + (threadIdx.x >> 5), lane, 28);
 
     for (uint32_t item = blockIdx.x * wpb + (threadIdx.x >> 5); item < nitems;
@@ -219,8 +220,8 @@ k_set2d(Dev dv, Shape2 sh, int nxt, int sigma, const uint32_t* __restrict__ item
             const uint32_t k = (uint32_t)sl;
             if (grp < Sv && k < nsel) {
                 const int ixp = (sigma & 1) + 2 * (jfirst + grp);
-                ws.mv[grp][sl] = precompute_select(rp, seed, sweep, (uint32_t)sigma,
-                                                   (uint32_t)ixp + (uint32_t)nc0 * (uint32_t)iy, k);
+                const uint32_t cg = rp.cbase + (uint32_t)ixp + (uint32_t)nc0 * (uint32_t)iy;
+                ws.mv[grp][sl] = msel[(size_t)cg * mstride + k];
             }
         }
         HPMC_STAMP(dv, wid, first, lane, 2);
@@ -381,13 +382,11 @@ k_set2d(Dev dv, Shape2 sh, int nxt, int sigma, const uint32_t* __restrict__ item
                         c_moves += 1;
                         uint32_t eA;
                         float fdx, fdy, fcd, fsd;
-                        uint32_t wr[6];
+                        uint32_t wr[6] = { 0u, 0u, 0u, 0u, 0u, 0u };
                         if (LAT) {
                             const MoveData& m = ws.mv[jc][k - k0];
                             eA = cb + __umulhi(m.r0, n_c);
                             fdx = m.fdx; fdy = m.fdy; fcd = m.fcd; fsd = m.fsd;
-#pragma unroll
-                            for (int q = 0; q < 6; ++q) wr[q] = m.w[q];
                         } else {
                             const uint4 b0 = move_block(seed, sweep, (uint32_t)sigma, cell_local, k, 0);
                             const uint4 b1 = move_block(seed, sweep, (uint32_t)sigma, cell_local, k, 1);
@@ -401,8 +400,10 @@ k_set2d(Dev dv, Shape2 sh, int nxt, int sigma, const uint32_t* __restrict__ item
                             fcd = __fmul_rn(__fsub_rn(1.0f, ftt), finv);
                             fsd = __fmul_rn(__fadd_rn(ft, ft), finv);
                         }
+                        if (!LAT) {
 #pragma unroll
-                        for (int q = 0; q < 6; ++q) ws.rw[grp][q] = wr[q];
+                            for (int q = 0; q < 6; ++q) ws.rw[grp][q] = wr[q];
+                        }
                         ws.eA[grp] = (uint16_t)eA;
                         if (F32) {
                             const uint32_t gA = ws.gidx[eA];
@@ -425,8 +426,10 @@ k_set2d(Dev dv, Shape2 sh, int nxt, int sigma, const uint32_t* __restrict__ item
                                 status = 1;
                             } else {
                                 c_rechk += 1;
-                                const Trial2 t2 = propose2d(rp, B.px[gA], B.py[gA], B.q0[gA], B.q1[gA], wr[0],
-                                                            wr[1], wr[2], wr[3], wr[4], wr[5]);
+                                const Trial2 t2 =
+                                    LAT ? apply64(rp, B.px[gA], B.py[gA], B.q0[gA], B.q1[gA], ws.mv[jc][k - k0])
+                                        : propose2d(rp, B.px[gA], B.py[gA], B.q0[gA], B.q1[gA], wr[0], wr[1],
+                                                    wr[2], wr[3], wr[4], wr[5]);
                                 const bool ok = cell_axis(t2.x, shx, rp.L[0], rp.inv_w[0], nc0) == ix &&
                                                 cell_axis(t2.y, shy, rp.L[1], rp.inv_w[1], nc1) == iy;
                                 status = ok ? 1 : 2;
@@ -619,7 +622,9 @@ k_set2d(Dev dv, Shape2 sh, int nxt, int sigma, const uint32_t* __restrict__ item
                                     } else {
                                         c_rechk += 1;
                                         const uint32_t gA = ws.gidx[myA];
-                                        const Trial2 t2 = trial_of(rp, B, gA, ws.rw[grp]);
+                                        const Trial2 t2 = LAT ? apply64(rp, B.px[gA], B.py[gA], B.q0[gA], B.q1[gA],
+                                                                        ws.mv[jc][k - k0])
+                                                              : trial_of(rp, B, gA, ws.rw[grp]);
                                         const uint32_t gB = ws.gidx[e];
                                         const double Dx = min_image(B.px[gB] - t2.x, rp.L[0], rp.halfL[0]);
                                         const double Dy = min_image(B.py[gB] - t2.y, rp.L[1], rp.halfL[1]);

@@ -20,8 +20,12 @@
 
 namespace hpmc {
 
-// Random words and orientation step of one select (state independent).
-struct MoveData3 {
+// Random words and orientation step of one select (state independent).  The
+// latency-regime kernels (G >= 8) load the first chunk of a cell's selects
+// from the table k_selects wrote for the sweep (selects.cu); later chunks,
+// and every chunk of the other kernels, are computed here, one (cell,
+// select) per lane.
+struct __align__(16) MoveData3 {
     double dq[4];        // (1, v) / sqrt(1 + v.v), the contract's orientation step
     uint32_t w[12];      // words r1..r12
     uint32_t r0;         // pick word
@@ -113,6 +117,8 @@ k_set3d(Dev dv, const __grid_constant__ Shape3 sh, int nxt, int sigma, const uin
     const uint32_t nitems = item_base[dv.R];
     const uint32_t wpb = blockDim.x >> 5;
     const uint32_t wid = blockIdx.x * wpb + (threadIdx.x >> 5);
+    const MoveData3* __restrict__ msel = static_cast<const MoveData3*>(dv.msel);
+    const uint32_t mstride = dv.msel_stride;
     HPMC_STAMP_NS(dv, wid, lane, 28);
 
     for (uint32_t item = wid; item < nitems; item += gridDim.x * wpb) {
@@ -281,8 +287,12 @@ k_set3d(Dev dv, const __grid_constant__ Shape3 sh, int nxt, int sigma, const uin
             // (cell, select) per lane
             {
                 const uint32_t kk = k0 + (uint32_t)sl;
-                if (live_cell && kk < nsel)
-                    ws.mv[grp][sl] = precompute_select3(rp, seed, sweep, (uint32_t)sigma, cell_local, kk);
+                if (live_cell && kk < nsel) {
+                    if (G >= 8 && k0 == 0)
+                        ws.mv[grp][sl] = msel[(size_t)(rp.cbase + cell_local) * mstride + kk];
+                    else
+                        ws.mv[grp][sl] = precompute_select3(rp, seed, sweep, (uint32_t)sigma, cell_local, kk);
+                }
                 __syncwarp();
             }
             const uint32_t kend = min(nsel, k0 + (uint32_t)G);

@@ -123,6 +123,12 @@ struct Dev {
     uint64_t* sweep;         // [R] sweep counter per replica
     unsigned long long* counters;   // [R * kNumCounters]
     int* error;              // device error word (ERR_*)
+    // state-independent part of the first selects of every cell in the
+    // running sweep (latency-regime kernels only): record of select k of
+    // global cell c at c * msel_stride + k; msel_n records allocated
+    void* msel;
+    uint32_t msel_stride;    // min(largest nselect over the replicas, G)
+    uint64_t msel_n;
     // warp phase timestamps (trace builds only, -DHPMC_TRACE): kTracePoints
     // clock64() stamps of the first work item of each warp of a set kernel
     unsigned long long* trace;
