@@ -292,6 +292,18 @@ int hpmc_sdf(hpmc_t h, int32_t r, double x_max, uint32_t nbins, uint64_t* hist);
 int hpmc_pair_test(int dim, const double* verts, uint32_t nv, uint32_t n, const double* D,
                    const double* qA, const double* qB, int32_t* out64, int32_t* out32);
 
+/*
+ * hpmc_pair_test_warp3d -- the 3D FP64 contract test (GJK, Sec. 2.3 / Eq. 2)
+ * as the FP32-filtered 3D sweep evaluates its re-checks: one warp per pair,
+ * the independent parts of the computation spread over its lanes.  Inputs
+ * as hpmc_pair_test with dim = 3; out64[n] the verdict (1 overlap, 0
+ * separated), iters[n] the support evaluations after the first (33 when the
+ * iteration cap is reached).  For validation; synchronous; allocates and
+ * frees its own device buffers.
+ */
+int hpmc_pair_test_warp3d(const double* verts, uint32_t nv, uint32_t n, const double* D, const double* qA,
+                          const double* qB, int32_t* out64, int32_t* iters);
+
 /* Geometry of replica r: cells per axis, cell width, circumradius. */
 int hpmc_geometry(hpmc_t h, int32_t r, int32_t* nc, double* w, double* R);
 

@@ -726,9 +726,11 @@ int or_sweep(or_system* s, uint32_t N, double* pos, double* orient, uint64_t swe
     return 0;
 }
 
-/* Batch evaluation of the overlap contract on many pairs (for tests). */
-void or_overlap_batch(const or_system* s, uint32_t n, const double* D, const double* qA,
-                      const double* qB, int32_t* out)
+/* Batch evaluation of the overlap contract on many pairs (for tests); in 3D
+ * iters[p] (when iters is not NULL) receives the GJK's support evaluations
+ * after the first, the count or_overlap_3d reports. */
+void or_overlap_batch_it(const or_system* s, uint32_t n, const double* D, const double* qA,
+                         const double* qB, int32_t* out, int32_t* iters)
 {
     const int dim = s->dim, qd = (dim == 2) ? 2 : 4;
     for (uint32_t p = 0; p < n; ++p) {
@@ -736,8 +738,15 @@ void or_overlap_batch(const or_system* s, uint32_t n, const double* D, const dou
         else {
             int it = 0;
             out[p] = or_overlap_3d(s, D + 3 * (size_t)p, qA + (size_t)qd * p, qB + (size_t)qd * p, &it);
+            if (iters) iters[p] = it;
         }
     }
+}
+
+void or_overlap_batch(const or_system* s, uint32_t n, const double* D, const double* qA,
+                      const double* qB, int32_t* out)
+{
+    or_overlap_batch_it(s, n, D, qA, qB, out, 0);
 }
 
 /* ------------------------------------------------------------------------ */

@@ -65,6 +65,8 @@ def lib():
                                          ctypes.POINTER(ctypes.c_int)]
             L.or_overlap_batch.argtypes = [ctypes.c_void_p, ctypes.c_uint32, dp, dp, dp,
                                            ctypes.POINTER(ctypes.c_int32)]
+            L.or_overlap_batch_it.argtypes = [ctypes.c_void_p, ctypes.c_uint32, dp, dp, dp,
+                                              ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32)]
             L.or_sweep.restype = ctypes.c_int
             L.or_sweep.argtypes = [ctypes.c_void_p, ctypes.c_uint32, dp, dp, ctypes.c_uint64,
                                    ctypes.c_uint32, ctypes.POINTER(ctypes.c_uint64)]
@@ -213,17 +215,21 @@ class OracleSystem:
                              cof.ctypes.data_as(ctypes.POINTER(ctypes.c_int)))
         return start, idx[:N], cof[:N]
 
-    def overlap(self, D, qA, qB):
-        """Vectorised overlap contract D over pairs; returns int32 (1 = overlap)."""
+    def overlap(self, D, qA, qB, iters=False):
+        """Vectorised overlap contract D over pairs; returns int32 (1 = overlap),
+        and with iters=True (3D) also the GJK's support evaluations after the
+        first for each pair."""
         D = np.ascontiguousarray(D, dtype=np.float64).reshape(-1, self.dim)
         qd = 2 if self.dim == 2 else 4
         qA = np.ascontiguousarray(qA, dtype=np.float64).reshape(-1, qd)
         qB = np.ascontiguousarray(qB, dtype=np.float64).reshape(-1, qd)
         n = D.shape[0]
         out = np.zeros(n, dtype=np.int32)
-        lib().or_overlap_batch(self.ptr, n, _dp(D), _dp(qA), _dp(qB),
-                               out.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)))
-        return out
+        its = np.zeros(n, dtype=np.int32)
+        ip = ctypes.POINTER(ctypes.c_int32)
+        lib().or_overlap_batch_it(self.ptr, n, _dp(D), _dp(qA), _dp(qB), out.ctypes.data_as(ip),
+                                  its.ctypes.data_as(ip))
+        return (out, its) if iters else out
 
     def sweep(self, pos, orient, sweep0, nsweeps):
         """Run nsweeps sweeps in place on (pos, orient) in tag order.

@@ -11,12 +11,14 @@
 // not split further), skipping pairs of moves already known to overlap.
 //
 // F32 = true : cull and in-cell decisions certified in FP32; each pair runs
-//              the certified FP32 GJK (hpmc_gjk32.cuh) and falls back to the
-//              FP64 contract GJK when a branch cannot be certified.
+//              the certified FP32 GJK (hpmc_gjk32.cuh); the pairs it cannot
+//              certify are then re-decided by the FP64 contract GJK, one pair
+//              at a time by the whole warp (hpmc_gjk64w.cuh).
 // F32 = false: plain FP64 contract.
 #pragma once
 #include "hpmc_device.cuh"
 #include "hpmc_gjk32.cuh"
+#include "hpmc_gjk64w.cuh"
 
 namespace hpmc {
 
@@ -71,7 +73,7 @@ struct Warp3 {
     uint16_t qe[QCAP];
     uint8_t qg[QCAP];
     float4 tra[S], trb[S];                            // FP32 trial: rel', qw' / qx', qy', qz'
-    double tp[S][3], tq[S][4];                        // FP64 trial (FP64 form)
+    double tp[S][3], tq[S][4];                        // FP64 trial (position: FP64 form; orientation: both)
     uint32_t rw[S][12];                               // words r1..r12
     uint16_t eA[S];
     MoveData3 mv[S][G];                               // selects of the current chunk
@@ -84,15 +86,15 @@ __device__ __forceinline__ uint32_t row_count3(const uint32_t* start, uint32_t r
     return (start[rowbase + nc0] - start[rowbase + xa]) + (start[rowbase + (xa + len - nc0)] - start[rowbase]);
 }
 
-__device__ __forceinline__ Trial3 trial3_of(const Rep& rp, const Bufs& B, uint32_t gA, const uint32_t* w12)
+// FP64 trial position of the contract from words r1..r6 (the position part
+// of propose3d, same operations); the rare FP64 paths of the FP32 form take
+// the trial orientation from the proposal (ws.tq) instead of recomputing it.
+__device__ __forceinline__ void trial3_pos(const Rep& rp, const Bufs& B, uint32_t gA, const uint32_t* w12,
+                                           double x[3])
 {
-    const double x[3] = { B.px[gA], B.py[gA], B.pz[gA] };
-    const double q[4] = { B.q0[gA], B.q1[gA], B.q2[gA], B.q3[gA] };
-    uint32_t r[13];
-    r[0] = 0;
-#pragma unroll
-    for (int k = 0; k < 12; ++k) r[k + 1] = w12[k];
-    return propose3d(rp, x, q, r);
+    x[0] = wrap_pos_bits(B.px[gA] + rp.d_s * pm53(w12[0], w12[1]), rp.L[0]);
+    x[1] = wrap_pos_bits(B.py[gA] + rp.d_s * pm53(w12[2], w12[3]), rp.L[1]);
+    x[2] = wrap_pos_bits(B.pz[gA] + rp.d_s * pm53(w12[4], w12[5]), rp.L[2]);
 }
 
 template <int G, bool F32, int NV>
@@ -322,10 +324,11 @@ k_set3d(Dev dv, const __grid_constant__ Shape3 sh, int nxt, int sigma, const uin
                             status = 1;
                         } else {
                             c_rechk += 1;
-                            const Trial3 t3 = trial3_of(rp, B, ws.gidx[eA], ws.rw[grp]);
-                            const bool ok = cell_axis(t3.x[0], shx, rp.L[0], rp.inv_w[0], nc0) == ix &&
-                                            cell_axis(t3.x[1], shy, rp.L[1], rp.inv_w[1], nc1) == iy &&
-                                            cell_axis(t3.x[2], shz, rp.L[2], rp.inv_w[2], nc2) == iz;
+                            double x[3];
+                            trial3_pos(rp, B, ws.gidx[eA], ws.rw[grp], x);
+                            const bool ok = cell_axis(x[0], shx, rp.L[0], rp.inv_w[0], nc0) == ix &&
+                                            cell_axis(x[1], shy, rp.L[1], rp.inv_w[1], nc1) == iy &&
+                                            cell_axis(x[2], shz, rp.L[2], rp.inv_w[2], nc2) == iz;
                             status = ok ? 1 : 2;
                         }
                     } else {
@@ -429,11 +432,12 @@ k_set3d(Dev dv, const __grid_constant__ Shape3 sh, int nxt, int sigma, const uin
                                     keep = false;
                                 } else {
                                     c_rechk += 1;
-                                    const Trial3 t3 = trial3_of(rp, B, ws.gidx[myA], ws.rw[grp]);
+                                    double x[3];
+                                    trial3_pos(rp, B, ws.gidx[myA], ws.rw[grp], x);
                                     const uint32_t gB = ws.gidx[e];
-                                    const double Dx = min_image(B.px[gB] - t3.x[0], rp.L[0], rp.halfL[0]);
-                                    const double Dy = min_image(B.py[gB] - t3.x[1], rp.L[1], rp.halfL[1]);
-                                    const double Dz = min_image(B.pz[gB] - t3.x[2], rp.L[2], rp.halfL[2]);
+                                    const double Dx = min_image(B.px[gB] - x[0], rp.L[0], rp.halfL[0]);
+                                    const double Dy = min_image(B.py[gB] - x[1], rp.L[1], rp.halfL[1]);
+                                    const double Dz = min_image(B.pz[gB] - x[2], rp.L[2], rp.halfL[2]);
                                     keep = ((Dx * Dx + Dy * Dy) + Dz * Dz) <= sh.rc2;
                                 }
                             } else {
@@ -466,12 +470,13 @@ k_set3d(Dev dv, const __grid_constant__ Shape3 sh, int nxt, int sigma, const uin
                     __syncwarp();
                     while (qn >= 32 || (!any_live && qn > 0)) {
                         const int np = qn < 32 ? qn : 32;
+                        bool need64 = false;                       // FP32 verdict uncertain
                         if (lane < np) {
                             const int e2 = ws.qe[lane];
                             const int g2 = ws.qg[lane];
                             if (!((ws.ovmask >> g2) & 1u)) {
                                 c_chk += 1;
-                                bool ov;
+                                bool ov = false;
                                 int its = 0;
                                 if (F32) {
                                     const float4 d2 = ws.qd[lane];
@@ -481,19 +486,8 @@ k_set3d(Dev dv, const __grid_constant__ Shape3 sh, int nxt, int sigma, const uin
                                                                  make_float4(a1.w, a2.x, a2.y, a2.z),
                                                                  make_float4(b1.w, b2.x, b2.y, b2.z), rp.e_pb32,
                                                                  rp.e_va32, rp.tau3);
-                                    if (v >= GJK32_UNCERTAIN) {
-                                        c_rechk += 1;
-                                        const Trial3 t3 = trial3_of(rp, B, ws.gidx[ws.eA[g2]], ws.rw[g2]);
-                                        const uint32_t gB = ws.gidx[e2];
-                                        const double D[3] = { min_image(B.px[gB] - t3.x[0], rp.L[0], rp.halfL[0]),
-                                                              min_image(B.py[gB] - t3.x[1], rp.L[1], rp.halfL[1]),
-                                                              min_image(B.pz[gB] - t3.x[2], rp.L[2], rp.halfL[2]) };
-                                        const double qB[4] = { B.q0[gB], B.q1[gB], B.q2[gB], B.q3[gB] };
-                                        its = 0;
-                                        ov = overlap3d64<NV>(sh, D, t3.q, qB, &its);
-                                    } else {
-                                        ov = (v == GJK32_OVERLAP);
-                                    }
+                                    need64 = v >= GJK32_UNCERTAIN;
+                                    ov = (v == GJK32_OVERLAP);
                                 } else {
                                     const double D[3] = { min_image(ws.ep[e2][0] - ws.tp[g2][0], rp.L[0], rp.halfL[0]),
                                                           min_image(ws.ep[e2][1] - ws.tp[g2][1], rp.L[1], rp.halfL[1]),
@@ -504,6 +498,37 @@ k_set3d(Dev dv, const __grid_constant__ Shape3 sh, int nxt, int sigma, const uin
                                 }
                                 if (its > kGjkMaxIt) c_cap += 1;
                                 if (ov) atomicOr(&ws.ovmask, 1u << g2);
+                            }
+                        }
+                        if (F32) {
+                            // the uncertain pairs, one at a time by the whole warp
+                            // (FP64 contract; a pair whose cell already overlaps
+                            // is skipped: its move is rejected either way)
+                            unsigned um = __ballot_sync(FULL, need64);
+                            __syncwarp();
+#pragma unroll 1
+                            while (um != 0u) {
+                                const int src = __ffs(um) - 1;
+                                um &= um - 1u;
+                                const int g2 = ws.qg[src];
+                                if ((ws.ovmask >> g2) & 1u) continue;
+                                const int e2 = ws.qe[src];
+                                double x[3];
+                                trial3_pos(rp, B, ws.gidx[ws.eA[g2]], ws.rw[g2], x);
+                                const uint32_t gB = ws.gidx[e2];
+                                const double D[3] = { min_image(B.px[gB] - x[0], rp.L[0], rp.halfL[0]),
+                                                      min_image(B.py[gB] - x[1], rp.L[1], rp.halfL[1]),
+                                                      min_image(B.pz[gB] - x[2], rp.L[2], rp.halfL[2]) };
+                                const double qa[4] = { ws.tq[g2][0], ws.tq[g2][1], ws.tq[g2][2], ws.tq[g2][3] };
+                                const double qB[4] = { B.q0[gB], B.q1[gB], B.q2[gB], B.q3[gB] };
+                                int its = 0;
+                                const bool ov = overlap3d64_warp<NV>(sh, D, qa, qB, &its);
+                                if (lane == src) {
+                                    c_rechk += 1;
+                                    if (its > kGjkMaxIt) c_cap += 1;
+                                }
+                                if (ov && lane == 0) ws.ovmask |= 1u << g2;
+                                __syncwarp();
                             }
                         }
                         __syncwarp();

@@ -10,6 +10,7 @@
 #include "hpmc_device.cuh"
 #include "hpmc_filter.cuh"
 #include "hpmc_gjk32.cuh"
+#include "hpmc_gjk64w.cuh"
 #include "hpmc_shape.h"
 
 namespace {
@@ -44,6 +45,24 @@ __global__ void k_pairs3d(const __grid_constant__ Shape3 sh, float e_pb, float e
     const float4 fb = make_float4((float)b[0], (float)b[1], (float)b[2], (float)b[3]);
     const int v = gjk32_cert<0>(sh, (float)d[0], (float)d[1], (float)d[2], fa, fb, e_pb, e_va, tau);
     o32[i] = v;   // 0, 1, or the reason it is uncertain (>= 2)
+}
+
+// one warp per pair: the warp-cooperative FP64 GJK the FP32-filtered 3D
+// kernels use for their re-checks
+__global__ void k_pairs3d_warp(const __grid_constant__ Shape3 sh, uint32_t n, const double* D, const double* qA,
+                               const double* qB, int32_t* o64, int32_t* oit)
+{
+    const uint32_t i = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (i >= n) return;                               // whole warps leave together
+    const double d[3] = { D[3 * i], D[3 * i + 1], D[3 * i + 2] };
+    const double a[4] = { qA[4 * i], qA[4 * i + 1], qA[4 * i + 2], qA[4 * i + 3] };
+    const double b[4] = { qB[4 * i], qB[4 * i + 1], qB[4 * i + 2], qB[4 * i + 3] };
+    int it = 0;
+    const bool ov = overlap3d64_warp<0>(sh, d, a, b, &it);
+    if ((threadIdx.x & 31) == 0) {
+        o64[i] = ov ? 1 : 0;
+        oit[i] = it;
+    }
 }
 
 float up32(double x)
@@ -111,6 +130,45 @@ extern "C" int hpmc_pair_test(int dim, const double* verts, uint32_t nv, uint32_
     cudaFree(dB);
     cudaFree(d64);
     cudaFree(d32);
+    if (e != cudaSuccess) {
+        (void)cudaGetLastError();
+        return e == cudaErrorMemoryAllocation ? HPMC_ERR_OOM : HPMC_ERR_CUDA;
+    }
+    return 0;
+}
+
+extern "C" int hpmc_pair_test_warp3d(const double* verts, uint32_t nv, uint32_t n, const double* D,
+                                     const double* qA, const double* qB, int32_t* out64, int32_t* iters)
+{
+    if (!D || !qA || !qB || !out64 || !iters) return HPMC_ERR_INVALID_ARG;
+    Shape2 s2{};
+    Shape3 s3{};
+    double Rc = 0.0, rc2 = 0.0;
+    int rc = build_shapes(3, verts, nv, s2, s3, Rc, rc2);
+    if (rc) return rc;
+    if (n == 0) return 0;
+    double *dD = nullptr, *dA = nullptr, *dB = nullptr;
+    int32_t *d64 = nullptr, *dit = nullptr;
+    cudaError_t e = cudaMalloc(&dD, sizeof(double) * n * 3);
+    if (e == cudaSuccess) e = cudaMalloc(&dA, sizeof(double) * n * 4);
+    if (e == cudaSuccess) e = cudaMalloc(&dB, sizeof(double) * n * 4);
+    if (e == cudaSuccess) e = cudaMalloc(&d64, sizeof(int32_t) * n);
+    if (e == cudaSuccess) e = cudaMalloc(&dit, sizeof(int32_t) * n);
+    if (e == cudaSuccess) e = cudaMemcpy(dD, D, sizeof(double) * n * 3, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(dA, qA, sizeof(double) * n * 4, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(dB, qB, sizeof(double) * n * 4, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) {
+        const uint32_t wpb = 4;
+        k_pairs3d_warp<<<(n + wpb - 1) / wpb, 32 * wpb>>>(s3, n, dD, dA, dB, d64, dit);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpy(out64, d64, sizeof(int32_t) * n, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemcpy(iters, dit, sizeof(int32_t) * n, cudaMemcpyDeviceToHost);
+    cudaFree(dD);
+    cudaFree(dA);
+    cudaFree(dB);
+    cudaFree(d64);
+    cudaFree(dit);
     if (e != cudaSuccess) {
         (void)cudaGetLastError();
         return e == cudaErrorMemoryAllocation ? HPMC_ERR_OOM : HPMC_ERR_CUDA;

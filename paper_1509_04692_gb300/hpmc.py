@@ -33,6 +33,7 @@ EXPORTS = [
     "hpmc_filter_margins", "hpmc_strerror", "hpmc_profile_sweeps", "hpmc_count_overlaps_noalloc",
     "hpmc_trace_read", "hpmc_pair_test", "hpmc_sdf", "hpmc_box_move", "hpmc_get_box",
     "hpmc_tune_moves", "hpmc_msd_reset", "hpmc_msd_update", "hpmc_msd_read", "hpmc_debug_fail_alloc",
+    "hpmc_pair_test_warp3d",
 ]
 
 
@@ -93,6 +94,8 @@ def _load():
         "hpmc_trace_read": [vp, ctypes.POINTER(u64), u32, ctypes.POINTER(u32)],
         "hpmc_pair_test": [ctypes.c_int, dp, u32, u32, dp, dp, dp, ctypes.POINTER(ctypes.c_int32),
                            ctypes.POINTER(ctypes.c_int32)],
+        "hpmc_pair_test_warp3d": [dp, u32, u32, dp, dp, dp, ctypes.POINTER(ctypes.c_int32),
+                                  ctypes.POINTER(ctypes.c_int32)],
         "hpmc_sdf": [ctypes.c_void_p, ctypes.c_int32, ctypes.c_double, u32, ctypes.POINTER(ctypes.c_uint64)],
         "hpmc_box_move": [ctypes.c_void_p, ctypes.c_int32, ctypes.c_double, ctypes.c_double,
                           ctypes.POINTER(ctypes.c_int)],
@@ -341,6 +344,25 @@ def pair_test(dim, verts, D, qA, qB):
     _ck(_lib.hpmc_pair_test(int(dim), _dp(v), v.shape[0], n, _dp(D), _dp(qA), _dp(qB),
                             o64.ctypes.data_as(ip), o32.ctypes.data_as(ip)), "hpmc_pair_test")
     return o64, o32
+
+
+def pair_test_warp3d(verts, D, qA, qB):
+    """The 3D FP64 contract test as the FP32-filtered sweep evaluates its
+    re-checks (one warp per pair).  Returns (out64, iters).  A scalar verts
+    is the radius of a sphere."""
+    round_ = np.ndim(verts) == 0
+    v = np.array([float(verts)]) if round_ else _c64(verts).reshape(-1, 3)
+    nv = 0 if round_ else v.shape[0]
+    D = _c64(D).reshape(-1, 3)
+    qA = _c64(qA).reshape(-1, 4)
+    qB = _c64(qB).reshape(-1, 4)
+    n = D.shape[0]
+    o64 = np.zeros(n, dtype=np.int32)
+    its = np.zeros(n, dtype=np.int32)
+    ip = ctypes.POINTER(ctypes.c_int32)
+    _ck(_lib.hpmc_pair_test_warp3d(_dp(v), nv, n, _dp(D), _dp(qA), _dp(qB), o64.ctypes.data_as(ip),
+                                   its.ctypes.data_as(ip)), "hpmc_pair_test_warp3d")
+    return o64, its
 
 
 def from_system(sysm, w_min=None):

@@ -104,3 +104,64 @@ def test_aligned_cubes_ties():
     D = rng.uniform(-1.6, 1.6, size=(n, 3))
     I = np.tile([1.0, 0, 0, 0], (n, 1))
     _check(3, v, D, I, I, 0.5)
+
+
+def _polyhedron(name, rng):
+    if name == "cube":
+        return inputs.cube(1.0)
+    if name == "octahedron":
+        return np.array([[1, 0, 0], [-1, 0, 0], [0, 1, 0], [0, -1, 0], [0, 0, 1], [0, 0, -1]], float) * 0.6
+    if name == "dodecahedron":
+        return inputs.dodecahedron(1.0)
+    p = rng.normal(size=(int(name[6:]), 3))                  # "random<n>": points on a sphere
+    return 0.5 * p / np.linalg.norm(p, axis=1)[:, None]
+
+
+@pytest.mark.parametrize("shape", ["cube", "octahedron", "random16", "dodecahedron", "random24", "random32"])
+def test_warp_gjk_equals_the_contract(shape):
+    # the FP64 GJK the FP32-filtered 3D sweep uses for its re-checks (one warp
+    # per pair, lanes sharing the vertices, supports and faces) gives the
+    # oracle's verdict after the same number of support evaluations
+    rng = np.random.default_rng(sum(map(ord, shape)))
+    v = _polyhedron(shape, rng)
+    R = np.sqrt((v ** 2).sum(1)).max()
+    s = orc.OracleSystem(3, [50.0] * 3, v)
+    n = 40000
+    d = rng.normal(size=(n, 3))
+    d /= np.linalg.norm(d, axis=1)[:, None]
+    D = d * (2 * R * 1.02 * rng.uniform(0, 1, n) ** (1 / 3))[:, None]
+    qA, qB = _quats(rng, n), _quats(rng, n)
+    m = 10000                                       # the first m pairs moved to near contact
+    lo, hi = np.zeros(m), np.full(m, 2 * R * 1.001)
+    for _ in range(45):
+        mid = 0.5 * (lo + hi)
+        ov = s.overlap(d[:m] * mid[:, None], qA[:m], qB[:m]).astype(bool)
+        lo, hi = np.where(ov, mid, lo), np.where(ov, hi, mid)
+    off = rng.choice([-1, 1], m) * 10.0 ** rng.uniform(-12, -3, m)
+    D[:m] = d[:m] * (0.5 * (lo + hi) + off)[:, None]
+    ref, rit = s.overlap(D, qA, qB, iters=True)
+    got, git = hpmc.pair_test_warp3d(v, D, qA, qB)
+    assert np.array_equal(got, ref), np.nonzero(got != ref)[0][:10]
+    assert np.array_equal(git, rit), np.nonzero(git != rit)[0][:10]
+    assert 0.1 < ref.mean() < 0.9 and rit.max() >= 3
+
+
+def test_warp_gjk_ties_and_spheres():
+    # identical orientations make every support query tie (the first vertex
+    # of the extremum must win, as in the one-lane scan); spheres take the
+    # distance branch
+    rng = np.random.default_rng(6)
+    v = inputs.cube(1.0)
+    n = 30000
+    D = rng.uniform(-1.6, 1.6, size=(n, 3))
+    D[: n // 3] = np.round(D[: n // 3] * 4) / 4                # exact ties of the dot products too
+    I = np.tile([1.0, 0, 0, 0], (n, 1))
+    s = orc.OracleSystem(3, [50.0] * 3, v)
+    ref, rit = s.overlap(D, I, I, iters=True)
+    got, git = hpmc.pair_test_warp3d(v, D, I, I)
+    assert np.array_equal(got, ref) and np.array_equal(git, rit)
+    sph = orc.OracleSystem(3, [50.0] * 3, 0.5)
+    qA, qB = _quats(rng, n), _quats(rng, n)
+    ref = sph.overlap(D, qA, qB)
+    got, git = hpmc.pair_test_warp3d(np.array(0.5), D, qA, qB)
+    assert np.array_equal(got, ref) and not git.any()
