@@ -110,9 +110,6 @@ __device__ __forceinline__ bool gjk_reduce_w(double sp[4][3], int& n, double v[3
     } else {
         // faces {0,1,2} opp 3, {0,1,3} opp 2, {0,2,3} opp 1, {1,2,3} opp 0
         const int f = lane & 3;
-        const int i0 = (f == 3) ? 1 : 0;
-        const int i1 = (f <= 1) ? 1 : 2;
-        const int i2 = (f == 0) ? 2 : 3;
         double P0[3], P1[3], P2[3], P3[3];
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
