@@ -467,10 +467,14 @@ int enqueue_sets(hpmc_batch* h, cudaStream_t st)
         args[2] = &nx;
         args[3] = &sg;
         args[4] = (void*)&ib;
-        // The set kernels keep the full stream dependency: launched early,
-        // their waiting blocks cost more than the saved latency (measured on
-        // the 4096-pentagon fluid: -8% moves/s, plain FP64 form -19%).
-        CK(cudaLaunchKernel(h->cfg_fn, dim3(h->cfg_grid), dim3(32 * h->wpb), args, h->cfg_smem, st));
+        // Sets 1.. are launched with programmatic stream serialisation and
+        // only wait (pdl_wait): the next set's launch is prepared while the
+        // previous one drains (4096-pentagon fluid +2.5%).  Set 0 keeps the
+        // full dependency on the rebuild, whose kernels let their successor
+        // be scheduled early: its blocks would wait beside k_place.
+        PdlLaunch L(dim3(h->cfg_grid), dim3(32 * h->wpb), h->cfg_smem, st);
+        if (sigma == 0) L.cfg.numAttrs = 0;
+        CK(cudaLaunchKernelExC(&L.cfg, h->cfg_fn, args));
     }
     h->cur = nxt;
     return 0;

@@ -27,6 +27,15 @@ __device__ __forceinline__ void pdl_enter()
     asm volatile("griddepcontrol.wait;" ::: "memory");
 }
 
+// The set kernels are launched with the same attribute but only wait: they
+// never let the next kernel be scheduled before their blocks exit (waiting
+// blocks beside a running set kernel measured slower), so what overlaps is
+// the next launch's setup with the drain of this one.
+__device__ __forceinline__ void pdl_wait()
+{
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+}
+
 // ---------------------------------------------------------------- Philox
 // Philox4x32-10 (Salmon, Moraes, Dror & Shaw, SC'11): ten rounds, each two
 // 32x32->64 multiplies whose halves are xored with the other counter words

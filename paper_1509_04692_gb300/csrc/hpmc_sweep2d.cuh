@@ -144,7 +144,7 @@ template <int G, bool F32, int NV>
 __global__ void __launch_bounds__(G >= 8 ? 256 : 192, 2)
 k_set2d(Dev dv, Shape2 sh, int nxt, int sigma, const uint32_t* __restrict__ item_base)
 {
-    pdl_enter();
+    pdl_wait();
     using W = Warp2<G, F32>;
     constexpr int S = W::S;
     constexpr bool LAT = W::LAT;

@@ -105,7 +105,7 @@ template <int G, bool F32, int NV>
 __global__ void __launch_bounds__(256, 1)
 k_set3d(Dev dv, const __grid_constant__ Shape3 sh, int nxt, int sigma, const uint32_t* __restrict__ item_base)
 {
-    pdl_enter();
+    pdl_wait();
     using W = Warp3<G, F32>;
     constexpr int S = W::S;
     extern __shared__ __align__(16) unsigned char smem_raw[];
