@@ -51,7 +51,7 @@ FLOPS = {2: (FLOP_MOVE, FLOP_CULL, FLOP_SAT), 3: (80, 8, 1000)}
 # DRAM bytes (read + write) of one set launch of this workload from ncu
 # (profiles/set2d_fluid4096.md, cold-cache replay); valid for the kernel as
 # captured there
-SET2D_FLUID_DRAM_BYTES = 227328
+SET2D_FLUID_DRAM_BYTES = 466432
 
 
 def job_totals(torch, ms, moves, device):
