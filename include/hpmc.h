@@ -113,6 +113,17 @@ int hpmc_destroy(hpmc_t h);
  */
 int hpmc_set_moves(hpmc_t h, int32_t r, double d, double a, uint32_t nselect);
 
+/*
+ * hpmc_set_cell_width_min -- new floor w_min >= 0 on the cell width of every
+ * replica (the w_min of creation; 0 = the circumdiameter, the paper's
+ * minimum, Sec. 2.2.1).  The cell grid follows the creation rule; the next
+ * sweep rebuilds the cell list.  Moves per sweep depend on the grid (one
+ * select stream per cell), so trajectories with different floors differ.
+ * BOX_TOO_SMALL (grid unchanged) when a replica would get fewer than 4 cells
+ * on an axis; INVALID_ARG for a negative or non-finite w_min.  Synchronous.
+ */
+int hpmc_set_cell_width_min(hpmc_t h, double w_min);
+
 /* hpmc_set_precision -- HPMC_FP64 or HPMC_FP32_FILTERED (default).  Both give
  * identical trajectories; the filtered form is faster. */
 int hpmc_set_precision(hpmc_t h, int mode);

@@ -749,6 +749,30 @@ int hpmc_set_moves(hpmc_t h, int32_t r, double d, double a, uint32_t nselect)
     return 0;
 }
 
+int relayout(hpmc_batch* h);
+
+int hpmc_set_cell_width_min(hpmc_t h, double w_min)
+{
+    if (!h || !is_finite(w_min) || w_min < 0.0) return HPMC_ERR_INVALID_ARG;
+    CK(cudaDeviceSynchronize());
+    const double w_old = h->w_min;
+    h->w_min = w_min;
+    std::vector<Rep> fresh(h->reps);
+    for (uint32_t r = 0; r < h->R; ++r) {
+        const int rc = rep_geometry(h, h->hr[r], fresh[r]);
+        if (rc) {
+            h->w_min = w_old;                           // the grid is unchanged
+            return rc;
+        }
+        fresh[r].pbase = h->reps[r].pbase;
+    }
+    h->reps = fresh;                                    // cbase: relayout
+    const int rc = relayout(h);
+    if (rc) return rc;
+    CK(cudaDeviceSynchronize());                        // the next sweep rebuilds cells and mirrors
+    return 0;
+}
+
 int hpmc_set_precision(hpmc_t h, int mode)
 {
     if (!h || (mode != HPMC_FP64 && mode != HPMC_FP32_FILTERED)) return HPMC_ERR_INVALID_ARG;

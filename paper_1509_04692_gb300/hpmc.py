@@ -33,7 +33,7 @@ EXPORTS = [
     "hpmc_filter_margins", "hpmc_strerror", "hpmc_profile_sweeps", "hpmc_count_overlaps_noalloc",
     "hpmc_trace_read", "hpmc_pair_test", "hpmc_sdf", "hpmc_box_move", "hpmc_get_box",
     "hpmc_tune_moves", "hpmc_msd_reset", "hpmc_msd_update", "hpmc_msd_read", "hpmc_debug_fail_alloc",
-    "hpmc_pair_test_warp3d",
+    "hpmc_pair_test_warp3d", "hpmc_set_cell_width_min",
 ]
 
 
@@ -77,6 +77,7 @@ def _load():
         "hpmc_set_moves": [vp, i32, ctypes.c_double, ctypes.c_double, u32],
         "hpmc_set_precision": [vp, ctypes.c_int],
         "hpmc_set_group_size": [vp, ctypes.c_int, ctypes.c_int],
+        "hpmc_set_cell_width_min": [vp, ctypes.c_double],
         "hpmc_sweep": [vp, u32, vp],
         "hpmc_sweep_graph": [vp, u32, vp],
         "hpmc_sync": [vp],
@@ -199,6 +200,10 @@ class Batch:
     # ---- configuration
     def set_moves(self, d, a, nselect, r=-1):
         _ck(_lib.hpmc_set_moves(self.h, int(r), float(d), float(a), int(nselect)), "hpmc_set_moves")
+
+    def set_cell_width_min(self, w_min):
+        """Floor on the cell width of every replica (0 = the circumdiameter)."""
+        _ck(_lib.hpmc_set_cell_width_min(self.h, float(w_min)), "hpmc_set_cell_width_min")
 
     def set_precision(self, mode):
         _ck(_lib.hpmc_set_precision(self.h, int(mode)), "hpmc_set_precision")

@@ -132,3 +132,31 @@ def test_switching_regimes_keeps_the_trajectory():
     b.close()
     assert sw == 12
     _same(gp, gq, p, q)
+
+
+@pytest.mark.parametrize("lanes", [4, 16])
+def test_cell_width_floor_set_after_creation(lanes):
+    # created on the paper's minimal grid, then switched to a coarser floor:
+    # the trajectory is the oracle's on the coarser grid from then on
+    s = inputs.pentagon_system(1200, 0.5, 41, d=0.12, a=0.15)
+    b = hpmc.from_system(s)
+    b.set_group_size(lanes, 2 if lanes >= 8 else 4)
+    nc0 = b.geometry()["nc"][0]
+    b.set_cell_width_min(1.7)
+    g = b.geometry()
+    o = orc.OracleSystem(2, s.L, s.verts, w_min=1.7)
+    assert g["nc"][0] < nc0 and g["nc"][0] == o.geometry()["nc"][0]
+    o.set_moves(s.d, s.a, s.nselect, s.seed)
+    p, q = s.pos.copy(), s.orient.copy()
+    rc = o.sweep(p, q, 0, 12)
+    b.sweep(12, graph=True)
+    c = b.counters()
+    assert (c["accept"], c["reject_overlap"], c["reject_boundary"]) == tuple(int(x) for x in rc[:3])
+    gp, gq, _ = b.get_state()
+    _same(gp, gq, p, q)
+    # a floor leaving fewer than 4 cells is refused and the grid kept
+    with pytest.raises(hpmc.HPMCError) as e:
+        b.set_cell_width_min(s.L[0] / 3.0)
+    assert e.value.code == -2
+    assert b.geometry()["nc"][0] == g["nc"][0]
+    b.close()
