@@ -19,18 +19,19 @@ namespace hpmc {
 // its memory is visible.  Nothing is read or written before the wait, so the
 // order of the stream is kept; what is saved is the launch latency between
 // the short rebuild kernels (24 -> 16 us per sweep of 4096 particles).  In a
-// kernel launched without the attribute (the set kernels) the wait returns
-// at once.
+// kernel launched without the attribute (the first set kernel of a sweep)
+// the wait returns at once.
 __device__ __forceinline__ void pdl_enter()
 {
     asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     asm volatile("griddepcontrol.wait;" ::: "memory");
 }
 
-// The set kernels are launched with the same attribute but only wait: they
-// never let the next kernel be scheduled before their blocks exit (waiting
-// blocks beside a running set kernel measured slower), so what overlaps is
-// the next launch's setup with the drain of this one.
+// The set kernels after the first of a sweep are launched with the same
+// attribute but only wait: no set kernel lets the next kernel be scheduled
+// before its blocks exit (waiting blocks beside a running set kernel
+// measured slower), so what overlaps is the next launch's setup with the
+// drain of this one.
 __device__ __forceinline__ void pdl_wait()
 {
     asm volatile("griddepcontrol.wait;" ::: "memory");
