@@ -151,13 +151,22 @@ __device__ __forceinline__ SPt g_support(int nv, const G32* pb, const Shape3& sh
 {
     int ib = 0, ia = 0;
     float best = g_dot(pb[0], d), least = g_dot(vA(sh, 0), d);
-#pragma unroll
-    for (int i = 1; i < (NV ? NV : kMaxV3); ++i) {
-        if (!NV && i >= nv) break;
+    auto step = [&](int i) {
         const float t = g_dot(pb[i], d);
         if (t > best) { best = t; ib = i; }
         const float u = g_dot(vA(sh, i), d);
         if (u < least) { least = u; ia = i; }
+    };
+    if constexpr (NV >= 16) {
+        // many vertices: a partly unrolled loop keeps the body small
+#pragma unroll 4
+        for (int i = 1; i < NV; ++i) step(i);
+    } else {
+#pragma unroll
+        for (int i = 1; i < (NV ? NV : kMaxV3); ++i) {
+            if (!NV && i >= nv) break;
+            step(i);
+        }
     }
     return { g_sub(pb[ib], vA(sh, ia)), ib, ia };
 }
@@ -256,13 +265,21 @@ __device__ __forceinline__ bool cert_separated(int nv, const G32* pb, const Shap
 {
     float minB = g_dot(pb[0], nrm), maxA = g_dot(vA(sh, 0), nrm);
     float P = 0.f, V = 0.f;
-#pragma unroll
-    for (int i = 0; i < (NV ? NV : kMaxV3); ++i) {
-        if (!NV && i >= nv) break;
+    auto step = [&](int i) {
         minB = fminf(minB, g_dot(pb[i], nrm));
         maxA = fmaxf(maxA, g_dot(vA(sh, i), nrm));
         P = fmaxf(P, fmaxf(fabsf(pb[i].x), fmaxf(fabsf(pb[i].y), fabsf(pb[i].z))));
         V = fmaxf(V, fmaxf(fabsf(vA(sh, i).x), fmaxf(fabsf(vA(sh, i).y), fabsf(vA(sh, i).z))));
+    };
+    if constexpr (NV >= 16) {
+#pragma unroll 4
+        for (int i = 0; i < NV; ++i) step(i);
+    } else {
+#pragma unroll
+        for (int i = 0; i < (NV ? NV : kMaxV3); ++i) {
+            if (!NV && i >= nv) break;
+            step(i);
+        }
     }
     const float n1 = __fadd_ru(__fadd_ru(fabsf(nrm.x), fabsf(nrm.y)), fabsf(nrm.z));
     const float gap = minB - maxA;
