@@ -395,11 +395,19 @@ __device__ __forceinline__ int gjk32_cert(const Shape3& sh, float dx, float dy, 
     };
     const G32 l = rot(a0, a1, a2, a3, G32{ dx, dy, dz });
     G32 pb[NV ? NV : kMaxV3];
+    if constexpr (NV >= 16) {
+#pragma unroll 4
+        for (int i = 0; i < NV; ++i) {
+            const G32 rr = rot(r0, r1, r2, r3, vA(sh, i));
+            pb[i] = G32{ rr.x + l.x, rr.y + l.y, rr.z + l.z };
+        }
+    } else {
 #pragma unroll
-    for (int i = 0; i < (NV ? NV : kMaxV3); ++i) {
-        if (!NV && i >= nv) break;
-        const G32 rr = rot(r0, r1, r2, r3, vA(sh, i));
-        pb[i] = G32{ rr.x + l.x, rr.y + l.y, rr.z + l.z };
+        for (int i = 0; i < (NV ? NV : kMaxV3); ++i) {
+            if (!NV && i >= nv) break;
+            const G32 rr = rot(r0, r1, r2, r3, vA(sh, i));
+            pb[i] = G32{ rr.x + l.x, rr.y + l.y, rr.z + l.z };
+        }
     }
     // the centre line first: well-separated pairs are certified without GJK
     if (cert_separated<NV>(nv, pb, sh, l, e_pb, e_va, tau)) return GJK32_SEPARATED;
