@@ -100,3 +100,26 @@ def test_gjk_general_polyhedra_vs_clipping(shape):
     assert not np.any(got & sure_sep)
     assert not np.any(~got & sure_ov)
     assert sure_ov.sum() > 300 and sure_sep.sum() > 300
+
+
+def test_gjk_iteration_counts():
+    # the oracle reports the GJK's support evaluations after the first (the
+    # GPU pair tests compare them): the verdict is the same with or without
+    # the count; every count lies in 1..33 (33 = cap reached); two aligned
+    # cubes far apart along an axis separate at the first test; spheres run
+    # no GJK
+    rng = np.random.default_rng(7)
+    s = _sys(inputs.cube(1.0))
+    n = 5000
+    D = _rand_dirs(rng, n) * rng.uniform(0.0, 2.0, n)[:, None]
+    qA, qB = _rand_quat(rng, n), _rand_quat(rng, n)
+    ov, it = s.overlap(D, qA, qB, iters=True)
+    assert np.array_equal(ov, s.overlap(D, qA, qB))
+    assert it.min() >= 1 and it.max() <= 33
+    I = np.tile([1.0, 0, 0, 0], (3, 1))
+    far = np.array([[3.0, 0, 0], [0, -2.5, 0], [0, 0, 1.2]])
+    ov, it = s.overlap(far, I, I, iters=True)
+    assert not ov.any() and np.all(it == 1)
+    sph = orc.OracleSystem(3, [30.0] * 3, 0.5)
+    ov, it = sph.overlap(D, qA, qB, iters=True)
+    assert np.array_equal(ov, (np.linalg.norm(D, axis=1) <= 1.0).astype(np.int32)) and not it.any()
