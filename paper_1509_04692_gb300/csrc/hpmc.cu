@@ -1365,9 +1365,9 @@ int hpmc_autotune(hpmc_t h, uint32_t n_trial, int* best_lanes, int* best_warps)
     cudaEvent_t e0, e1;
     CK(cudaEventCreate(&e0));
     CK(cudaEventCreate(&e1));
-    const int wpbs[3] = { 2, 4, 8 };
+    const int wpbs[4] = { 1, 2, 4, 8 };
     for (int gi = 0; gi < 6; ++gi) {
-        for (int wi = 0; wi < 3; ++wi) {
+        for (int wi = 0; wi < 4; ++wi) {
             if (hpmc_set_group_size(h, kGroupSizes[gi], wpbs[wi]) != 0) continue;
             int rc = hpmc_sweep(h, 1, nullptr);      // warm-up
             if (rc) continue;
