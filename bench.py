@@ -247,6 +247,36 @@ def run_ours(args):
     moves = cnt["moves"]
     ms_job, moves_job = job_totals(torch, ms, moves, "cuda")
     value = moves_job / (ms_job * 1e-3)
+
+    # ---- end to end through the C ABI with host buffers, on every rank
+    # (whole job: the slowest rank's time, the moves and bytes of all ranks)
+    N = s.N
+    p_in, o_in, _ = b.get_state()
+    pin_p = torch.from_numpy(np.ascontiguousarray(p_in)).pin_memory()
+    pin_o = torch.from_numpy(np.ascontiguousarray(o_in)).pin_memory()
+    out_p = torch.empty_like(pin_p).pin_memory()
+    out_o = torch.empty_like(pin_o).pin_memory()
+    torch.cuda.synchronize()
+    b.run_host(pin_p.numpy(), pin_o.numpy(), SWEEPS_PER_STEP, out_p.numpy(), out_o.numpy(),
+               stream=stream.cuda_stream)                    # warm-up
+    e2e_moves, e2e_dt = 0, 0.0
+    e2e_steps = max(3, args.steps // 2)
+    if ws > 1:
+        dist.barrier()
+    for _ in range(e2e_steps):
+        b.reset_counters()
+        t0 = time.perf_counter()
+        c = b.run_host(pin_p.numpy(), pin_o.numpy(), SWEEPS_PER_STEP, out_p.numpy(), out_o.numpy(),
+                       stream=stream.cuda_stream)
+        e2e_dt += time.perf_counter() - t0
+        e2e_moves += c["moves"]
+        pin_p.copy_(out_p)
+        pin_o.copy_(out_o)
+    e2e_ms_job, e2e_moves_job = job_totals(torch, e2e_dt * 1e3, e2e_moves, "cuda")
+    e2e = {"value": e2e_moves_job / (e2e_ms_job * 1e-3), "unit": UNIT,
+           "h2d_bytes_per_step": int(ws * N * 4 * 8), "d2h_bytes_per_step": int(ws * N * 4 * 8),
+           "api": "hpmc_run_host (pinned host buffers, H2D + 200 sweeps + D2H + counters)"}
+    b.reset_counters()
     if rank != 0:
         b.close()
         if ws > 1:
@@ -269,38 +299,22 @@ def run_ours(args):
                 "peak_source": "152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz (nominal unit counts)",
                 "flops_per_move_model": f"{FLOP_MOVE} + {FLOP_CULL}*culls + {FLOP_SAT}*SAT checks"}
 
-    # ---- end to end through the C ABI with host buffers
-    N = s.N
-    p_in, o_in, _ = b.get_state()
-    pin_p = torch.from_numpy(np.ascontiguousarray(p_in)).pin_memory()
-    pin_o = torch.from_numpy(np.ascontiguousarray(o_in)).pin_memory()
-    out_p = torch.empty_like(pin_p).pin_memory()
-    out_o = torch.empty_like(pin_o).pin_memory()
-    torch.cuda.synchronize()
-    b.run_host(pin_p.numpy(), pin_o.numpy(), SWEEPS_PER_STEP, out_p.numpy(), out_o.numpy(),
-               stream=stream.cuda_stream)                    # warm-up
-    e2e_moves, e2e_dt = 0, 0.0
-    for _ in range(max(3, args.steps // 2)):
-        b.reset_counters()
-        t0 = time.perf_counter()
-        c = b.run_host(pin_p.numpy(), pin_o.numpy(), SWEEPS_PER_STEP, out_p.numpy(), out_o.numpy(),
-                       stream=stream.cuda_stream)
-        e2e_dt += time.perf_counter() - t0
-        e2e_moves += c["moves"]
-        pin_p.copy_(out_p)
-        pin_o.copy_(out_o)
-    e2e = {"value": e2e_moves / e2e_dt, "unit": UNIT,
-           "h2d_bytes_per_step": int(N * 4 * 8), "d2h_bytes_per_step": int(N * 4 * 8),
-           "api": "hpmc_run_host (pinned host buffers, H2D + 200 sweeps + D2H + counters)"}
-
     forms = {"fp32_filtered": {"value": value, "fp64_rechecks": cnt["fp64_rechecks"],
                                "overlap_checks": cnt["overlap_checks"],
                                "acceptance": cnt["accept"] / max(1, moves)}}
+    # ---- the other forms and the CPU baseline: one GPU only (with N > 1
+    # the job reports its headline; the forms are one-GPU measurements)
+    multi = ws > 1
+    args.no_batched = args.no_batched or multi
+    args.no_cubes = args.no_cubes or multi
+    args.no_large = args.no_large or multi
+    args.no_cpu = args.no_cpu or multi
     # ---- plain FP64 form on the same workload (same trajectory)
-    b64 = hpmc.from_system(s)
-    forms["fp64"] = measure_form(b64, torch, stream, flush, hpmc.HPMC_FP64, MELT, SWEEPS_PER_STEP,
-                                 max(2, args.steps // 2))
-    b64.close()
+    if not multi:
+        b64 = hpmc.from_system(s)
+        forms["fp64"] = measure_form(b64, torch, stream, flush, hpmc.HPMC_FP64, MELT, SWEEPS_PER_STEP,
+                                     max(2, args.steps // 2))
+        b64.close()
 
     # ---- batched form: 512 independent replicas, one graph-captured launch sequence
     if not args.no_batched:
