@@ -320,7 +320,7 @@ def run_ours(args):
     if not args.no_batched:
         reps = inputs.replica_systems(512)
         bb = hpmc.from_systems(reps)
-        f = measure_form(bb, torch, stream, flush, hpmc.HPMC_FP32_FILTERED, 20, SWEEPS_PER_STEP, 2)
+        f = measure_form(bb, torch, stream, flush, hpmc.HPMC_FP32_FILTERED, 20, SWEEPS_PER_STEP, 2, n_tune=8)
         f.update(replicas=512, particles=int(sum(r.N for r in reps)))
         forms["batched_512_replicas_fp32_filtered"] = f
         bb.close()
