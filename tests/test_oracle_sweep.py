@@ -132,3 +132,48 @@ def test_two_pentagon_pair_distance_law():
     ref = r[keep]
     res = stats.ks_2samp(chain, ref)
     assert res.pvalue > 1e-3, res
+
+
+def test_one_particle_chain_carries_no_current():
+    # Detailed balance.  With a single particle exactly one checkerboard set
+    # acts in a sweep (the set of its cell), after a random grid shift that
+    # does not depend on the state; each such update is reversible for the
+    # uniform measure (symmetric proposals, in-cell rejection symmetric
+    # between x and x'), and so is their mixture.  A reversible chain carries
+    # no net probability current across any cut, so the net number of
+    # crossings of the x, y and angle bin boundaries (forward minus
+    # backward) stays within noise of zero.  A bias of 0.005 in x per sweep
+    # (under 2% of the step) reads z = 5.3 here, a rotation bias of 0.01 rad
+    # per sweep z = 4.6; the unbiased chain |z| < 0.4.
+    v = inputs.regular_polygon(5, 0.5)
+    L = 4.4                                         # 4 x 4 cells
+    s = orc.OracleSystem(2, [L, L], v)
+    s.set_moves(0.35, 0.6, 4, 2024)
+    pos = np.array([[1.3, 2.9]])
+    ori = np.array([[1.0, 0.0]])
+    nb, na = 8, 4
+
+    def bins(p, o):
+        ix = min(int(p[0, 0] / L * nb), nb - 1)
+        iy = min(int(p[0, 1] / L * nb), nb - 1)
+        ia = min(int((np.arctan2(o[0, 1], o[0, 0]) + np.pi) / (2 * np.pi) * na), na - 1)
+        return ix, iy, ia
+
+    s.sweep(pos, ori, 0, 200)                       # burn-in
+    a = bins(pos, ori)
+    current, crossings = np.zeros(3), np.zeros(3)
+    for sw in range(200, 150200):
+        s.sweep(pos, ori, sw, 1)
+        b = bins(pos, ori)
+        for k, m in enumerate((nb, nb, na)):
+            step = (b[k] - a[k]) % m
+            if step == 1:
+                current[k] += 1
+                crossings[k] += 1
+            elif step == m - 1:
+                current[k] -= 1
+                crossings[k] += 1
+        a = b
+    assert np.all(crossings > 20000)
+    z = current / np.sqrt(crossings)
+    assert np.all(np.abs(z) < 4.0), (z, crossings)
