@@ -766,9 +766,16 @@ int hpmc_set_cell_width_min(hpmc_t h, double w_min)
         }
         fresh[r].pbase = h->reps[r].pbase;
     }
+    const std::vector<Rep> old = h->reps;
     h->reps = fresh;                                    // cbase: relayout
     const int rc = relayout(h);
-    if (rc) return rc;
+    if (rc) {
+        // allocation failed: back to the old grid (it fits the arrays we have)
+        h->w_min = w_old;
+        h->reps = old;
+        const int rc2 = relayout(h);
+        return rc2 ? rc2 : rc;
+    }
     CK(cudaDeviceSynchronize());                        // the next sweep rebuilds cells and mirrors
     return 0;
 }
@@ -959,12 +966,17 @@ int relayout(hpmc_batch* h)
     if (ctot > 0x7fffffffull) return HPMC_ERR_INVALID_ARG;
     Dev& dv = h->dv;
     if (ctot > h->ctot_cap) {
+        // all three arrays first, switched only together: a failed allocation
+        // leaves the device layout as it was (the caller restores the host's)
         const uint32_t cap = (uint32_t)std::min<uint64_t>(std::max<uint64_t>(ctot, 2ull * h->ctot_cap), 0x7fffffffull);
         const uint32_t nt = (cap + kScanTile - 1) / kScanTile;
+        uint32_t *cnt = nullptr, *sta = nullptr, *tsu = nullptr;
         int rc;
-        if ((rc = dalloc(h, &dv.count, cap)) || (rc = dalloc(h, &dv.start, (size_t)cap + 1)) ||
-            (rc = dalloc(h, &dv.tile_sums, nt)))
+        if ((rc = dalloc(h, &cnt, cap)) || (rc = dalloc(h, &sta, (size_t)cap + 1)) || (rc = dalloc(h, &tsu, nt)))
             return rc;
+        dv.count = cnt;
+        dv.start = sta;
+        dv.tile_sums = tsu;
         h->ctot_cap = cap;
     }
     h->ctot = (uint32_t)ctot;
@@ -1045,7 +1057,14 @@ int hpmc_box_move(hpmc_t h, int32_t r, double beta_P, double dV_max, int* accept
     CK(cudaGetLastError());
     h->reps[r] = rp_new;
     int rc = grid_changed ? relayout(h) : upload_reps(h, 0);
-    if (rc) return rc;
+    if (rc) {
+        // the trial grid could not be laid out: positions and grid as before
+        for (int a = 0; a < dim; ++a)
+            CK(cudaMemcpy(src[a] + pb, h->bak[a] + pb, sizeof(double) * n, cudaMemcpyDeviceToDevice));
+        h->reps[r] = rp_old;
+        const int rc2 = grid_changed ? relayout(h) : upload_reps(h, 0);
+        return rc2 ? rc2 : rc;
+    }
     // any overlapping pair of the replica rejects (FP64 contract, cell list of the trial box)
     uint64_t n_ov = 0;
     rc = hpmc_check_overlaps(h, r, &n_ov);

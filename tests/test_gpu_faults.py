@@ -60,3 +60,31 @@ def test_lazy_allocations_fail_cleanly():
     b.box_move(5.0, 0.5)
     assert b.check_overlaps() == 0 and b.box().shape == L0.shape
     b.close()
+
+
+def test_failed_grid_growth_keeps_the_old_grid():
+    # a finer cell grid needs larger cell arrays; when one of their three
+    # allocations fails, the call reports OOM and the old grid stays in force
+    # on host and device alike (the run matches the oracle on that grid)
+    s = inputs.pentagon_system(700, 0.5, 53, d=0.12, a=0.15, w_min=1.7)
+    b = hpmc.from_system(s)
+    nc = b.geometry()["nc"][0]
+    for n in range(3):
+        hpmc.debug_fail_alloc(n)
+        with pytest.raises(hpmc.HPMCError) as e:
+            b.set_cell_width_min(0.0)
+        assert e.value.code == OOM
+        assert b.geometry()["nc"][0] == nc
+    hpmc.debug_fail_alloc(-1)
+    b.sweep(12, graph=True)
+    c = b.counters()
+    p, q, _ = b.get_state()
+    o = orc.OracleSystem(2, s.L, s.verts, w_min=1.7)
+    o.set_moves(s.d, s.a, s.nselect, s.seed)
+    rp, rq = s.pos.copy(), s.orient.copy()
+    rc = o.sweep(rp, rq, 0, 12)
+    assert (c["accept"], c["reject_overlap"], c["reject_boundary"]) == tuple(int(x) for x in rc[:3])
+    assert np.array_equal(p, rp) and np.array_equal(q, rq)
+    b.set_cell_width_min(0.0)                     # and the growth itself works
+    assert b.geometry()["nc"][0] > nc
+    b.close()
