@@ -88,3 +88,28 @@ def test_failed_grid_growth_keeps_the_old_grid():
     b.set_cell_width_min(0.0)                     # and the growth itself works
     assert b.geometry()["nc"][0] > nc
     b.close()
+
+
+def test_select_table_allocation_failure_is_reported():
+    # the latency-regime kernels allocate their select table at the first
+    # sweep after the configuration change; a failure there is OOM from the
+    # sweep call, and the next sweep allocates and runs normally
+    s = inputs.pentagon_system(500, 0.5, 54, d=0.12, a=0.15)
+    b = hpmc.from_system(s)
+    b.set_group_size(32, 2)
+    hpmc.debug_fail_alloc(0)
+    with pytest.raises(hpmc.HPMCError) as e:
+        b.sweep(3)
+    assert e.value.code == OOM
+    hpmc.debug_fail_alloc(-1)
+    b.sweep(6)
+    c = b.counters()
+    p, q, sw = b.get_state()
+    b.close()
+    assert sw == 6
+    o = orc.OracleSystem(2, s.L, s.verts)
+    o.set_moves(s.d, s.a, s.nselect, s.seed)
+    rp, rq = s.pos.copy(), s.orient.copy()
+    rc = o.sweep(rp, rq, 0, 6)
+    assert (c["accept"], c["reject_overlap"], c["reject_boundary"]) == tuple(int(x) for x in rc[:3])
+    assert np.array_equal(p, rp) and np.array_equal(q, rq)
