@@ -142,8 +142,9 @@ int hpmc_set_group_size(hpmc_t h, int lanes_per_cell, int warps_per_block);
  * the cell-list rebuild and the 2^d checkerboard sets (Sec. 2.5.2), for
  * every replica.  Asynchronous; the sweep counter advances on the device.
  * hpmc_sweep launches the kernels directly; hpmc_sweep_graph captures the
- * launch sequence of two sweeps once into a CUDA graph (per buffer parity)
- * and replays it.  Both give the same trajectory.  With 8 or more lanes per
+ * launch sequence of 16 sweeps (for runs of 16 or more) and of two sweeps
+ * once into CUDA graphs (per buffer parity) and replays them.  Both give the
+ * same trajectory.  With 8 or more lanes per
  * cell each sweep also runs one kernel on an internal second stream (the
  * state-independent part of every select, computed beside the rebuild and
  * joined before the first set); the first sweep after a change of group

@@ -93,8 +93,11 @@ struct hpmc_batch {
     std::vector<void*> allocs;
     cudaStream_t last_stream = nullptr;
     int pending_error = 0;
-    // graph of two sweeps per starting buffer parity (two sweeps return to it)
+    // graphs of two and of kLongGraph sweeps per starting buffer parity (an
+    // even number of sweeps returns to it); the long one for long runs, so
+    // that graph-launch boundaries are rare
     cudaGraphExec_t graph[2] = { nullptr, nullptr };
+    cudaGraphExec_t graph_long[2] = { nullptr, nullptr };
     cudaStream_t graph_stream = nullptr;
     // set-kernel launch configuration (recomputed when G, wpb or precision change)
     bool cfg_valid = false;
@@ -314,6 +317,10 @@ void invalidate_graph(hpmc_batch* h)
         if (h->graph[p]) {
             cudaGraphExecDestroy(h->graph[p]);
             h->graph[p] = nullptr;
+        }
+        if (h->graph_long[p]) {
+            cudaGraphExecDestroy(h->graph_long[p]);
+            h->graph_long[p] = nullptr;
         }
     }
 }
@@ -821,30 +828,47 @@ int hpmc_sweep(hpmc_t h, uint32_t n, void* stream)
     return 0;
 }
 
+static constexpr uint32_t kLongGraph = 16;
+
+// capture `sweeps` sweeps (even) from the current parity into *out
+static int capture_sweeps(hpmc_batch* h, cudaStream_t st, uint32_t sweeps, cudaGraphExec_t* out)
+{
+    int prc = prepare_set(h);
+    if (prc) return prc;
+    if (!h->graph_stream) CK(cudaStreamCreateWithFlags(&h->graph_stream, cudaStreamNonBlocking));
+    CK(cudaStreamSynchronize(st));
+    const int cur0 = h->cur;
+    CK(cudaStreamBeginCapture(h->graph_stream, cudaStreamCaptureModeThreadLocal));
+    int rc = 0;
+    for (uint32_t k = 0; k < sweeps && !rc; ++k) rc = enqueue_sweep(h, h->graph_stream);
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamEndCapture(h->graph_stream, &g);
+    h->cur = cur0;
+    if (rc) { if (g) cudaGraphDestroy(g); return rc; }
+    if (e != cudaSuccess) return cuda_fail(e);
+    e = cudaGraphInstantiate(out, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) { *out = nullptr; return cuda_fail(e); }
+    return 0;
+}
+
 int hpmc_sweep_graph(hpmc_t h, uint32_t n, void* stream)
 {
     if (!h) return HPMC_ERR_INVALID_ARG;
     cudaStream_t st = (cudaStream_t)stream;
     h->last_stream = st;
-    if (n >= 2 && !h->graph[h->cur]) {
-        int prc = prepare_set(h);
-        if (prc) return prc;
-        if (!h->graph_stream) CK(cudaStreamCreateWithFlags(&h->graph_stream, cudaStreamNonBlocking));
-        CK(cudaStreamSynchronize(st));
-        const int cur0 = h->cur;
-        CK(cudaStreamBeginCapture(h->graph_stream, cudaStreamCaptureModeThreadLocal));
-        int rc = enqueue_sweep(h, h->graph_stream);
-        if (!rc) rc = enqueue_sweep(h, h->graph_stream);
-        cudaGraph_t g = nullptr;
-        cudaError_t e = cudaStreamEndCapture(h->graph_stream, &g);
-        h->cur = cur0;
-        if (rc) { if (g) cudaGraphDestroy(g); return rc; }
-        if (e != cudaSuccess) return cuda_fail(e);
-        e = cudaGraphInstantiate(&h->graph[cur0], g, 0);
-        cudaGraphDestroy(g);
-        if (e != cudaSuccess) { h->graph[cur0] = nullptr; return cuda_fail(e); }
-    }
     uint32_t s = 0;
+    if (n >= kLongGraph) {
+        if (!h->graph_long[h->cur]) {
+            const int rc = capture_sweeps(h, st, kLongGraph, &h->graph_long[h->cur]);
+            if (rc) return rc;
+        }
+        for (; s + kLongGraph <= n; s += kLongGraph) CK(cudaGraphLaunch(h->graph_long[h->cur], st));
+    }
+    if (n - s >= 2 && !h->graph[h->cur]) {
+        const int rc = capture_sweeps(h, st, 2, &h->graph[h->cur]);
+        if (rc) return rc;
+    }
     for (; s + 2 <= n; s += 2) CK(cudaGraphLaunch(h->graph[h->cur], st));
     if (s < n) {
         int rc = enqueue_sweep(h, st);
