@@ -52,6 +52,11 @@ FLOPS = {2: (FLOP_MOVE, FLOP_CULL, FLOP_SAT), 3: (80, 8, 1000)}
 # (profiles/set2d_fluid4096.md, cold-cache replay); valid for the kernel as
 # captured there
 SET2D_FLUID_DRAM_BYTES = 466432
+# the same capture's unit utilisations (fractions of each unit's peak): no
+# unit is near its peak, the kernel is bound by one warp's dependency chain
+SET2D_FLUID_NCU = {"issue_active": 0.185, "fp64_pipe": 0.113, "alu_pipe": 0.102, "fma_pipe": 0.054,
+                   "warps_active": 0.083, "dram_throughput": 0.0034,
+                   "binding": "latency (one warp's chain of 4 selects per active cell)"}
 
 
 def job_totals(torch, ms, moves, device):
@@ -294,7 +299,7 @@ def run_ours(args):
     achieved = (flop_per_sweep / nsets) / (set_ms * 1e-3) / 1e12
     roofline = {"bound": "alu", "kernel": "k_set2d (checkerboard set)", "achieved": achieved,
                 "peak": PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / PEAK_TFLOPS,
-                "traffic": SET2D_FLUID_DRAM_BYTES,
+                "traffic": SET2D_FLUID_DRAM_BYTES, "ncu_utilisation": SET2D_FLUID_NCU,
                 "set_kernel_ms": set_ms, "rebuild_ms_per_sweep": ms_rebuild,
                 "peak_source": "152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz (nominal unit counts)",
                 "flops_per_move_model": f"{FLOP_MOVE} + {FLOP_CULL}*culls + {FLOP_SAT}*SAT checks"}
