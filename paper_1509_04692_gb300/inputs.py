@@ -227,7 +227,9 @@ def fluid4096(seed: int = 42) -> System:
 
 def replica_params(n_replicas: int = 512, gen_seed: int = 2024, n_lo: int = 256,
                    n_hi: int = 8192, phi_lo: float = 0.40, phi_hi: float = 0.70):
-    """(N_r, phi_r, seed_r = 42 + r) for a batch of independent replicas."""
+    """(N_r, phi_r, seed_r = 42 + r) for a batch of independent replicas.
+    All N are drawn before all densities, so the densities of the first k
+    replicas depend on the batch size (a shorter batch is not a prefix)."""
     rng = np.random.default_rng(gen_seed)
     Ns = rng.integers(n_lo, n_hi + 1, size=n_replicas)
     phis = rng.uniform(phi_lo, phi_hi, size=n_replicas)
