@@ -418,6 +418,8 @@ int prepare_selects(hpmc_batch* h)
             cudaFree(h->msel);
             h->msel = nullptr;
             h->msel_cap = 0;
+            h->dv.msel = nullptr;
+            h->dv.msel_n = 0;
         }
         uint4* p = nullptr;
         const int rc = dalloc(h, &p, need * rec / sizeof(uint4));
