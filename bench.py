@@ -81,19 +81,32 @@ def dist_env():
 
 
 class ClockSampler:
-    """nvidia-smi samples during the timed region."""
+    """nvidia-smi samples during the timed region: the constructor returns once
+    the sampler has written its first line (at most `wait_s` later), and the
+    lines written before that point are left out of the record unless no
+    other line came."""
 
-    def __init__(self, gpu):
+    def __init__(self, gpu, period_ms=100, wait_s=5.0):
         self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
         q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        self.skip = 0
         try:
             self.p = subprocess.Popen(["nvidia-smi", f"--id={gpu}", f"--query-gpu={q}",
-                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                       "--format=csv,noheader,nounits", "-lms", str(period_ms)],
                                       stdout=self.f, stderr=subprocess.DEVNULL)
         except Exception:
             self.p = None
+            return
+        t_end = time.time() + wait_s
+        while time.time() < t_end and self.p.poll() is None:
+            with open(self.f.name) as g:
+                n = g.read().count("\n")
+            if n:
+                self.skip = n
+                break
+            time.sleep(0.02)
 
     def stop(self):
         if self.p is None:
@@ -107,7 +120,10 @@ class ClockSampler:
         self.f.seek(0)
         sm, mx, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for line in self.f.read().splitlines():
+        lines = self.f.read().splitlines()
+        if len(lines) > self.skip:
+            lines = lines[self.skip:]
+        for line in lines:
             c = [x.strip() for x in line.split(",")]
             if len(c) < 9:
                 continue
@@ -597,7 +613,7 @@ def main():
     ap.add_argument("--warps", type=int, default=4)
     ap.add_argument("--trace", action="store_true", help="with --profile-sweeps: per-warp phase stamps")
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=40)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--cpu-sweeps", type=int, default=2000)
