@@ -140,6 +140,25 @@ def _c64(a, shape=None):
     return a
 
 
+def _sized(a, n, what):
+    """Contiguous float64 copy of `a` holding exactly n values (the library
+    reads n values through the pointer)."""
+    a = _c64(a)
+    if a.size != n:
+        raise ValueError(f"{what}: {a.size} values given, {n} expected")
+    return a
+
+
+def _out(a, n, what, dtype=np.float64):
+    """An output array the library writes n values into: it must be a
+    writable C-contiguous array of `dtype` with exactly n elements."""
+    if not isinstance(a, np.ndarray) or a.dtype != dtype or not a.flags.c_contiguous \
+            or not a.flags.writeable or a.size != n:
+        raise ValueError(f"{what}: a writable C-contiguous {np.dtype(dtype).name} array of {n} "
+                         f"elements is needed")
+    return a
+
+
 class Batch:
     """A batch of R replicas of one convex shape (R = 1: a single system)."""
 
@@ -241,11 +260,20 @@ class Batch:
         return pos, ori, int(sw.value)
 
     def set_state(self, pos, orient, sweep=0, r=0):
-        pos = _c64(pos)
-        ori = _c64(orient)
+        N = self.N[r]
+        pos = _sized(pos, N * self.dim, "set_state pos")
+        ori = _sized(orient, N * self.qd, "set_state orient")
         _ck(_lib.hpmc_set_state(self.h, int(r), _dp(pos), _dp(ori), int(sweep)), "hpmc_set_state")
 
     def run_host(self, pos, orient, n, pos_out, orient_out, stream=0):
+        """pos/orient: every replica's configuration, concatenated in replica
+        order (tag order inside); the result is written into pos_out /
+        orient_out (same sizes).  Returns the summed counters."""
+        nt = sum(self.N)
+        pos = _sized(pos, nt * self.dim, "run_host pos")
+        orient = _sized(orient, nt * self.qd, "run_host orient")
+        _out(pos_out, nt * self.dim, "run_host pos_out")
+        _out(orient_out, nt * self.qd, "run_host orient_out")
         c = Counters()
         _ck(_lib.hpmc_run_host(self.h, _dp(pos), _dp(orient), int(n), _dp(pos_out), _dp(orient_out),
                                ctypes.byref(c), ctypes.c_void_p(int(stream) if stream else None)),
@@ -289,6 +317,7 @@ class Batch:
         spheres) to ``hist`` (uint64[nbins], created when None); returns it."""
         if hist is None:
             hist = np.zeros(int(nbins), dtype=np.uint64)
+        _out(hist, int(nbins), "sdf hist", np.uint64)
         _ck(_lib.hpmc_sdf(self.h, int(r), float(x_max), int(nbins),
                           hist.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64))), "hpmc_sdf")
         return hist

@@ -85,3 +85,32 @@ def test_a_valid_call_fails_loudly_without_a_gpu():
     with pytest.raises(hpmc.HPMCError) as e:
         _create(N=4)
     assert e.value.code == CUDA
+
+
+def test_binding_checks_array_sizes_before_the_library_reads_them():
+    # a handle-less batch of two replicas (3 and 5 disks): the checks raise
+    # before any call into the library, which would read or write exactly
+    # N * dim (N * 2 | 4) doubles through the pointers
+    b = object.__new__(hpmc.Batch)
+    b.h, b.dim, b.qd, b.N, b.R = None, 2, 2, [3, 5], 2
+    with pytest.raises(ValueError):
+        b.set_state(np.zeros((2, 2)), np.zeros((3, 2)), r=0)          # too few positions
+    with pytest.raises(ValueError):
+        b.set_state(np.zeros((5, 2)), np.zeros((3, 2)), r=0)          # replica 0 holds 3
+    with pytest.raises(ValueError):
+        b.set_state(np.zeros((5, 2)), np.zeros((5, 4)), r=1)          # 2D orientations: 2 values
+    p, o = np.zeros((8, 2)), np.zeros((8, 2))
+    with pytest.raises(ValueError):
+        b.run_host(p[:7], o, 1, np.zeros((8, 2)), np.zeros((8, 2)))    # inputs of every replica
+    with pytest.raises(ValueError):
+        b.run_host(p, o, 1, np.zeros((8, 2), np.float32), np.zeros((8, 2)))
+    with pytest.raises(ValueError):
+        b.run_host(p, o, 1, np.zeros((2, 8)).T, np.zeros((8, 2)))      # not C-contiguous
+    ro = np.zeros((8, 2))
+    ro.flags.writeable = False
+    with pytest.raises(ValueError):
+        b.run_host(p, o, 1, np.zeros((8, 2)), ro)
+    with pytest.raises(ValueError):
+        b.sdf(0.05, 10, hist=np.zeros(9, dtype=np.uint64))
+    with pytest.raises(ValueError):
+        b.sdf(0.05, 10, hist=np.zeros(10, dtype=np.int64))
