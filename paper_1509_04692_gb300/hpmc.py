@@ -175,7 +175,7 @@ class Batch:
         self.N = []
         for i, r in enumerate(replicas):
             pos = _c64(r["pos"]).reshape(-1, self.dim)
-            ori = _c64(r["orient"]).reshape(-1, self.qd)
+            ori = _sized(r["orient"], pos.shape[0] * self.qd, f"replica {i} orient").reshape(-1, self.qd)
             self._keep += [pos, ori]
             box = list(np.broadcast_to(np.asarray(r["box"], dtype=np.float64), (self.dim,))) + [1.0] * (3 - self.dim)
             descs[i].N = pos.shape[0]
@@ -369,9 +369,9 @@ def pair_test(dim, verts, D, qA, qB):
     v = _c64(verts).reshape(-1, dim)
     D = _c64(D).reshape(-1, dim)
     qd = 2 if dim == 2 else 4
-    qA = _c64(qA).reshape(-1, qd)
-    qB = _c64(qB).reshape(-1, qd)
     n = D.shape[0]
+    qA = _sized(qA, n * qd, "pair_test qA").reshape(-1, qd)
+    qB = _sized(qB, n * qd, "pair_test qB").reshape(-1, qd)
     o64 = np.zeros(n, dtype=np.int32)
     o32 = np.zeros(n, dtype=np.int32)
     ip = ctypes.POINTER(ctypes.c_int32)
@@ -388,9 +388,9 @@ def pair_test_warp3d(verts, D, qA, qB):
     v = np.array([float(verts)]) if round_ else _c64(verts).reshape(-1, 3)
     nv = 0 if round_ else v.shape[0]
     D = _c64(D).reshape(-1, 3)
-    qA = _c64(qA).reshape(-1, 4)
-    qB = _c64(qB).reshape(-1, 4)
     n = D.shape[0]
+    qA = _sized(qA, n * 4, "pair_test_warp3d qA").reshape(-1, 4)
+    qB = _sized(qB, n * 4, "pair_test_warp3d qB").reshape(-1, 4)
     o64 = np.zeros(n, dtype=np.int32)
     its = np.zeros(n, dtype=np.int32)
     ip = ctypes.POINTER(ctypes.c_int32)

@@ -114,3 +114,13 @@ def test_binding_checks_array_sizes_before_the_library_reads_them():
         b.sdf(0.05, 10, hist=np.zeros(9, dtype=np.uint64))
     with pytest.raises(ValueError):
         b.sdf(0.05, 10, hist=np.zeros(10, dtype=np.int64))
+
+
+def test_binding_checks_pair_and_replica_arrays():
+    v = inputs.regular_polygon(5, 0.5)
+    with pytest.raises(ValueError):
+        hpmc.pair_test(2, v, np.zeros((4, 2)), np.zeros((3, 2)), np.zeros((4, 2)))
+    with pytest.raises(ValueError):
+        hpmc.pair_test_warp3d(inputs.cube(1.0), np.zeros((4, 3)), np.zeros((4, 4)), np.zeros((4, 2)))
+    with pytest.raises(ValueError):                                   # 4 positions, 3 orientations
+        _create(N=4, orient=np.tile([1.0, 0.0], (3, 1)))
