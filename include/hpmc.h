@@ -88,7 +88,10 @@ typedef struct {
  *             minimum, Sec. 2.2.1).
  *   reps      R replica descriptors (see above).
  *   out       receives the handle.
- * Cell geometry per axis: nc = floor(L / max(2R, w_min)), made even, >= 4.
+ * Cell geometry per axis: nc = floor(L / max(2R, w_min)), made even, >= 4
+ * (BOX_TOO_SMALL otherwise).  Limits (INVALID_ARG beyond them): nc <= 65536
+ * per axis, and at most 2^31 - 1 cells in a replica, cells in the batch and
+ * particles in the batch (cell and particle indices are 32-bit).
  * Errors: INVALID_ARG, BOX_TOO_SMALL, OOM, CUDA.  Synchronous.
  */
 int hpmc_batch_create(int dim, const double* verts, uint32_t nv, double w_min,

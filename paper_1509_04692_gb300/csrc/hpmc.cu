@@ -206,7 +206,11 @@ int rep_geometry(const hpmc_batch* h, const HostRep& hr, Rep& rp)
     rp.d32 = (float)rp.d;
     rp.tau32 = (float)rp.tau;
     rp.nselect = hr.nselect;
-    rp.ncell = (uint32_t)rp.nc[0] * (uint32_t)rp.nc[1] * (uint32_t)(h->dim == 3 ? rp.nc[2] : 1);
+    // the cell count in 64 bits: a dilute box can exceed 32 bits (cell
+    // indices are 32-bit, so at most 2^31 - 1 cells)
+    const uint64_t ncell = (uint64_t)rp.nc[0] * (uint64_t)rp.nc[1] * (uint64_t)(h->dim == 3 ? rp.nc[2] : 1);
+    if (ncell > 0x7fffffffull) return HPMC_ERR_INVALID_ARG;
+    rp.ncell = (uint32_t)ncell;
     // certified FP32 thresholds
     double wmax = 0.0, Lmax = 0.0;
     for (int a = 0; a < h->dim; ++a) { wmax = std::max(wmax, rp.w[a]); Lmax = std::max(Lmax, rp.L[a]); }

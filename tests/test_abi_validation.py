@@ -56,6 +56,22 @@ def test_configurations_and_boxes_are_checked():
     assert _code(dim=3, L=3.0) == BOX_SMALL
 
 
+def test_grid_limits_are_checked_before_any_allocation():
+    # cell and particle indices are 32-bit: at most 65536 cells per axis and
+    # 2^31 - 1 cells per replica and per batch, counted in 64 bits
+    assert _code(L=70000.0) == INVALID                                            # 70000 cells per axis
+    assert _code(L=65536.5, w_min=1.0) == INVALID                                 # 65536^2 = 2^32 cells
+    assert _code(L=46342.5, w_min=1.0) == INVALID                                 # 46342^2 > 2^31 - 1
+    assert _code(dim=3, L=4000.0) == INVALID                                      # 2308^3 cubes' cells
+    assert _code(dim=3, L=3000.0, w_min=2.0) == INVALID                           # 1500^3
+    rng = np.random.default_rng(1)
+    reps = [dict(box=40000.0, pos=rng.uniform(0, 40000.0, (4, 2)), orient=np.tile([1.0, 0.0], (4, 1)),
+                 seed=42 + r) for r in range(2)]                                  # 2 x 1.6e9 cells
+    with pytest.raises(hpmc.HPMCError) as e:
+        hpmc.Batch(2, inputs.regular_polygon(5, 0.5), reps, w_min=1.0)
+    assert e.value.code == INVALID
+
+
 def test_null_handles_and_pointers():
     lib = hpmc.lib()
     null = ctypes.c_void_p()
