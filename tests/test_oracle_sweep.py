@@ -99,6 +99,40 @@ def test_ideal_gas_boundary_rejection_closed_form():
     assert stats.kstest((ang + np.pi) / (2 * np.pi), "uniform").pvalue > 1e-4
 
 
+def test_ideal_gas_boundary_rejection_closed_form_3d():
+    # the same in 3D (vanishing cubes, eight sets): in-cell probability
+    # (1 - d / (2 w))^3, and the uniform law stays stationary -- positions,
+    # and orientations uniform on the unit quaternions, whose components have
+    # the marginal density (2 / pi) sqrt(1 - x^2)
+    L = 20.0
+    s = orc.OracleSystem(3, [L, L, L], inputs.cube(1e-4), w_min=1.0)
+    d = 0.3
+    s.set_moves(d, 0.5, 4, 12)
+    rng = np.random.default_rng(1)
+    N = 3000
+    pos = rng.uniform(0, L, (N, 3))
+    q = rng.normal(size=(N, 4))
+    ori = q / np.linalg.norm(q, axis=1)[:, None]
+    c = s.sweep(pos, ori, 0, 40)
+    moves = int(c[0] + c[1] + c[2])
+    assert c[1] == 0
+    w = s.geometry()["w"]
+    assert len(w) == 3 and np.all(w == 1.0)
+    p_in = np.prod(1 - d / (2 * w))
+    rate = c[2] / moves
+    sigma = np.sqrt(p_in * (1 - p_in) / moves)
+    assert abs(rate - (1 - p_in)) < 5 * sigma, (rate, 1 - p_in, sigma)
+    h, _ = np.histogramdd(pos, bins=5, range=[[0, L]] * 3)
+    assert stats.chisquare(h.ravel()).pvalue > 1e-4
+    assert np.allclose(np.linalg.norm(ori, axis=1), 1.0, atol=1e-14)
+
+    def cdf(x):
+        return 0.5 + (x * np.sqrt(1 - x * x) + np.arcsin(x)) / np.pi
+
+    for k in range(4):
+        assert stats.kstest(ori[:, k], cdf).pvalue > 1e-4, k
+
+
 def test_two_pentagon_pair_distance_law():
     # Two hard pentagons in a small periodic box: the chain's stationary law is
     # uniform over non-overlapping configurations.  Compare the distribution
