@@ -233,8 +233,13 @@ int rep_geometry(const hpmc_batch* h, const HostRep& hr, Rep& rp)
     }
     rp.e_pb32 = f32_up(h->dim == 3 ? g.e_sat : 0.0);
     rp.e_va32 = f32_up(2.0 * kU32 * vm);
-    // band outside which the FP64 GJK verdict equals the exact predicate: far
-    // above its own rounding (~1e-13 of the shape size)
+    // certificate band: an overlap certificate needs the origin this deep
+    // inside the Minkowski difference, far above the FP64 rounding of a
+    // support query (~1e-13 of the shape size), so that no FP64 support can
+    // show a separating plane.  A separation certificate needs, besides
+    // tau |n|_1, a gap of |n|_1 times the FP32 vertex error bound (~6e-5 of
+    // the size for cubes), outside the zone near contact (below ~3e-7 of
+    // the size) where the FP64 GJK may conservatively answer overlap.
     rp.tau3 = f32_up(1e-9 * 2.0 * h->Rc);
     rp.in_lo = f32_up(g.e_in);
     rp.out_lo = f32_down(-g.e_in);

@@ -66,7 +66,7 @@ struct Rep {
     float e_ori32;           // |q'32 - q'64| per component of the FP32 trial orientation
     float e_pb32;            // 3D: |pb32 - pb| per component of B's vertices in A's frame
     float e_va32;            // 3D: |fl32(v) - v| per component of A's local vertices
-    float tau3;              // 3D: certificate band (GJK64 = exact predicate outside it)
+    float tau3;              // 3D: certificate band (depth / extra gap a certificate needs)
     float ins32;             // |D32|^2 < ins32 -> certain overlap (inscribed balls meet)
     double ins64;            // the same test on the FP64 |D|^2
     double e_in, e_cull, e_sat;  // the same margins in FP64 (reporting)

@@ -180,6 +180,30 @@ def classify_3d(verts, D, qA, qB, eps=1e-9):
     return ov_small, ~ov_big
 
 
+def sat15_exit(h, u, qA, qB):
+    """Distance along the unit directions u at which two boxes (half-extents
+    h) stop overlapping: the set of overlapping offsets is the intersection of
+    the 15 slabs |D.L| <= ra + rb (L a unit test axis), so the ray t u leaves
+    it at the smallest (ra + rb) / |u.L|."""
+    RA = quat_to_mat(qA)
+    RB = quat_to_mat(qB)
+    A = np.swapaxes(RA, 1, 2)
+    B = np.swapaxes(RB, 1, 2)
+    axes = [A[:, i] for i in range(3)] + [B[:, j] for j in range(3)]
+    axes += [np.cross(A[:, i], B[:, j]) for i in range(3) for j in range(3)]
+    t = np.full(u.shape[0], np.inf)
+    for L_ in axes:
+        ln = np.linalg.norm(L_, axis=1)
+        ok = ln > 1e-12
+        Ln = np.where(ok[:, None], L_ / np.where(ok, ln, 1.0)[:, None], 0.0)
+        ra = sum(h[i] * np.abs(np.einsum("nk,nk->n", A[:, i], Ln)) for i in range(3))
+        rb = sum(h[j] * np.abs(np.einsum("nk,nk->n", B[:, j], Ln)) for j in range(3))
+        c = np.abs(np.einsum("nk,nk->n", u, Ln))
+        hit = ok & (c > 0)
+        t = np.minimum(t, np.where(hit, (ra + rb) / np.where(hit, c, 1.0), np.inf))
+    return t
+
+
 def sat15_boxes(h, D, qA, qB):
     """Signed separation proxy of two boxes (half-extents h) by the 15-axis
     test: > 0 separated, < 0 overlapping (per-axis gap over |axis|)."""

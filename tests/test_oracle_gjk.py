@@ -123,3 +123,53 @@ def test_gjk_iteration_counts():
     sph = orc.OracleSystem(3, [30.0] * 3, 0.5)
     ov, it = sph.overlap(D, qA, qB, iters=True)
     assert np.array_equal(ov, (np.linalg.norm(D, axis=1) <= 1.0).astype(np.int32)) and not it.any()
+
+
+def _contact_dirs(rng, n):
+    u = _rand_dirs(rng, n)
+    q = _rand_quat(rng, 2 * n)
+    return u, q[:n], q[n:]
+
+
+def test_gjk_answers_separated_beyond_a_micro_gap():
+    # What the FP32 filter's separation certificate relies on: the contract's
+    # GJK answers "separated" for every pair farther apart than a small gap.
+    # Just outside contact it is conservative -- a cap or a degenerate simplex
+    # counts as overlap, and for unit cubes separated pairs up to ~2e-7 apart
+    # can read "overlap" (that is the contract, which the GPU re-check
+    # reproduces) -- but the certificate proves a gap of at least |n|_1 times
+    # its FP32 error bound, ~6e-5 for the 32768-cube system, so it only acts
+    # where this test shows the contract to be exact.  Classifiers: the 15-axis
+    # test on cubes enlarged by 1 + eps (disjoint enlarged cubes are more than
+    # eps apart; every pair more than sqrt(3) eps apart qualifies) and, for
+    # dodecahedra, the clipping brute force on shapes scaled by 1 + eps.
+    eps = 1e-6
+    rng = np.random.default_rng(8)
+    s = _sys(inputs.cube(1.0))
+    h = np.array([0.5, 0.5, 0.5])
+    n_sep = 0
+    for _ in range(4):
+        n = 250000
+        u, qA, qB = _contact_dirs(rng, n)
+        tstar = bf.sat15_exit(h, u, qA, qB)          # contact distance along u
+        D = u * (tstar + 10.0 ** rng.uniform(-7.5, -3, n))[:, None]
+        sep = bf.sat15_boxes(h * (1 + eps), D, qA, qB) > 1e-13
+        got = s.overlap(D, qA, qB).astype(bool)
+        assert not np.any(got & sep), np.nonzero(got & sep)[0][:5]
+        n_sep += int(sep.sum())
+    assert n_sep > 500000
+    v = inputs.dodecahedron(1.0)
+    s = _sys(v)
+    n = 20000
+    u, qA, qB = _contact_dirs(rng, n)
+    R = np.sqrt((v ** 2).sum(1)).max()
+    lo, hi = np.zeros(n), np.full(n, 2 * R * 1.001)
+    for _ in range(50):
+        mid = 0.5 * (lo + hi)
+        ov = s.overlap(u * mid[:, None], qA, qB).astype(bool)
+        lo, hi = np.where(ov, mid, lo), np.where(ov, hi, mid)
+    D = u * (hi + 10.0 ** rng.uniform(-7, -3, n))[:, None]
+    _, sep = bf.classify_3d(v, D, qA, qB, eps=eps)
+    got = s.overlap(D, qA, qB).astype(bool)
+    assert not np.any(got & sep)
+    assert sep.sum() > 10000
