@@ -41,7 +41,7 @@ extern "C" {
 #define HPMC_ERR_OVERLAP      -3   /* (reserved) overlapping input where forbidden */
 #define HPMC_ERR_OOM          -4   /* device allocation failed */
 #define HPMC_ERR_CUDA         -5   /* a CUDA runtime call failed */
-#define HPMC_ERR_TIMEOUT      -6   /* a bounded device wait gave up */
+#define HPMC_ERR_TIMEOUT      -6   /* (reserved) a bounded device wait gave up: no kernel here waits */
 #define HPMC_ERR_CAPACITY     -7   /* a cell or stencil exceeded the staging capacity */
 #define HPMC_ERR_NOT_READY    -8   /* call order violated (e.g. no moves set) */
 
