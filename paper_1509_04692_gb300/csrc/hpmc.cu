@@ -1313,6 +1313,27 @@ int hpmc_run_host(hpmc_t h, const double* pos, const double* orient, uint32_t n,
     return read_error(h);
 }
 
+// CUDA events owned by a host scope (destroyed on every return path)
+struct Events {
+    std::vector<cudaEvent_t> e;
+    explicit Events(size_t n) : e(n, nullptr) {}
+    ~Events()
+    {
+        for (cudaEvent_t x : e)
+            if (x) cudaEventDestroy(x);
+    }
+    cudaError_t create()
+    {
+        for (cudaEvent_t& x : e) {
+            const cudaError_t r = cudaEventCreate(&x);
+            if (r != cudaSuccess) return r;
+        }
+        return cudaSuccess;
+    }
+    Events(const Events&) = delete;
+    Events& operator=(const Events&) = delete;
+};
+
 // The state in tag order, the sweep counters and the event counters, kept on
 // the host while trial runs (tuning) use the device state.
 struct Snapshot {
@@ -1377,16 +1398,23 @@ int hpmc_tune_moves(hpmc_t h, int32_t r, double target, uint32_t n_pilot, uint32
         }
         return 0;
     };
+    // a failed pilot leaves the state and the moves as they were
+    auto fail = [&](int code) {
+        snapshot_restore(h, snap);
+        set_scale(1.0);
+        return code;
+    };
     // geometric bisection on a common scale of (d, a): acceptance falls as the
     // moves grow; the best pilot (closest to the target) wins
     double best_f = 1.0, best_acc = -1.0;
     for (uint32_t it = 0; it < iters; ++it) {
         const double mid = std::sqrt(lo * hi);
-        if ((rc = snapshot_restore(h, snap)) || (rc = set_scale(mid))) return rc;
-        CK(cudaMemset(h->dv.counters, 0, sizeof(unsigned long long) * h->R * kNumCounters));
-        if ((rc = hpmc_sweep(h, n_pilot, nullptr))) return rc;
+        if ((rc = snapshot_restore(h, snap)) || (rc = set_scale(mid))) return fail(rc);
+        const cudaError_t ce = cudaMemset(h->dv.counters, 0, sizeof(unsigned long long) * h->R * kNumCounters);
+        if (ce != cudaSuccess) return fail(cuda_fail(ce));
+        if ((rc = hpmc_sweep(h, n_pilot, nullptr))) return fail(rc);
         hpmc_counters_t c{};
-        if ((rc = hpmc_counters(h, r, &c))) return rc;
+        if ((rc = hpmc_counters(h, r, &c))) return fail(rc);
         const double acc = c.moves ? (double)c.accept / (double)c.moves : 0.0;
         if (best_acc < 0.0 || std::fabs(acc - target) < std::fabs(best_acc - target)) {
             best_acc = acc;
@@ -1416,27 +1444,34 @@ int hpmc_autotune(hpmc_t h, uint32_t n_trial, int* best_lanes, int* best_warps)
     const int G0 = h->G, W0 = h->wpb;
     float best_ms = 1e30f;
     int bg = G0, bw = W0;
-    cudaEvent_t e0, e1;
-    CK(cudaEventCreate(&e0));
-    CK(cudaEventCreate(&e1));
+    // a CUDA failure leaves the configuration and the state as they were
+    auto fail = [&](cudaError_t e) {
+        const int code = cuda_fail(e);
+        h->G = G0;
+        h->wpb = W0;
+        invalidate_graph(h);
+        snapshot_restore(h, snap);
+        return code;
+    };
+    Events ev(2);
+    cudaError_t ce = ev.create();
+    if (ce != cudaSuccess) return fail(ce);
     const int wpbs[4] = { 1, 2, 4, 8 };
     for (int gi = 0; gi < 6; ++gi) {
         for (int wi = 0; wi < 4; ++wi) {
             if (hpmc_set_group_size(h, kGroupSizes[gi], wpbs[wi]) != 0) continue;
             int rc = hpmc_sweep(h, 1, nullptr);      // warm-up
             if (rc) continue;
-            CK(cudaEventRecord(e0));
+            if ((ce = cudaEventRecord(ev.e[0])) != cudaSuccess) return fail(ce);
             rc = hpmc_sweep(h, n_trial, nullptr);
-            CK(cudaEventRecord(e1));
-            CK(cudaEventSynchronize(e1));
+            if ((ce = cudaEventRecord(ev.e[1])) != cudaSuccess) return fail(ce);
+            if ((ce = cudaEventSynchronize(ev.e[1])) != cudaSuccess) return fail(ce);
             if (rc) continue;
             float ms = 0.f;
-            CK(cudaEventElapsedTime(&ms, e0, e1));
+            if ((ce = cudaEventElapsedTime(&ms, ev.e[0], ev.e[1])) != cudaSuccess) return fail(ce);
             if (ms < best_ms) { best_ms = ms; bg = kGroupSizes[gi]; bw = wpbs[wi]; }
         }
     }
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
     h->G = bg;
     h->wpb = bw;
     invalidate_graph(h);
@@ -1454,8 +1489,9 @@ int hpmc_profile_sweeps(hpmc_t h, uint32_t n, void* stream, double* ms_rebuild, 
     h->last_stream = st;
     int rc = prepare_set(h);
     if (rc) return rc;
-    std::vector<cudaEvent_t> ev(3 * (size_t)n);
-    for (auto& e : ev) CK(cudaEventCreate(&e));
+    Events evs(3 * (size_t)n);
+    CK(evs.create());
+    std::vector<cudaEvent_t>& ev = evs.e;
     for (uint32_t s = 0; s < n; ++s) {
         CK(cudaEventRecord(ev[3 * s], st));
         rc = enqueue_rebuild(h, st, true);
@@ -1476,7 +1512,6 @@ int hpmc_profile_sweeps(hpmc_t h, uint32_t n, void* stream, double* ms_rebuild, 
         a += x;
         b += y;
     }
-    for (auto& e : ev) cudaEventDestroy(e);
     if (rc) return rc;
     if (ms_rebuild) *ms_rebuild = a / n;
     if (ms_sets) *ms_sets = b / n;
