@@ -28,9 +28,11 @@
  *
  * Parity status: every function here is pinned by the CPU tests (Philox
  * known-answer vectors, brute-force polygon/polyhedron predicates, SAT-15 for
- * boxes, ideal-gas closed form, move distributions, O(N^2) no-overlap; for
+ * boxes, ideal-gas closed forms in 2D and 3D, move distributions, O(N^2)
+ * no-overlap, zero net probability current of one-particle chains in 2D and
+ * 3D (detailed balance), the two-pentagon pair-distance law; for
  * disks/spheres the contact definition and lattice closed forms of the
- * scale-distribution histogram).
+ * scale-distribution histogram; for volume moves the ideal-gas Gamma law).
  */
 #include <math.h>
 #include <stdint.h>
