@@ -66,3 +66,51 @@ def test_reference_arm_runs_on_rank_zero_only(monkeypatch, capsys):
         steps, warmup = 1, 3
     bench.run_reference(A())
     assert capsys.readouterr().out == ""
+
+
+def test_reference_arm_line_on_one_process(monkeypatch, capsys):
+    # the oracle timed as the reference arm: one JSON line with the GPU
+    # arm's metric, unit and direction, its CPU sample described, no copies
+    sys.path.insert(0, ROOT)
+    import json
+    import bench
+    for k in ("WORLD_SIZE", "RANK", "LOCAL_RANK"):
+        monkeypatch.delenv(k, raising=False)
+
+    class A:
+        steps, warmup = 1, 3
+    bench.run_reference(A())
+    lines = capsys.readouterr().out.strip().splitlines()
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference" and d["metric"] == bench.METRIC and d["unit"] == bench.UNIT
+    assert d["higher_is_better"] is True and d["n_gpus"] == 1 and d["steps"] == 1 and d["warmup"] == 3
+    assert d["value"] > 0 and d["cpu_baseline"]["value"] == d["value"]
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] >= 1
+    assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0,
+                        "d2h_bytes_per_step": 0}
+    assert d["config"]["workload"].startswith("pentagon fluid N=4096")
+
+
+def test_clock_sampler_keeps_samples_of_the_timed_region(tmp_path, monkeypatch):
+    # a stand-in for nvidia-smi that prints one CSV line per 50 ms, the first
+    # one before the timed region starts (left out of the record)
+    sys.path.insert(0, ROOT)
+    import time
+    import bench
+    exe = tmp_path / "nvidia-smi"
+    exe.write_text("#!/bin/bash\n"
+                   "echo '0, 1200, 2070, 90.0, 0x0, Not Active, Not Active, Not Active, Not Active'\n"
+                   "while true; do\n"
+                   "  echo '0, 2070, 2070, 900.0, 0x4, Not Active, Not Active, Not Active, Active'\n"
+                   "  sleep 0.05\n"
+                   "done\n")
+    exe.chmod(0o755)
+    monkeypatch.setenv("PATH", f"{tmp_path}:{os.environ['PATH']}")
+    s = bench.ClockSampler(0, period_ms=50)
+    time.sleep(0.4)
+    c = s.stop()
+    assert c["samples"] >= 3 and c["sm_mhz"] == 2070.0 and c["sm_max_mhz"] == 2070.0
+    assert c["reasons"] == ["sw_power_cap"]
+    monkeypatch.setenv("PATH", str(tmp_path / "none"))
+    assert bench.ClockSampler(0).stop()["reasons"] == ["nvidia-smi unavailable"]
