@@ -34,6 +34,8 @@ def main():
     with open(out, "w") as f:
         f.write(f"# RSA start: N={N} regular pentagons R=0.5, phi={PHI}, L={L.hex()}, seed={SEED}, "
                 f"attempts={used}\n")
+        f.write("# written by tests/golden/make_rsa_init.py with the oracle's or_rsa_2d (random sequential "
+                "addition; overlaps by the contract test of Sec. 2.3); columns x y cos sin as float.hex()\n")
         for i in range(N):
             f.write(" ".join(float(t).hex() for t in (pos[i, 0], pos[i, 1], ori[i, 0], ori[i, 1])) + "\n")
     print(out, used)

@@ -17,7 +17,8 @@ def load_rsa_start():
     header = None
     for line in open(GOLD):
         if line.startswith("#"):
-            header = line
+            if " L=" in line:
+                header = line
             continue
         rows.append([float.fromhex(t) for t in line.split()])
     a = np.array(rows)
