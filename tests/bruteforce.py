@@ -41,8 +41,6 @@ def _poly_world(verts, z, t, scale):
 
 
 def _bf_overlap_2d(PA, PB):
-    n, na, _ = PA.shape
-    nb = PB.shape[1]
     A0 = PA
     A1 = np.roll(PA, -1, axis=1)
     B0 = PB

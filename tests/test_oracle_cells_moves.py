@@ -57,6 +57,7 @@ def test_cell_list_definition():
             members = idx[start[c]:start[c + 1]]
             assert np.all(np.diff(members.astype(np.int64)) > 0)   # ascending tags
             seen[members] += 1
+            assert np.all(cof[members] == c)                        # per-particle cell agrees
             ix, iy = c % nc[0], c // nc[0]
             for t in members:
                 for a, i in ((0, ix), (1, iy)):

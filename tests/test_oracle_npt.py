@@ -4,8 +4,6 @@ An ideal gas (point-like disks) at fixed beta P has the volume law
 P(V) ~ V^N exp(-beta P V) for uniform proposals in V, a Gamma(N + 1,
 beta P) law: mean (N + 1) / (beta P), variance (N + 1) / (beta P)^2.  Hard
 particles: a compression that would create an overlap is never accepted."""
-import math
-
 import numpy as np
 import pytest
 
