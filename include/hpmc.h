@@ -187,8 +187,10 @@ int hpmc_set_state(hpmc_t h, int32_t r, const double* pos, const double* orient,
 /*
  * hpmc_run_host -- end-to-end call for callers holding host buffers: upload
  * every replica's configuration from pos/orient (all replicas concatenated in
- * replica order, tag order inside), run n sweeps, download the result into
- * pos_out/orient_out and the summed counters into *out.  Synchronous.
+ * replica order, tag order inside: pos[Ntot*dim], orient[Ntot*(2|4)], Ntot
+ * the batch's particle count), run n sweeps, download the result into
+ * pos_out/orient_out (same sizes, caller-owned) and the summed counters into
+ * *out (may be NULL).  Synchronous.
  */
 int hpmc_run_host(hpmc_t h, const double* pos, const double* orient, uint32_t n,
                   double* pos_out, double* orient_out, hpmc_counters_t* out, void* stream);
@@ -197,7 +199,9 @@ int hpmc_run_host(hpmc_t h, const double* pos, const double* orient, uint32_t n,
  * hpmc_autotune -- time each (lanes per cell, warps per block) choice on
  * n_trial sweeps from a saved copy of the state, restore the state and
  * sweep counters, and keep the fastest choice.  The trajectory does not
- * depend on the choice.  *best_lanes / *best_warps receive it.  Synchronous.
+ * depend on the choice.  *best_lanes / *best_warps receive it.  A choice
+ * whose sweeps cannot be launched is skipped; a failing CUDA call restores
+ * the previous choice and the state before returning its error.  Synchronous.
  */
 int hpmc_autotune(hpmc_t h, uint32_t n_trial, int* best_lanes, int* best_warps);
 
@@ -253,7 +257,9 @@ int hpmc_get_box(hpmc_t h, int32_t r, double* box);
  * closest to `target` sets the moves.  The configuration, sweep counters
  * and event counters are restored afterwards, so the trajectory continues
  * as if no pilot had run.  *d_out, *a_out (replica r, or replica 0 when
- * r = -1) and *acc_out (may be NULL) receive the result.  Synchronous.
+ * r = -1) and *acc_out (may be NULL) receive the result.  A failing pilot
+ * restores the state and the previous moves before its error is returned.
+ * Synchronous.
  */
 int hpmc_tune_moves(hpmc_t h, int32_t r, double target, uint32_t n_pilot, uint32_t iters, double lo,
                     double hi, double* d_out, double* a_out, double* acc_out);
