@@ -141,6 +141,26 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def host_cpu():
+    """The host the oracle ran on: CPU model (from /proc/cpuinfo where it
+    names one) and the number of logical CPUs."""
+    import platform
+    seen = {}
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                k, _, v = line.partition(":")
+                if v.strip():
+                    seen.setdefault(k.strip(), v.strip())
+    except OSError:
+        pass
+    model = seen.get("model name") or seen.get("Model") or seen.get("Hardware")
+    if not model and "CPU part" in seen:              # Arm: implementer and part number
+        model = f"{platform.machine()} (CPU implementer {seen.get('CPU implementer', '?')}, " \
+                f"part {seen['CPU part']})"
+    return {"model": model or platform.processor() or platform.machine(), "nproc": os.cpu_count()}
+
+
 def oracle_rate(s, melt, sweeps):
     """Oracle (plain C, 1 thread) on the workload: melt, then time `sweeps`."""
     from oracle import oracle as orc
@@ -185,7 +205,8 @@ def run_reference(args):
            "config": {"workload": WORKLOAD, "sweeps_per_step": per_step, "melt_sweeps": MELT},
            "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
                             "sample": f"{args.steps} x {per_step} sweeps of the 4096-pentagon fluid "
-                                      f"after a {MELT}-sweep melt (plain C oracle, 1 thread)"},
+                                      f"after a {MELT}-sweep melt (plain C oracle, 1 thread)",
+                            "host": host_cpu()},
            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
            "gpu_launches": 0}
     print(json.dumps(out))
@@ -381,7 +402,7 @@ def run_ours(args):
     cpu = None
     if not args.no_cpu:
         rate, cmoves, cdt, _ = oracle_rate(s, MELT, args.cpu_sweeps)
-        cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
+        cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle", "host": host_cpu(),
                "sample": f"{args.cpu_sweeps} sweeps ({cmoves} trial moves, {cdt:.1f} s) of the same "
                          f"4096-pentagon fluid after a {MELT}-sweep melt, plain C oracle, 1 thread"}
 
