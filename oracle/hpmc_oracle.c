@@ -31,8 +31,9 @@
  * boxes, ideal-gas closed forms in 2D and 3D, move distributions, O(N^2)
  * no-overlap, zero net probability current of one-particle chains in 2D and
  * 3D (detailed balance), the two-pentagon pair-distance law; for
- * disks/spheres the contact definition and lattice closed forms of the
- * scale-distribution histogram; for volume moves the ideal-gas Gamma law).
+ * disks/spheres the contact definition, lattice closed forms of the
+ * scale-distribution histogram and the dilute hard-disk virial series; for
+ * volume moves the ideal-gas Gamma law).
  */
 #include <math.h>
 #include <stdint.h>
