@@ -32,7 +32,7 @@
  * no-overlap, zero net probability current of one-particle chains in 2D and
  * 3D (detailed balance), the two-pentagon pair-distance law; for
  * disks/spheres the contact definition, lattice closed forms of the
- * scale-distribution histogram and the dilute hard-disk virial series; for
+ * scale-distribution histogram and the dilute disk and sphere virial series; for
  * volume moves the ideal-gas Gamma law).
  */
 #include <math.h>
