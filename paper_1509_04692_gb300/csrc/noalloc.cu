@@ -15,6 +15,7 @@
 // the same width rule and no shift.
 #include <cuda_runtime.h>
 
+#include <atomic>
 #include <cmath>
 #include <cstring>
 
@@ -32,8 +33,10 @@ constexpr size_t kScratchWords = (size_t)kMaxCells + (kMaxCells + 1) + 3 * (size
 
 static __device__ __align__(256) uint32_t g_noalloc_scratch[kScratchWords];
 
-// device address of g_noalloc_scratch per device, looked up once per device
-uint32_t* g_scratch_ptr[kMaxDevices] = {};
+// device address of g_noalloc_scratch per device, looked up on a device's
+// first call; atomic so that host threads making their first calls at the
+// same time do not race (each would store the same address)
+std::atomic<uint32_t*> g_scratch_ptr[kMaxDevices] = {};
 
 struct Grid2 {
     double L[2], halfL[2], inv_w[2];
@@ -141,13 +144,15 @@ int scratch_for_current_device(uint32_t** out)
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) { (void)cudaGetLastError(); return HPMC_ERR_CUDA; }
     if (dev < 0 || dev >= kMaxDevices) return HPMC_ERR_CUDA;
-    if (!g_scratch_ptr[dev]) {
+    uint32_t* known = g_scratch_ptr[dev].load(std::memory_order_acquire);
+    if (!known) {
         void* p = nullptr;
         const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
         if (e != cudaSuccess || !p) { (void)cudaGetLastError(); return HPMC_ERR_CUDA; }
-        g_scratch_ptr[dev] = (uint32_t*)p;
+        known = (uint32_t*)p;
+        g_scratch_ptr[dev].store(known, std::memory_order_release);
     }
-    *out = g_scratch_ptr[dev];
+    *out = known;
     return 0;
 }
 
@@ -197,7 +202,11 @@ extern "C" int hpmc_count_overlaps_noalloc(const double* box, const double* vert
     for (int a = 0; a < 2; ++a) {
         const double L = box[a];
         if (!(L > 0.0) || !std::isfinite(L)) return HPMC_ERR_INVALID_ARG;
-        int n = (int)std::floor(L / dcut);
+        // range check in double before the cast: a large finite box must
+        // read as beyond the scratch, not overflow the integer conversion
+        const double fl = std::floor(L / dcut);
+        if (!(fl <= (double)kMaxCells + 1.0)) return HPMC_ERR_SCRATCH_LIMIT;
+        int n = (int)fl;
         if (n % 2) n -= 1;
         if (n < 4) return HPMC_ERR_BOX_TOO_SMALL;
         if (n > (int)kMaxCells) return HPMC_ERR_SCRATCH_LIMIT;

@@ -8,6 +8,7 @@ import pytest
 
 from oracle import oracle as orc
 from paper_1509_04692_gb300 import inputs
+from tests.paircount import oracle_pair_count, plant_wrap_pairs
 from tests.test_oracle_sweep import load_rsa_start
 
 pytestmark = pytest.mark.gpu
@@ -143,11 +144,14 @@ def test_overlap_check_counts_pairs():
     b.sweep(50)
     assert b.check_overlaps() == 0
     p, o, sw = b.get_state()
-    # plant two overlapping pairs
-    p[1] = p[0]
-    p[3] = np.mod(p[2] + np.array([0.3, 0.0]), s.L)
+    # plant overlapping pairs, across the periodic boundaries too; the count
+    # equals the O(N^2) count with the oracle's overlap test
+    p = plant_wrap_pairs(p, s.L, seed=2)
+    p[41] = p[40]
     b.set_state(p, o, sw)
-    assert b.check_overlaps() >= 2
+    want = oracle_pair_count(orc.OracleSystem(2, s.L, s.verts), p, o)
+    assert want >= 3
+    assert b.check_overlaps() == want
     b.close()
 
 

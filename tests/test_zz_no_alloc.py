@@ -5,17 +5,21 @@ where they need an overlap check (inside a custom memory pool or a callback
 that must not touch the allocator, while a tool records work, or in an
 embedder that owns all device memory).  It takes the caller's device arrays
 and keeps its cell list in a fixed array of the library.  This test checks,
-on two calls in a row, that it counts the same pairs as the allocating entry
-point hpmc_check_overlaps (integer counts: exact equality), and that sizes
-beyond its fixed limit are refused.  The file is named so that pytest runs
-it after every other test.
+on two calls in a row, that it counts the same pairs as an O(N^2) count with
+the oracle's overlap test and as the allocating entry point
+hpmc_check_overlaps (integer counts: exact equality), with pairs planted
+across the periodic x and y boundaries and the corner, and that sizes beyond
+its fixed limit are refused.  The file is named so that pytest runs it after
+every other test.
 """
 import ctypes
 
 import numpy as np
 import pytest
 
+from oracle import oracle as orc
 from paper_1509_04692_gb300 import inputs
+from tests.paircount import oracle_pair_count, plant_wrap_pairs
 
 pytestmark = pytest.mark.gpu
 
@@ -56,24 +60,25 @@ def _allocating_count(s, pos, ori):
     return n
 
 
-def test_noalloc_matches_check_overlaps_on_two_calls():
+def test_noalloc_matches_the_oracle_pair_count_on_two_calls():
     s = inputs.pentagon_system(3000, 0.55, seed=21)
+    ref = orc.OracleSystem(2, s.L, s.verts)
     # call 1: a valid configuration after some sweeps (no overlaps)
     b = hpmc.from_system(s)
     b.sweep(30)
     pos, ori, _ = b.get_state()
     b.close()
-    want1 = _allocating_count(s, pos, ori)
-    got1 = _noalloc_count(s, pos, ori)
-    assert want1 == 0 and got1 == want1
-    # call 2: plant overlaps; the fixed scratch still holds call 1's cell list
-    pos2 = pos.copy()
-    pos2[1] = pos2[0]
-    pos2[5] = np.mod(pos2[4] + np.array([0.25, 0.1]), s.L)
-    pos2[9] = np.mod(pos2[8] + np.array([0.0, 0.3]), s.L)
-    want2 = _allocating_count(s, pos2, ori)
-    got2 = _noalloc_count(s, pos2, ori)
-    assert want2 >= 3 and got2 == want2
+    assert oracle_pair_count(ref, pos, ori) == 0
+    assert _allocating_count(s, pos, ori) == 0
+    assert _noalloc_count(s, pos, ori) == 0
+    # call 2: pairs planted across the x wrap, the y wrap and the corner; the
+    # fixed scratch still holds call 1's cell list
+    pos2 = plant_wrap_pairs(pos, s.L, seed=1)
+    pos2[41] = pos2[40]                     # and two coincident centres
+    want2 = oracle_pair_count(ref, pos2, ori)
+    assert want2 >= 3
+    assert _allocating_count(s, pos2, ori) == want2
+    assert _noalloc_count(s, pos2, ori) == want2
 
 
 def test_noalloc_refuses_sizes_beyond_its_scratch():
@@ -86,8 +91,11 @@ def test_noalloc_refuses_sizes_beyond_its_scratch():
            verts.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), 5, 65537,
            dummy.data_ptr(), dummy.data_ptr(), dummy.data_ptr(), None)
     assert rc == -9
-    big = np.array([600.0, 600.0])          # 600 x 600 cells > 65536
-    rc = f(big.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
-           verts.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), 5, 10,
-           dummy.data_ptr(), dummy.data_ptr(), dummy.data_ptr(), None)
-    assert rc == -9
+    # 600 x 600 cells > 65536; and a box so large that its cell count does
+    # not fit an int (refused before any conversion)
+    for side in (600.0, 1e12):
+        big = np.array([side, side])
+        rc = f(big.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+               verts.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), 5, 10,
+               dummy.data_ptr(), dummy.data_ptr(), dummy.data_ptr(), None)
+        assert rc == -9
