@@ -26,16 +26,24 @@
  * Where the paper is silent the oracle follows the readings listed in the
  * header comments below (philox counter layout, move distributions, ties).
  *
+ * The cells of one checkerboard set never touch one another, so or_sweep can
+ * share them out over host threads (or_set_threads; serial by default) with
+ * a trajectory identical byte for byte to the serial one.
+ *
  * Parity status: every function here is pinned by the CPU tests (Philox
  * known-answer vectors, brute-force polygon/polyhedron predicates, SAT-15 for
  * boxes, ideal-gas closed forms in 2D and 3D, move distributions, O(N^2)
  * no-overlap, zero net probability current of one-particle chains in 2D and
- * 3D (detailed balance), the two-pentagon pair-distance law; for
+ * 3D (detailed balance), the two-pentagon pair-distance law, the exact
+ * one-move acceptance probability of a pentagon beside another (Minkowski
+ * sum overlap region integrated against the in-cell probability); for
  * disks/spheres the contact definition, lattice closed forms of the
  * scale-distribution histogram and the dilute disk and sphere virial series; for
  * volume moves the ideal-gas Gamma law).
  */
+#define _POSIX_C_SOURCE 200809L
 #include <math.h>
+#include <pthread.h>
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
@@ -121,6 +129,7 @@ typedef struct {
     double d, a, tau;
     uint32_t nselect;
     uint64_t seed;
+    int nthreads;               /* host threads sharing a set's cells (<= 1: serial) */
 } or_system;
 
 size_t or_system_size(void) { return sizeof(or_system); }
@@ -639,94 +648,216 @@ static double or_min_image(double dlt, double L, double halfL)
 /* ------------------------------------------------------------------------ */
 /* The sweep (Sec. 2.1 + 2.2.1 + 2.5.1 + 2.5.2)                              */
 /* ------------------------------------------------------------------------ */
+
+/* The nselect trial moves of one active cell (ix, iy, iz) of set `set`
+ * (Sec. 2.5.2: the moves of one cell run in sequence; a trial that leaves the
+ * cell is rejected, so the cell's contents stay fixed during the set).
+ * counters[0] accept, [1] reject_overlap, [2] reject_boundary, [3] gjk caps */
+static void or_cell_moves(const or_system* s, double* pos, double* orient, const double sh[3],
+                          const uint32_t* start, const uint32_t* idx, uint64_t sweep, int set,
+                          int ix, int iy, int iz, uint64_t* counters)
+{
+    const int dim = s->dim;
+    const int qd = (dim == 2) ? 2 : 4;
+    int cell = ix + s->nc[0] * (iy + s->nc[1] * iz);
+    uint32_t n_c = start[cell + 1] - start[cell];
+    if (n_c == 0) return;                             /* empty cells propose nothing */
+    for (uint32_t k = 0; k < s->nselect; ++k) {
+        uint32_t r[16];
+        or_move_words(s, sweep, (uint32_t)set, (uint32_t)cell, k, r);
+        uint32_t j = (uint32_t)(((uint64_t)r[0] * (uint64_t)n_c) >> 32);
+        uint32_t i = idx[start[cell] + j];
+        double xn[3] = { 0, 0, 0 }, qn[4] = { 0, 0, 0, 0 };
+        or_propose(s, r, pos + (size_t)i * dim, orient + (size_t)i * qd, xn, qn);
+        /* checkerboard rule: a trial position outside the
+         * active cell is rejected (Sec. 2.5.1 / 2.5.2) */
+        int ci[3];
+        if (or_cell_of(s, sh, xn, ci) != cell) { counters[2] += 1; continue; }
+        int overlap = 0;
+        for (int oz = (dim == 3 ? -1 : 0); oz <= (dim == 3 ? 1 : 0) && !overlap; ++oz)
+        for (int oy = -1; oy <= 1 && !overlap; ++oy)
+        for (int ox = -1; ox <= 1 && !overlap; ++ox) {
+            int jx = (ix + ox + s->nc[0]) % s->nc[0];
+            int jy = (iy + oy + s->nc[1]) % s->nc[1];
+            int jz = (dim == 3) ? (iz + oz + s->nc[2]) % s->nc[2] : 0;
+            int nb = jx + s->nc[0] * (jy + s->nc[1] * jz);
+            for (uint32_t e = start[nb]; e < start[nb + 1]; ++e) {
+                uint32_t b = idx[e];
+                if (b == i) continue;
+                double D[3] = { 0, 0, 0 };
+                double q2 = 0.0;
+                for (int kk = 0; kk < dim; ++kk) {
+                    D[kk] = or_min_image(pos[(size_t)b * dim + kk] - xn[kk], s->L[kk], s->halfL[kk]);
+                }
+                q2 = D[0] * D[0] + D[1] * D[1];
+                if (dim == 3) q2 = q2 + D[2] * D[2];
+                if (q2 > s->rc2) continue;           /* circumsphere cull */
+                int ov;
+                if (s->nv == 0) {
+                    ov = 1;                 /* disks/spheres: q2 <= (2R)^2 */
+                } else if (dim == 2) {
+                    ov = or_overlap_2d(s, D, qn, orient + (size_t)b * qd);
+                } else {
+                    int it = 0;
+                    ov = or_overlap_3d(s, D, qn, orient + (size_t)b * qd, &it);
+                    if (it > OR_GJK_MAXIT) counters[3] += 1;
+                }
+                if (ov) { overlap = 1; break; }     /* early exit (Sec. 2.1) */
+            }
+        }
+        if (overlap) { counters[1] += 1; continue; }
+        for (int kk = 0; kk < dim; ++kk) pos[(size_t)i * dim + kk] = xn[kk];
+        for (int kk = 0; kk < qd; ++kk) orient[(size_t)i * qd + kk] = qn[kk];
+        counters[0] += 1;
+    }
+}
+
+/* One set of a sweep: every active cell (parity bits = set) in turn, or,
+ * with nthr > 1, the cells whose rank in that order is thr modulo nthr.
+ * Active cells of one set never touch one another (a moved particle stays in
+ * its cell, and a cell's 3^d stencil holds no other active cell), so the
+ * result does not depend on how the cells are shared out. */
+static void or_set_cells(const or_system* s, double* pos, double* orient, const double sh[3],
+                         const uint32_t* start, const uint32_t* idx, uint64_t sweep, int set,
+                         int thr, int nthr, uint64_t* counters)
+{
+    const int dim = s->dim;
+    const int nz = (dim == 3) ? s->nc[2] : 1;
+    int px = set & 1, py = (set >> 1) & 1, pz = (set >> 2) & 1;
+    long rank = 0;
+    for (int iz = 0; iz < nz; ++iz) {
+        if (dim == 3 && (iz & 1) != pz) continue;
+        for (int iy = 0; iy < s->nc[1]; ++iy) {
+            if ((iy & 1) != py) continue;
+            for (int ix = 0; ix < s->nc[0]; ++ix) {
+                if ((ix & 1) != px) continue;
+                if (rank++ % nthr != thr) continue;
+                or_cell_moves(s, pos, orient, sh, start, idx, sweep, set, ix, iy, iz, counters);
+            }
+        }
+    }
+}
+
+/* One thread's share of a set (threaded sweeps). */
+typedef struct {
+    const or_system* s;
+    double* pos;
+    double* orient;
+    const double* sh;
+    const uint32_t* start;
+    const uint32_t* idx;
+    uint64_t sweep;
+    int set, thr, nthr;
+    uint64_t counters[4];
+} or_share;
+
+static void* or_share_run(void* p)
+{
+    or_share* a = (or_share*)p;
+    or_set_cells(a->s, a->pos, a->orient, a->sh, a->start, a->idx, a->sweep, a->set, a->thr, a->nthr,
+                 a->counters);
+    return NULL;
+}
+
+/* Host threads for the sets of or_sweep (1 = serial, the default). */
+int or_set_threads(or_system* s, int nthreads)
+{
+    if (nthreads < 1 || nthreads > 1024) return -1;
+    s->nthreads = nthreads;
+    return 0;
+}
+
 /* counters[0] accept, [1] reject_overlap, [2] reject_boundary, [3] gjk caps */
 int or_sweep(or_system* s, uint32_t N, double* pos, double* orient, uint64_t sweep0,
              uint32_t nsweeps, uint64_t* counters)
 {
     const int dim = s->dim;
-    const int qd = (dim == 2) ? 2 : 4;
     const int C = or_ncells(s);
     uint32_t* start = (uint32_t*)malloc(sizeof(uint32_t) * (size_t)(C + 1));
     uint32_t* idx = (uint32_t*)malloc(sizeof(uint32_t) * (size_t)(N > 0 ? N : 1));
     int* cell_of = (int*)malloc(sizeof(int) * (size_t)(N > 0 ? N : 1));
     if (!start || !idx || !cell_of) { free(start); free(idx); free(cell_of); return -3; }
     const int nsets = 1 << dim;
-    const int nz = (dim == 3) ? s->nc[2] : 1;
+    const int nthr = s->nthreads > 1 ? s->nthreads : 1;
+    int rc = 0;
 
-    for (uint32_t sw = 0; sw < nsweeps; ++sw) {
-        uint64_t sweep = sweep0 + sw;
-        double sh[3];
-        or_grid_shift(s, sweep, sh);
-        or_build_cells(s, N, pos, sh, start, idx, cell_of);
-
-        for (int set = 0; set < nsets; ++set) {
-            int px = set & 1, py = (set >> 1) & 1, pz = (set >> 2) & 1;
-            for (int iz = 0; iz < nz; ++iz) {
-                if (dim == 3 && (iz & 1) != pz) continue;
-                for (int iy = 0; iy < s->nc[1]; ++iy) {
-                    if ((iy & 1) != py) continue;
-                    for (int ix = 0; ix < s->nc[0]; ++ix) {
-                        if ((ix & 1) != px) continue;
-                        int cell = ix + s->nc[0] * (iy + s->nc[1] * iz);
-                        uint32_t n_c = start[cell + 1] - start[cell];
-                        if (n_c == 0) continue;           /* empty cells propose nothing */
-                        for (uint32_t k = 0; k < s->nselect; ++k) {
-                            uint32_t r[16];
-                            or_move_words(s, sweep, (uint32_t)set, (uint32_t)cell, k, r);
-                            uint32_t j = (uint32_t)(((uint64_t)r[0] * (uint64_t)n_c) >> 32);
-                            uint32_t i = idx[start[cell] + j];
-                            double xn[3] = { 0, 0, 0 }, qn[4] = { 0, 0, 0, 0 };
-                            or_propose(s, r, pos + (size_t)i * dim, orient + (size_t)i * qd, xn, qn);
-                            /* checkerboard rule: a trial position outside the
-                             * active cell is rejected (Sec. 2.5.1 / 2.5.2) */
-                            int ci[3];
-                            if (or_cell_of(s, sh, xn, ci) != cell) { counters[2] += 1; continue; }
-                            int overlap = 0;
-                            for (int oz = (dim == 3 ? -1 : 0); oz <= (dim == 3 ? 1 : 0) && !overlap; ++oz)
-                            for (int oy = -1; oy <= 1 && !overlap; ++oy)
-                            for (int ox = -1; ox <= 1 && !overlap; ++ox) {
-                                int jx = (ix + ox + s->nc[0]) % s->nc[0];
-                                int jy = (iy + oy + s->nc[1]) % s->nc[1];
-                                int jz = (dim == 3) ? (iz + oz + s->nc[2]) % s->nc[2] : 0;
-                                int nb = jx + s->nc[0] * (jy + s->nc[1] * jz);
-                                for (uint32_t e = start[nb]; e < start[nb + 1]; ++e) {
-                                    uint32_t b = idx[e];
-                                    if (b == i) continue;
-                                    double D[3] = { 0, 0, 0 };
-                                    double q2 = 0.0;
-                                    for (int kk = 0; kk < dim; ++kk) {
-                                        D[kk] = or_min_image(pos[(size_t)b * dim + kk] - xn[kk], s->L[kk], s->halfL[kk]);
-                                    }
-                                    q2 = D[0] * D[0] + D[1] * D[1];
-                                    if (dim == 3) q2 = q2 + D[2] * D[2];
-                                    if (q2 > s->rc2) continue;           /* circumsphere cull */
-                                    int ov;
-                                    if (s->nv == 0) {
-                                        ov = 1;                 /* disks/spheres: q2 <= (2R)^2 */
-                                    } else if (dim == 2) {
-                                        ov = or_overlap_2d(s, D, qn, orient + (size_t)b * qd);
-                                    } else {
-                                        int it = 0;
-                                        ov = or_overlap_3d(s, D, qn, orient + (size_t)b * qd, &it);
-                                        if (it > OR_GJK_MAXIT) counters[3] += 1;
-                                    }
-                                    if (ov) { overlap = 1; break; }     /* early exit (Sec. 2.1) */
-                                }
-                            }
-                            if (overlap) { counters[1] += 1; continue; }
-                            for (int kk = 0; kk < dim; ++kk) pos[(size_t)i * dim + kk] = xn[kk];
-                            for (int kk = 0; kk < qd; ++kk) orient[(size_t)i * qd + kk] = qn[kk];
-                            counters[0] += 1;
-                        }
-                    }
+    if (nthr == 1) {
+        for (uint32_t sw = 0; sw < nsweeps; ++sw) {
+            uint64_t sweep = sweep0 + sw;
+            double sh[3];
+            or_grid_shift(s, sweep, sh);
+            or_build_cells(s, N, pos, sh, start, idx, cell_of);
+            for (int set = 0; set < nsets; ++set)
+                or_set_cells(s, pos, orient, sh, start, idx, sweep, set, 0, 1, counters);
+        }
+    } else {
+        /* each set forks nthr shares and joins them before the next set; a
+         * share whose thread cannot be started runs on this thread */
+        or_share* sh_args = (or_share*)calloc((size_t)nthr, sizeof(or_share));
+        pthread_t* tid = (pthread_t*)calloc((size_t)nthr, sizeof(pthread_t));
+        int* started = (int*)calloc((size_t)nthr, sizeof(int));
+        if (!sh_args || !tid || !started) rc = -3;
+        for (uint32_t sw = 0; sw < nsweeps && rc == 0; ++sw) {
+            uint64_t sweep = sweep0 + sw;
+            double sh[3];
+            or_grid_shift(s, sweep, sh);
+            or_build_cells(s, N, pos, sh, start, idx, cell_of);
+            for (int set = 0; set < nsets; ++set) {
+                for (int t = 0; t < nthr; ++t) {
+                    or_share* a = &sh_args[t];
+                    a->s = s; a->pos = pos; a->orient = orient; a->sh = sh;
+                    a->start = start; a->idx = idx; a->sweep = sweep;
+                    a->set = set; a->thr = t; a->nthr = nthr;
+                    started[t] = (t > 0) && pthread_create(&tid[t], NULL, or_share_run, a) == 0;
+                }
+                or_share_run(&sh_args[0]);
+                for (int t = 1; t < nthr; ++t) {
+                    if (started[t]) pthread_join(tid[t], NULL);
+                    else or_share_run(&sh_args[t]);
                 }
             }
         }
+        if (rc == 0)
+            for (int t = 0; t < nthr; ++t)
+                for (int k = 0; k < 4; ++k) counters[k] += sh_args[t].counters[k];
+        free(sh_args);
+        free(tid);
+        free(started);
     }
     free(start);
     free(idx);
     free(cell_of);
-    return 0;
+    return rc;
+}
+
+/* Test hook: n independent one-sweep runs of or_sweep, each from the same
+ * configuration (pos0, ori0) at sweep index sweep0 + k.  moved[k*N + i] is 1
+ * when particle i's position or orientation changed in run k; shifts[3k..]
+ * receives that run's grid shift.  Used to measure the one-move acceptance
+ * frequency of a fixed configuration (Sec. 2.1). */
+int or_sweep_repeats(or_system* s, uint32_t N, const double* pos0, const double* ori0, uint64_t sweep0,
+                     uint32_t n, uint8_t* moved, double* shifts)
+{
+    const int dim = s->dim, qd = (dim == 2) ? 2 : 4;
+    double* pos = (double*)malloc(sizeof(double) * (size_t)N * dim);
+    double* ori = (double*)malloc(sizeof(double) * (size_t)N * qd);
+    if (!pos || !ori) { free(pos); free(ori); return -3; }
+    int rc = 0;
+    for (uint32_t k = 0; k < n && rc == 0; ++k) {
+        uint64_t cnt[4] = { 0, 0, 0, 0 };
+        memcpy(pos, pos0, sizeof(double) * (size_t)N * dim);
+        memcpy(ori, ori0, sizeof(double) * (size_t)N * qd);
+        rc = or_sweep(s, N, pos, ori, sweep0 + k, 1, cnt);
+        or_grid_shift(s, sweep0 + k, shifts + 3 * (size_t)k);
+        for (uint32_t i = 0; i < N; ++i)
+            moved[(size_t)k * N + i] = (uint8_t)(memcmp(pos + (size_t)i * dim, pos0 + (size_t)i * dim,
+                                                        sizeof(double) * dim) != 0 ||
+                                                 memcmp(ori + (size_t)i * qd, ori0 + (size_t)i * qd,
+                                                        sizeof(double) * qd) != 0);
+    }
+    free(pos);
+    free(ori);
+    return rc;
 }
 
 /* Batch evaluation of the overlap contract on many pairs (for tests); in 3D

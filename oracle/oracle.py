@@ -36,7 +36,7 @@ def build(force: bool = False) -> str:
             and os.path.getmtime(_SO) >= os.path.getmtime(_SRC)):
         return _SO
     tmp = _SO + f".tmp{os.getpid()}"
-    subprocess.check_call(["gcc", *CFLAGS, "-o", tmp, _SRC, "-lm"])
+    subprocess.check_call(["gcc", *CFLAGS, "-o", tmp, _SRC, "-lm", "-pthread"])
     os.replace(tmp, _SO)
     return _SO
 
@@ -67,6 +67,11 @@ def lib():
                                            ctypes.POINTER(ctypes.c_int32)]
             L.or_overlap_batch_it.argtypes = [ctypes.c_void_p, ctypes.c_uint32, dp, dp, dp,
                                               ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32)]
+            L.or_sweep_repeats.restype = ctypes.c_int
+            L.or_sweep_repeats.argtypes = [ctypes.c_void_p, ctypes.c_uint32, dp, dp, ctypes.c_uint64,
+                                           ctypes.c_uint32, ctypes.POINTER(ctypes.c_uint8), dp]
+            L.or_set_threads.restype = ctypes.c_int
+            L.or_set_threads.argtypes = [ctypes.c_void_p, ctypes.c_int]
             L.or_sweep.restype = ctypes.c_int
             L.or_sweep.argtypes = [ctypes.c_void_p, ctypes.c_uint32, dp, dp, ctypes.c_uint64,
                                    ctypes.c_uint32, ctypes.POINTER(ctypes.c_uint64)]
@@ -177,6 +182,12 @@ class OracleSystem:
         self.seed = int(seed)
         self.nselect = int(nselect)
 
+    def set_threads(self, n):
+        """Host threads sharing the active cells of each set in sweep()
+        (1 = serial, the default); the trajectory does not depend on it."""
+        if lib().or_set_threads(self.ptr, int(n)) != 0:
+            raise ValueError("thread count must be 1..1024")
+
     def geometry(self):
         R = ctypes.c_double()
         rc2 = ctypes.c_double()
@@ -245,6 +256,20 @@ class OracleSystem:
         if rc != 0:
             raise RuntimeError(f"or_sweep failed ({rc})")
         return cnt
+
+    def sweep_repeats(self, pos, orient, sweep0, n):
+        """n independent single sweeps, each from (pos, orient) at sweep index
+        sweep0 + k.  Returns (moved[n, N] bool, shifts[n, dim])."""
+        pos = np.ascontiguousarray(pos, dtype=np.float64)
+        orient = np.ascontiguousarray(orient, dtype=np.float64)
+        N = pos.shape[0]
+        moved = np.zeros((n, N), dtype=np.uint8)
+        shifts = np.zeros((n, 3))
+        rc = lib().or_sweep_repeats(self.ptr, N, _dp(pos), _dp(orient), int(sweep0), int(n),
+                                    moved.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)), _dp(shifts))
+        if rc != 0:
+            raise RuntimeError(f"or_sweep_repeats failed ({rc})")
+        return moved.astype(bool), shifts[:, : self.dim].copy()
 
     def propose(self, sweep, set_, cell, k, n_c, x, q):
         x = np.ascontiguousarray(x, dtype=np.float64)
