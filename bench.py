@@ -1,21 +1,27 @@
 """Benchmark: trial moves/s of the checkerboard hard-particle MC sweep on GB300.
 
-Workload (the configuration the headline metric is quoted on): 4096 regular
-pentagons (circumradius 0.5) at area fraction 0.60, d = a = 0.165 (30%
-acceptance), nselect = 4, Philox seed 42, melted 1000 sweeps from the lattice
-start before timing.  One step = SWEEPS_PER_STEP sweeps (shift + cell-list
-rebuild + 4 checkerboard sets each), replayed from a CUDA graph.
+Headline workload (the largest single-GPU configuration): 2^24 regular
+pentagons (circumradius 0.5) at area fraction 0.60 on a 2048 x 2048 cell
+list (cell width >= 1.99), d = a = 0.165, nselect = 4, Philox seed 42, melted
+200 sweeps from the lattice start before timing.  One step = 40 sweeps
+(shift + cell-list rebuild + 4 checkerboard sets each), replayed from CUDA
+graphs.  The state (2 GB) is larger than L2, and L2 is also flushed between
+timed steps.
 
 Headline `value`: FP32-filtered form (decisions identical to FP64), inputs
-resident in HBM.  `forms` reports the plain FP64 form on the same workload,
-the batched form (512 replicas of N ~ U{256..8192}, phi ~ U[0.40, 0.70]),
-32768 cubes and 32000 dodecahedra at volume fraction 0.50 in both forms, and
-2^24 pentagons at area
-fraction 0.60 on a 2048^2 cell list (FP32-filtered).
-`e2e`: the same metric through hpmc_run_host with host buffers (H2D + sweeps
-+ D2H inside the timed region).  `cpu_baseline`: the C oracle on host cores.
+resident in HBM.  `forms` reports the plain FP64 form of the same system from
+the same melted state (its accept / reject counts must equal the filtered
+form's, else the run stops), and every other configuration in both forms
+with the same check: 1024 pentagons from their random-sequential-addition
+start, the 4096-pentagon fluid, 32768 cubes and 32000 dodecahedra at volume
+fraction 0.50, and the batch of 512 independent replicas (N ~ U{256..8192},
+phi ~ U[0.40, 0.70]).  `roofline`: the set kernel's algorithmic flops over
+its CUDA-event duration against the FP32 fused multiply-add rate measured in
+the same run.  `e2e`: the same metric through hpmc_run_host with host
+buffers (H2D + sweeps + D2H inside the timed region).  `cpu_baseline`: the C
+oracle on all host cores (and on one).
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference] [--quick]
 """
 from __future__ import annotations
 
@@ -37,26 +43,19 @@ from paper_1509_04692_gb300 import inputs  # noqa: E402
 
 METRIC = "trial moves/sec on 1 GB300 (FP32-filtered+batched vs plain FP64), % of roofline"
 UNIT = "trial moves/s"
-WORKLOAD = "pentagon fluid N=4096 phi=0.60 d=a=0.165 (~30% acceptance), nselect=4, seed 42"
-SWEEPS_PER_STEP = 200
-MELT = 1000
-# roofline of the set kernel: FP32 lanes x 2 flop (FMA) x max SM clock
-SMS, FP32_LANES, MAX_MHZ = 152, 128, 2070.0
-PEAK_TFLOPS = SMS * FP32_LANES * 2 * MAX_MHZ * 1e6 / 1e12
-# algorithmic flops: move arithmetic + circumsphere culls + full SAT checks
-FLOP_MOVE, FLOP_CULL, FLOP_SAT = 30, 5, 330
-# per dimension: (move, cull candidate, full overlap test); 3D: the cube GJK
-# estimate (B's vertices into A's frame ~300, ~5 iterations of ~130)
-FLOPS = {2: (FLOP_MOVE, FLOP_CULL, FLOP_SAT), 3: (80, 8, 1000)}
-# DRAM bytes (read + write) of one set launch of this workload from ncu
-# (profiles/set2d_fluid4096.md, cold-cache replay); valid for the kernel as
-# captured there
-SET2D_FLUID_DRAM_BYTES = 466432
-# the same capture's unit utilisations (fractions of each unit's peak): no
-# unit is near its peak, the kernel is bound by one warp's dependency chain
-SET2D_FLUID_NCU = {"issue_active": 0.185, "fp64_pipe": 0.113, "alu_pipe": 0.102, "fma_pipe": 0.054,
-                   "warps_active": 0.083, "dram_throughput": 0.0034,
-                   "binding": "latency (one warp's chain of 4 selects per active cell)"}
+# the headline workload: the largest single-GPU configuration
+WORKLOAD = ("2^24 regular pentagons (circumradius 0.5), area fraction 0.60, 2048^2 cells (w_min 1.99), "
+            "d=a=0.165, nselect=4, Philox seed 42")
+MELT_LARGE = 200              # graph-replayed sweeps from the lattice before timing
+SWEEPS_LARGE = 40             # sweeps per timed step
+MELT = 1000                   # melt of the smaller systems
+RSA1024 = os.path.join(ROOT, "tests", "golden", "rsa_pentagons_N1024_phi050_seed42.txt")
+# algorithmic flops per unit of work, per dimension: (trial move arithmetic,
+# circumsphere cull candidate, full overlap test: the pentagon separating-axis
+# test / the cube GJK estimate)
+FLOPS = {2: (30, 5, 330), 3: (80, 8, 1000)}
+# FMA-chain sizes of the peak measurement (each launch lasts ~20-40 ms)
+PEAK_ITERS = {False: 400000, True: 6000}
 
 
 def job_totals(torch, ms, moves, device):
@@ -161,32 +160,57 @@ def host_cpu():
     return {"model": model or platform.processor() or platform.machine(), "nproc": os.cpu_count()}
 
 
-def oracle_rate(s, melt, sweeps):
-    """Oracle (plain C, 1 thread) on the workload: melt, then time `sweeps`."""
+def load_rsa1024():
+    """The 1024-pentagon random-sequential-addition start (area fraction
+    0.50, seed 42; hex floats x y cos sin), an inputs.System with the
+    configuration's move sizes d = a = 0.1, nselect 4."""
+    rows, L = [], None
+    with open(RSA1024) as f:
+        for line in f:
+            if line.startswith("#"):
+                if " L=" in line:
+                    L = float.fromhex(line.split("L=")[1].split(",")[0])
+                continue
+            rows.append([float.fromhex(t) for t in line.split()])
+    a = np.array(rows)
+    return inputs.System(name="pentagons N=1024 phi=0.50 (RSA start)", dim=2, verts=inputs.regular_polygon(5, 0.5),
+                         L=np.array([L, L]), pos=a[:, :2].copy(), orient=a[:, 2:].copy(), seed=42, d=0.1,
+                         a=0.1, nselect=4, phi=0.50)
+
+
+def oracle_rate(s, pos, ori, sweep0, sweeps, threads):
+    """The C oracle (threaded set sweep) on `sweeps` sweeps of system s from
+    (pos, ori) at sweep index sweep0: (moves/s, moves, seconds)."""
     from oracle import oracle as orc
-    ref = orc.OracleSystem(2, s.L, s.verts, w_min=s.w_min)
+    ref = orc.OracleSystem(s.dim, s.L, s.verts, w_min=s.w_min)
     ref.set_moves(s.d, s.a, s.nselect, s.seed)
-    pos, ori = s.pos.copy(), s.orient.copy()
-    ref.sweep(pos, ori, 0, melt)
+    ref.set_threads(threads)
+    p, q = np.ascontiguousarray(pos).copy(), np.ascontiguousarray(ori).copy()
     t0 = time.perf_counter()
-    c = ref.sweep(pos, ori, melt, sweeps)
+    c = ref.sweep(p, q, sweep0, sweeps)
     dt = time.perf_counter() - t0
     moves = int(c[0] + c[1] + c[2])
-    return moves / dt, moves, dt, (pos, ori)
+    return moves / dt, moves, dt
 
 
-def run_reference(args):
+def run_reference(args, system=None, melt=MELT_LARGE):
+    """The oracle as it stands, on the host cores (threaded set sweep, every
+    logical CPU), on the headline workload: the same melt from the same
+    lattice start (untimed), then warm-up and timed steps of one sweep.
+    (`system` and `melt` replace the workload in the CPU tests.)"""
     ws, rank, _ = dist_env()
     if rank != 0:
         return
-    s = inputs.fluid4096(42)
-    per_step = 40                     # sweeps of the oracle per step (bounded sample)
     from oracle import oracle as orc
-    ref = orc.OracleSystem(2, s.L, s.verts)
+    s = system if system is not None else inputs.large2d(42)
+    threads = os.cpu_count() or 1
+    ref = orc.OracleSystem(2, s.L, s.verts, w_min=s.w_min)
     ref.set_moves(s.d, s.a, s.nselect, s.seed)
+    ref.set_threads(threads)
     pos, ori = s.pos.copy(), s.orient.copy()
-    ref.sweep(pos, ori, 0, MELT)
-    sweep = MELT
+    ref.sweep(pos, ori, 0, melt)
+    sweep = melt
+    per_step = 1
     for _ in range(args.warmup):
         ref.sweep(pos, ori, sweep, per_step)
         sweep += per_step
@@ -202,19 +226,33 @@ def run_reference(args):
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
            "data": "synthetic",
-           "config": {"workload": WORKLOAD, "sweeps_per_step": per_step, "melt_sweeps": MELT},
-           "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
-                            "sample": f"{args.steps} x {per_step} sweeps of the 4096-pentagon fluid "
-                                      f"after a {MELT}-sweep melt (plain C oracle, 1 thread)",
+           "config": {"workload": WORKLOAD if system is None else s.name, "sweeps_per_step": per_step,
+                      "melt_sweeps": melt},
+           "cpu_baseline": {"value": v, "unit": UNIT, "cores": threads, "kind": "oracle",
+                            "sample": f"{args.steps} x {per_step} sweep(s) of {s.name} after "
+                                      f"the oracle's own {melt}-sweep melt from the lattice (plain C "
+                                      f"oracle, cells of each set shared over {threads} threads)",
                             "host": host_cpu()},
            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
            "gpu_launches": 0}
     print(json.dumps(out))
 
 
-def time_steps(b, torch, stream, steps, warmup, flush, sweeps=SWEEPS_PER_STEP):
+def time_steps(b, torch, stream, steps, warmup, flush, sweeps):
+    """warmup + steps graph-replayed steps of `sweeps` sweeps; CUDA events on
+    the launching stream around each timed step, L2 flushed before each.
+    Returns (total ms of the timed steps, counter deltas of the timed steps,
+    cumulative (accept, reject_overlap, reject_boundary) after each step
+    from the start, warm-up steps included)."""
+    c_start = b.counters()
+    cum = []
+
+    def mark():
+        c = b.counters()
+        cum.append(tuple(c[k] - c_start[k] for k in ("accept", "reject_overlap", "reject_boundary")))
     for _ in range(warmup):
         b.sweep(sweeps, stream=stream.cuda_stream, graph=True)
+        mark()
     torch.cuda.synchronize()
     c0 = b.counters()
     total_ms = 0.0
@@ -227,37 +265,78 @@ def time_steps(b, torch, stream, steps, warmup, flush, sweeps=SWEEPS_PER_STEP):
         e1.record(stream)
         e1.synchronize()
         total_ms += e0.elapsed_time(e1)
+        mark()
     c1 = b.counters()
     d = {k: c1[k] - c0[k] for k in c1}
-    return total_ms, d
+    return total_ms, d, cum
 
 
-def measure_form(b, torch, stream, flush, precision, melt, sweeps, steps, n_tune=4):
-    """Melt (untimed), autotune, then time `steps` graph-replayed steps of
-    `sweeps` sweeps; L2 flushed between steps."""
+def set_kernel_roofline(b, stream, n_prof, peak32, peak64):
+    """Algorithmic flops of the set kernels over `n_prof` directly launched
+    sweeps, divided by their mean duration (CUDA events on the stream the
+    kernels run on), against the measured FP32 and FP64 fused multiply-add
+    peaks.  The state advances by n_prof sweeps."""
+    b.reset_counters()
+    ms_rebuild, ms_sets = b.profile_sweeps(n_prof, stream=stream.cuda_stream)
+    cp = b.counters()
+    nsets = 1 << b.dim
+    fm, fc, ft = FLOPS[b.dim]
+    flop_per_launch = (fm * cp["moves"] + fc * cp["cull_pairs"] + ft * cp["overlap_checks"]) / (n_prof * nsets)
+    set_ms = ms_sets / nsets
+    achieved = flop_per_launch / (set_ms * 1e-3)
+    return {"bound": "alu", "achieved": achieved / 1e12, "peak": peak32 / 1e12, "unit": "TFLOP/s",
+            "frac": achieved / peak32, "traffic": None,
+            "frac_of_fp64_peak": achieved / peak64,
+            "set_kernel_ms": set_ms, "rebuild_ms_per_sweep": ms_rebuild,
+            "flop_per_launch": flop_per_launch,
+            "moves_per_launch": cp["moves"] / (n_prof * nsets),
+            "flops_model": f"{fm} per trial move + {fc} per cull candidate + {ft} per full overlap test"}
+
+
+def measure_form(b, torch, stream, flush, precision, melt, sweeps, steps, peaks, n_tune=4):
+    """Melt (untimed, graph-replayed), autotune (state restored), one warm-up
+    step, then `steps` timed steps of `sweeps` sweeps; L2 flushed between
+    steps; then the set kernels' roofline over a few more sweeps."""
     from paper_1509_04692_gb300 import hpmc
     b.set_precision(precision)
     if melt:
         b.sweep(melt, stream=stream.cuda_stream, graph=True)
     lanes, warps = b.autotune(n_tune)
-    ms, c = time_steps(b, torch, stream, steps, 1, flush, sweeps)
-    # the set kernels' ALU roofline fraction under the same flop model as the
-    # headline (per move, per cull candidate, per full overlap test)
-    b.reset_counters()
-    n_prof = max(1, sweeps // 2)
-    _, ms_sets = b.profile_sweeps(n_prof, stream=stream.cuda_stream)
-    cp = b.counters()
-    fm, fc, ft = FLOPS[b.dim]
-    flop = fm * cp["moves"] + fc * cp["cull_pairs"] + ft * cp["overlap_checks"]
-    achieved = flop / (ms_sets * n_prof * 1e-3) / 1e12
+    ms, c, cum = time_steps(b, torch, stream, steps, 1, flush, sweeps)
+    rf = set_kernel_roofline(b, stream, max(1, min(sweeps, 20)), *peaks)
     return {"value": c["moves"] / (ms * 1e-3),
-            "roofline_frac_alu": achieved / PEAK_TFLOPS, "set_kernels_tflops": achieved,
             "precision": "FP64" if precision == hpmc.HPMC_FP64 else "FP32_FILTERED",
             "lanes_per_cell": lanes, "warps_per_block": warps, "ms_per_step": ms / steps,
             "sweeps_per_step": sweeps, "steps": steps, "melt_sweeps": melt,
             "acceptance": c["accept"] / max(1, c["moves"]),
             "overlap_checks": c["overlap_checks"], "fp64_rechecks": c["fp64_rechecks"],
-            "accept": c["accept"], "moves": c["moves"]}
+            "accept": c["accept"], "reject_overlap": c["reject_overlap"],
+            "reject_boundary": c["reject_boundary"], "moves": c["moves"],
+            "set_kernel_frac_alu": rf["frac"], "set_kernel_tflops": rf["achieved"],
+            "set_kernel_ms": rf["set_kernel_ms"]}
+
+
+def same_decisions(a, b, what):
+    """The FP32-filtered and plain FP64 forms of one workload must make the
+    same accept / reject decisions; a difference stops the benchmark."""
+    ka = (a["accept"], a["reject_overlap"], a["reject_boundary"])
+    kb = (b["accept"], b["reject_overlap"], b["reject_boundary"])
+    if ka != kb:
+        raise SystemExit(f"{what}: FP32-filtered and FP64 decisions differ: {ka} vs {kb}")
+    return True
+
+
+def measure_peaks(hpmc, local):
+    """Measured FP32 and FP64 fused multiply-add rates (flop/s) with the SM
+    clock sampled during the measurement."""
+    sampler = ClockSampler(local)
+    p32, ms32 = hpmc.measure_fma_peak(False, PEAK_ITERS[False], reps=5)
+    p64, ms64 = hpmc.measure_fma_peak(True, PEAK_ITERS[True], reps=5)
+    clk = sampler.stop()
+    return p32, p64, {"fp32_tflops": p32 / 1e12, "fp64_tflops": p64 / 1e12, "fp32_launch_ms": ms32,
+                      "fp64_launch_ms": ms64, "clocks": clk,
+                      "method": "8 independent FMA chains per thread, 2048 threads per SM on every SM, "
+                                "best of 5 launches, CUDA events"}
 
 
 def run_ours(args):
@@ -272,19 +351,24 @@ def run_ours(args):
         torch.cuda.set_device(0)
     stream = torch.cuda.current_stream()
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    multi = ws > 1
 
-    s = inputs.fluid4096(42 + rank)
+    p32, p64, peaks = measure_peaks(hpmc, local)
+
+    # ---- headline: the 2^24-pentagon system, FP32-filtered
+    s = inputs.large2d(42 + rank)
     b = hpmc.from_system(s)
     b.set_precision(hpmc.HPMC_FP32_FILTERED)
-    b.sweep(MELT, stream=stream.cuda_stream, graph=True)       # melt (untimed)
-    lanes, warps = b.autotune(8)                               # state restored afterwards
+    b.sweep(MELT_LARGE, stream=stream.cuda_stream, graph=True)      # melt (untimed)
+    lanes, warps = b.autotune(2)                                      # state restored afterwards
+    snap = b.get_state() if not multi else None                      # for the FP64 form and the CPU baseline
     torch.cuda.synchronize()
 
-    if ws > 1:
+    if multi:
         dist.barrier()
     torch.cuda.synchronize()
     sampler = ClockSampler(local) if rank == 0 else None
-    ms, cnt = time_steps(b, torch, stream, args.steps, args.warmup, flush)
+    ms, cnt, cum32 = time_steps(b, torch, stream, args.steps, args.warmup, flush, SWEEPS_LARGE)
     clocks = sampler.stop() if sampler else None
     moves = cnt["moves"]
     ms_job, moves_job = job_totals(torch, ms, moves, "cuda")
@@ -298,131 +382,124 @@ def run_ours(args):
     pin_o = torch.from_numpy(np.ascontiguousarray(o_in)).pin_memory()
     out_p = torch.empty_like(pin_p).pin_memory()
     out_o = torch.empty_like(pin_o).pin_memory()
+    del p_in, o_in
     torch.cuda.synchronize()
-    b.run_host(pin_p.numpy(), pin_o.numpy(), SWEEPS_PER_STEP, out_p.numpy(), out_o.numpy(),
+    b.run_host(pin_p.numpy(), pin_o.numpy(), SWEEPS_LARGE, out_p.numpy(), out_o.numpy(),
                stream=stream.cuda_stream)                    # warm-up
     e2e_moves, e2e_dt = 0, 0.0
     e2e_steps = max(3, args.steps // 2)
-    if ws > 1:
+    if multi:
         dist.barrier()
     for _ in range(e2e_steps):
         b.reset_counters()
         t0 = time.perf_counter()
-        c = b.run_host(pin_p.numpy(), pin_o.numpy(), SWEEPS_PER_STEP, out_p.numpy(), out_o.numpy(),
+        c = b.run_host(pin_p.numpy(), pin_o.numpy(), SWEEPS_LARGE, out_p.numpy(), out_o.numpy(),
                        stream=stream.cuda_stream)
         e2e_dt += time.perf_counter() - t0
         e2e_moves += c["moves"]
         pin_p.copy_(out_p)
         pin_o.copy_(out_o)
     e2e_ms_job, e2e_moves_job = job_totals(torch, e2e_dt * 1e3, e2e_moves, "cuda")
+    state_bytes = int(ws * N * 4 * 8)
     e2e = {"value": e2e_moves_job / (e2e_ms_job * 1e-3), "unit": UNIT,
-           "h2d_bytes_per_step": int(ws * N * 4 * 8), "d2h_bytes_per_step": int(ws * N * 4 * 8),
-           "api": "hpmc_run_host (pinned host buffers, H2D + 200 sweeps + D2H + counters)"}
+           "h2d_bytes_per_step": state_bytes, "d2h_bytes_per_step": state_bytes,
+           "api": f"hpmc_run_host (pinned host buffers, H2D + {SWEEPS_LARGE} sweeps + D2H + counters)"}
+    del pin_p, pin_o, out_p, out_o
     b.reset_counters()
     if rank != 0:
         b.close()
-        if ws > 1:
+        if multi:
             dist.destroy_process_group()
         return
 
     # ---- roofline of the dominant kernel (the set kernel), CUDA events live
-    nsets = 4
-    b.reset_counters()
-    ms_rebuild, ms_sets = b.profile_sweeps(SWEEPS_PER_STEP, stream=stream.cuda_stream)
-    cp = b.counters()
-    set_ms = ms_sets / nsets
-    flop_per_sweep = (FLOP_MOVE * cp["moves"] + FLOP_CULL * cp["cull_pairs"] +
-                      FLOP_SAT * cp["overlap_checks"]) / SWEEPS_PER_STEP
-    achieved = (flop_per_sweep / nsets) / (set_ms * 1e-3) / 1e12
-    roofline = {"bound": "alu", "kernel": "k_set2d (checkerboard set)", "achieved": achieved,
-                "peak": PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / PEAK_TFLOPS,
-                "traffic": SET2D_FLUID_DRAM_BYTES, "ncu_utilisation": SET2D_FLUID_NCU,
-                "set_kernel_ms": set_ms, "rebuild_ms_per_sweep": ms_rebuild,
-                "peak_source": "152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz (nominal unit counts)",
-                "flops_per_move_model": f"{FLOP_MOVE} + {FLOP_CULL}*culls + {FLOP_SAT}*SAT checks"}
+    roofline = set_kernel_roofline(b, stream, 8, p32, p64)
+    roofline["kernel"] = "k_set2d (checkerboard set), 2^24-pentagon system"
+    roofline["peak_source"] = "FP32 fused multiply-add rate measured in this run (hpmc_measure_fma_peak)"
+    roofline["traffic_note"] = ("DRAM bytes of this kernel come from a separate ncu capture of a 2^22-particle "
+                                "instance (kept with the profiles), not from this run")
+    launches = args.steps * SWEEPS_LARGE * b.launches_per_sweep()
+    b.close()
 
-    forms = {"fp32_filtered": {"value": value, "fp64_rechecks": cnt["fp64_rechecks"],
-                               "overlap_checks": cnt["overlap_checks"],
-                               "acceptance": cnt["accept"] / max(1, moves)}}
-    # ---- the other forms and the CPU baseline: one GPU only (with N > 1
-    # the job reports its headline; the forms are one-GPU measurements)
-    multi = ws > 1
-    args.no_batched = args.no_batched or multi
-    args.no_cubes = args.no_cubes or multi
-    args.no_large = args.no_large or multi
-    args.no_cpu = args.no_cpu or multi
-    # ---- plain FP64 form on the same workload (same trajectory)
-    if not multi:
-        b64 = hpmc.from_system(s)
-        forms["fp64"] = measure_form(b64, torch, stream, flush, hpmc.HPMC_FP64, MELT, SWEEPS_PER_STEP,
-                                     max(2, args.steps // 2))
-        b64.close()
-
-    # ---- batched form: 512 independent replicas, one graph-captured launch sequence
-    if not args.no_batched:
-        reps = inputs.replica_systems(512)
-        bb = hpmc.from_systems(reps)
-        f = measure_form(bb, torch, stream, flush, hpmc.HPMC_FP32_FILTERED, 20, SWEEPS_PER_STEP, 2, n_tune=8)
-        f.update(replicas=512, particles=int(sum(r.N for r in reps)))
-        forms["batched_512_replicas_fp32_filtered"] = f
-        bb.close()
-
-    # ---- 3D: 32768 cubes at volume fraction 0.5, both precision forms
-    if not args.no_cubes:
-        sc = inputs.cubes32768(42)
-        for prec, key in ((hpmc.HPMC_FP32_FILTERED, "cubes32768_fp32_filtered"),
-                          (hpmc.HPMC_FP64, "cubes32768_fp64")):
-            bc = hpmc.from_system(sc)
-            f = measure_form(bc, torch, stream, flush, prec, MELT, 100, 2)
-            f.update(workload=sc.name, N=sc.N, d=sc.d, a=sc.a, nselect=sc.nselect)
-            forms[key] = f
-            bc.close()
-
-    # ---- 3D: 32000 dodecahedra at volume fraction 0.5 (the paper's 3D shape), both forms
-    if not args.no_cubes:
-        sd = inputs.dodecahedra32000(42)
-        for prec, key in ((hpmc.HPMC_FP32_FILTERED, "dodecahedra32000_fp32_filtered"),
-                          (hpmc.HPMC_FP64, "dodecahedra32000_fp64")):
-            bd = hpmc.from_system(sd)
-            f = measure_form(bd, torch, stream, flush, prec, MELT, 50, 2)
-            f.update(workload=sd.name, N=sd.N, d=sd.d, a=sd.a, nselect=sd.nselect)
-            forms[key] = f
-            bd.close()
-
-    # ---- large 2D: 2^24 pentagons on a 2048^2 cell list (state > L2)
-    if not args.no_large:
-        sl = inputs.large2d(42)
-        bl = hpmc.from_system(sl)
-        f = measure_form(bl, torch, stream, flush, hpmc.HPMC_FP32_FILTERED, 20, 5, 2, n_tune=2)
-        f.update(workload=sl.name, N=sl.N, cells=2048 * 2048)
-        forms["large2d_2p24_fp32_filtered"] = f
-        bl.close()
-
-    # ---- CPU baseline: the oracle on host cores, bounded sample
+    forms = {"large2d_2p24_fp32_filtered": {"value": value, "fp64_rechecks": cnt["fp64_rechecks"],
+                                            "overlap_checks": cnt["overlap_checks"],
+                                            "acceptance": cnt["accept"] / max(1, moves),
+                                            "lanes_per_cell": lanes, "warps_per_block": warps}}
     cpu = None
-    if not args.no_cpu:
-        rate, cmoves, cdt, _ = oracle_rate(s, MELT, args.cpu_sweeps)
-        cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle", "host": host_cpu(),
-               "sample": f"{args.cpu_sweeps} sweeps ({cmoves} trial moves, {cdt:.1f} s) of the same "
-                         f"4096-pentagon fluid after a {MELT}-sweep melt, plain C oracle, 1 thread"}
+    if not multi:
+        # ---- the plain FP64 form of the headline, from the same melted state:
+        # its cumulative decisions must equal the FP32-filtered form's
+        b64 = hpmc.from_system(s)
+        b64.set_state(*snap)
+        b64.set_precision(hpmc.HPMC_FP64)
+        l64, w64 = b64.autotune(2)
+        k64 = min(args.steps, 5)
+        ms64, c64, cum64 = time_steps(b64, torch, stream, k64, args.warmup, flush, SWEEPS_LARGE)
+        b64.close()
+        n_cmp = args.warmup + k64
+        if cum64[n_cmp - 1] != cum32[n_cmp - 1]:
+            raise SystemExit(f"2^24 system: FP32-filtered and FP64 decisions differ after {n_cmp} steps: "
+                             f"{cum32[n_cmp - 1]} vs {cum64[n_cmp - 1]}")
+        forms["large2d_2p24_fp64"] = {"value": c64["moves"] / (ms64 * 1e-3), "steps": k64,
+                                      "lanes_per_cell": l64, "warps_per_block": w64,
+                                      "decisions_equal_fp32_filtered": True,
+                                      "compared_sweeps": n_cmp * SWEEPS_LARGE}
 
-    launches = args.steps * SWEEPS_PER_STEP * b.launches_per_sweep()
+        # ---- the other configurations (one GPU)
+        def pair(key, make, melt, sweeps, steps, n_tune, batched=False):
+            out = {}
+            for prec, tag in ((hpmc.HPMC_FP32_FILTERED, "fp32_filtered"), (hpmc.HPMC_FP64, "fp64")):
+                if args.quick and prec == hpmc.HPMC_FP64:
+                    continue
+                bb = make()
+                out[tag] = measure_form(bb, torch, stream, flush, prec, melt, sweeps, steps, (p32, p64), n_tune)
+                bb.close()
+            if "fp64" in out:
+                out["fp32_filtered"]["decisions_equal_fp64"] = same_decisions(out["fp32_filtered"], out["fp64"], key)
+            for tag, f in out.items():
+                forms[f"{key}_{tag}"] = f
+
+        s1 = load_rsa1024()
+        pair("rsa1024", lambda: hpmc.from_system(s1), 0, 1000, 3, 8)
+        sf = inputs.fluid4096(42)
+        pair("fluid4096", lambda: hpmc.from_system(sf), MELT, 200, 5, 8)
+        if not args.no_cubes:
+            sc = inputs.cubes32768(42)
+            pair("cubes32768", lambda: hpmc.from_system(sc), MELT, 100, 5, 4)
+            sd = inputs.dodecahedra32000(42)
+            pair("dodecahedra32000", lambda: hpmc.from_system(sd), MELT, 50, 5, 4)
+        if not args.no_batched:
+            reps = inputs.replica_systems(512)
+            pair("batched512", lambda: hpmc.from_systems(reps), MELT, 200, 5, 8)
+            forms["batched512_fp32_filtered"].update(replicas=512, particles=int(sum(r.N for r in reps)))
+
+        # ---- CPU baseline: the oracle on the host cores, bounded sample of
+        # the headline workload (from the GPU's melted state: a timing sample)
+        if not args.no_cpu:
+            threads = os.cpu_count() or 1
+            rate, cmoves, cdt = oracle_rate(s, snap[0], snap[1], snap[2], 2, threads)
+            rate1, cmoves1, cdt1 = oracle_rate(s, snap[0], snap[1], snap[2], 1, 1)
+            cpu = {"value": rate, "unit": UNIT, "cores": threads, "kind": "oracle", "host": host_cpu(),
+                   "sample": f"2 sweeps ({cmoves} trial moves, {cdt:.1f} s) of the 2^24-pentagon system from "
+                             f"the state after the {MELT_LARGE}-sweep melt, plain C oracle with the cells of "
+                             f"each set shared over {threads} threads",
+                   "single_core": {"value": rate1, "cores": 1,
+                                   "sample": f"1 sweep ({cmoves1} trial moves, {cdt1:.1f} s), 1 thread"}}
+
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": ms_job / args.steps, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64 (FP32 certified filter, FP64 state)",
            "data": "synthetic",
-           "config": {"workload": WORKLOAD, "N": N, "phi": 0.60, "d": s.d, "a": s.a,
-                      "nselect": s.nselect, "sweeps_per_step": SWEEPS_PER_STEP, "melt_sweeps": MELT,
+           "config": {"workload": WORKLOAD, "N": N, "cells": 2048 * 2048, "phi": 0.60, "d": s.d, "a": s.a,
+                      "nselect": s.nselect, "sweeps_per_step": SWEEPS_LARGE, "melt_sweeps": MELT_LARGE,
                       "precision": "FP32_FILTERED", "lanes_per_cell": lanes, "warps_per_block": warps,
-                      "l2": "flushed between timed steps (256 MiB write); the 4096-particle state "
-                            "is L2-resident within a step",
-                      "parallelism": f"replicas only: {ws} independent replica(s), one per GPU"},
+                      "l2": "inputs larger than L2 (2 GB of state against 129 MB) and a 256 MiB write "
+                            "between timed steps",
+                      "parallelism": f"replicas only: {ws} independent system(s), one per GPU"},
            "roofline": roofline, "cpu_baseline": cpu, "clocks": clocks, "e2e": e2e,
-           "gpu_launches": launches, "forms": forms,
-           "counters": cnt}
+           "gpu_launches": launches, "peaks": peaks, "forms": forms, "counters": cnt}
     print(json.dumps(out))
-    b.close()
-    if ws > 1:
+    if multi:
         dist.destroy_process_group()
 
 
@@ -634,10 +711,9 @@ def main():
     ap.add_argument("--warps", type=int, default=4)
     ap.add_argument("--trace", action="store_true", help="with --profile-sweeps: per-warp phase stamps")
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=40)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--cpu-sweeps", type=int, default=5000)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-cubes", action="store_true")
@@ -648,7 +724,7 @@ def main():
     ap.add_argument("--efficiency", type=int, default=0,
                     help="diffusion per GPU second against move size (sweeps per point)")
     ap.add_argument("--sample-every", type=int, default=50)
-    ap.add_argument("--no-large", action="store_true")
+    ap.add_argument("--quick", action="store_true", help="skip the plain FP64 forms of the smaller systems")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

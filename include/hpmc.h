@@ -100,7 +100,12 @@ int hpmc_batch_create(int dim, const double* verts, uint32_t nv, double w_min,
 /*
  * hpmc_create -- single-system form of hpmc_batch_create (R = 1) taking the
  * box, shape, configuration and Philox seed; moves default to d = a = 0.1,
- * nselect = 4 until hpmc_set_moves is called.
+ * nselect = 4 until hpmc_set_moves is called.  The system is the one Sec. 2.1
+ * simulates: N hard convex shapes of one type in a periodic box, each with a
+ * position and an orientation, no two overlapping; the seed keys the
+ * per-move random streams of Sec. 2.5 (hash-style counters instead of a
+ * stored generator state).  Same arguments and errors as
+ * hpmc_batch_create (pos[N*dim], orient[N*(2|4)] host arrays in tag order).
  */
 int hpmc_create(const double* box, int dim, uint32_t N, const double* verts, uint32_t nv,
                 const double* pos, const double* orient, uint64_t seed, double w_min,
@@ -127,8 +132,15 @@ int hpmc_set_moves(hpmc_t h, int32_t r, double d, double a, uint32_t nselect);
  */
 int hpmc_set_cell_width_min(hpmc_t h, double w_min);
 
-/* hpmc_set_precision -- HPMC_FP64 or HPMC_FP32_FILTERED (default).  Both give
- * identical trajectories; the filtered form is faster. */
+/*
+ * hpmc_set_precision -- HPMC_FP64 or HPMC_FP32_FILTERED (default).  Sec. 2.3
+ * runs the overlap tests in single precision on double-precision separations
+ * in the frame of one particle (Eq. 2); here the single-precision verdict is
+ * used only when a forward error bound certifies that it equals the FP64
+ * test's, and the test is re-run in FP64 otherwise, so both modes give
+ * identical trajectories; the filtered form is faster.  INVALID_ARG for any
+ * other mode.  Takes effect at the next sweep.
+ */
 int hpmc_set_precision(hpmc_t h, int mode);
 
 /*
@@ -162,7 +174,13 @@ int hpmc_sync(hpmc_t h);
 
 /*
  * hpmc_counters -- synchronise, then copy the counters of replica r (r = -1:
- * the sum over replicas) into *out.  hpmc_reset_counters zeroes them.
+ * the sum over replicas) into *out.  hpmc_reset_counters zeroes them.  The
+ * accept / reject counts are the outcomes of the Metropolis steps of Sec.
+ * 2.1 (accepted when the trial overlaps nothing) and of the checkerboard
+ * rule of Sec. 2.5.2 (rejected when the trial leaves its active cell); their
+ * ratio is the acceptance the paper tunes move sizes to.  INVALID_ARG for a
+ * null handle or output or r out of range; a recorded device error is
+ * returned.
  */
 int hpmc_counters(hpmc_t h, int32_t r, hpmc_counters_t* out);
 int hpmc_reset_counters(hpmc_t h);
@@ -170,16 +188,25 @@ int hpmc_reset_counters(hpmc_t h);
 /*
  * hpmc_check_overlaps -- synchronise, rebuild the cell list and count the
  * overlapping pairs of replica r (r = -1: all) with the FP64 contract
- * predicate (circumsphere cull, then SAT / GJK).  *n_pairs receives the count.
+ * predicate (circumsphere cull, then SAT / GJK; Sec. 2.1 defines a valid
+ * configuration as one in which no pair overlaps, and the system tests of
+ * Sec. 4 check runs for overlaps).  *n_pairs receives the count.  The grid
+ * shift of the running sweep is kept, so the trajectory is unaffected.
+ * INVALID_ARG for a null handle or output or r out of range.
  */
 int hpmc_check_overlaps(hpmc_t h, int32_t r, uint64_t* n_pairs);
 
 /*
  * hpmc_get_state / hpmc_set_state -- copy replica r's configuration in tag
  * order to / from caller-owned host arrays pos[N*dim], orient[N*(2|4)], and
- * its sweep counter.  Both synchronise.  set_state checks that positions are
- * finite and inside [0, L) and orientations finite (INVALID_ARG otherwise);
- * it does not check overlaps (see hpmc_check_overlaps).
+ * its sweep counter.  The state of Sec. 2.1 is exactly this: every
+ * particle's position and orientation; with the sweep counter (the step
+ * index that keys the random streams of Sec. 2.5) it fixes the rest of the
+ * trajectory, so a state read and written back continues bit for bit
+ * (checkpoint and restart).  Both synchronise.  set_state checks that
+ * positions are finite and inside [0, L) and orientations finite
+ * (INVALID_ARG otherwise); it does not check overlaps (see
+ * hpmc_check_overlaps).
  */
 int hpmc_get_state(hpmc_t h, int32_t r, double* pos, double* orient, uint64_t* sweep);
 int hpmc_set_state(hpmc_t h, int32_t r, const double* pos, const double* orient, uint64_t sweep);
@@ -223,8 +250,9 @@ int hpmc_profile_sweeps(hpmc_t h, uint32_t n, void* stream, double* ms_rebuild, 
 int hpmc_trace_read(hpmc_t h, uint64_t* out, uint32_t max_warps, uint32_t* n_points);
 
 /*
- * hpmc_box_move -- one isotropic volume move of replica r (the NPT ensemble,
- * which the paper runs following Frenkel & Smit): V' = V + dV_max (2u - 1)
+ * hpmc_box_move -- one isotropic volume move of replica r (the NPT ensemble
+ * that Sec. 1 lists among the paper's HPMC capabilities and whose
+ * acceptance rule it takes from its NPT references): V' = V + dV_max (2u - 1)
  * with u from the replica's volume-move stream (Philox key = the replica's
  * seed, counter (lo32(m), hi32(m), 0, 4 << 24) for its m-th attempt; u from
  * words 0-1, u' from words 2-3); every box length and position scaled by
@@ -297,6 +325,35 @@ int hpmc_msd_read(hpmc_t h, int32_t r, double* msd);
  */
 int hpmc_sdf(hpmc_t h, int32_t r, double x_max, uint32_t nbins, uint64_t* hist);
 
+/* Result of hpmc_pressure. */
+typedef struct {
+    double beta_P_over_rho;       /* 1 + h(0) / (dim N) */
+    double beta_P_over_rho_err;   /* standard error from the fit */
+    double P_star;                /* beta P sigma^2 (2D) or beta P v0, v0 = pi sigma^3 / 6 (3D) */
+    double P_star_err;
+    double h0;                    /* extrapolated pairs per unit x per configuration at x = 0 */
+    double h0_err;
+} hpmc_pressure_t;
+
+/*
+ * hpmc_pressure -- pressure from a scale-distribution histogram (Sec. 4: the
+ * volume-perturbation estimator).  hist[nbins] holds the counts hpmc_sdf
+ * accumulated over n_samples configurations of N particles in a box of
+ * volume `volume` (area in 2D), bins of width x_max / nbins from x = 0.
+ * h(x) = count / (n_samples * bin width) is extrapolated to x = 0 by a
+ * weighted least-squares fit of log h on the bin centres with a polynomial
+ * of degree `deg` (0..8; weights sqrt(count), the inverse standard error of
+ * a Poisson log count; empty bins left out), and beta P / rho = 1 + h(0) /
+ * (dim N).  P* uses `sigma`, the diameter of the disks / spheres the paper
+ * reports (any length scale for shaped particles).  Host computation only
+ * (no device work, no allocation on the device).  Errors: INVALID_ARG (null
+ * pointers, nbins = 0, n_samples = 0, N = 0, dim not 2/3, deg outside 0..8,
+ * non-positive or non-finite x_max, volume or sigma, at most deg + 1
+ * populated bins).
+ */
+int hpmc_pressure(const uint64_t* hist, uint32_t nbins, uint64_t n_samples, double x_max, uint64_t N,
+                  double volume, int dim, int deg, double sigma, hpmc_pressure_t* out);
+
 /*
  * hpmc_pair_test -- evaluate the overlap test on n independent pairs on the
  * GPU, for validation.  A sits at the origin with orientation qA, B at Delta
@@ -336,6 +393,20 @@ int hpmc_launches_per_sweep(hpmc_t h, uint32_t* n);
 int hpmc_filter_margins(hpmc_t h, int32_t r, double* e_in, double* e_cull, double* e_overlap);
 
 const char* hpmc_strerror(int code);
+
+/*
+ * hpmc_measure_fma_peak -- measured peak of the pipe the set kernels' ALU
+ * work runs on (the roofline denominator of their arithmetic; the paper
+ * states no machine peak).  Times `iters` iterations of 8 independent fused
+ * multiply-adds per thread in 2048 resident threads on every SM, FP64 when
+ * fp64 != 0 else FP32, with CUDA events on a private stream, `reps` times
+ * after one short warm-up launch; *flops_per_s receives the best rate (2
+ * flops per multiply-add) and *ms (may be NULL) that launch's duration.  The
+ * rate is at the clock the GPU ran, which the caller samples alongside.
+ * Synchronous; allocates and frees its own device buffer.  Errors:
+ * INVALID_ARG (null output, iters = 0, reps outside 1..1000), OOM, CUDA.
+ */
+int hpmc_measure_fma_peak(int fp64, uint32_t iters, int reps, double* flops_per_s, double* ms);
 
 /*
  * hpmc_count_overlaps_noalloc -- count the overlapping pairs of one 2D

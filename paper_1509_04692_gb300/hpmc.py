@@ -33,7 +33,7 @@ EXPORTS = [
     "hpmc_filter_margins", "hpmc_strerror", "hpmc_profile_sweeps", "hpmc_count_overlaps_noalloc",
     "hpmc_trace_read", "hpmc_pair_test", "hpmc_sdf", "hpmc_box_move", "hpmc_get_box",
     "hpmc_tune_moves", "hpmc_msd_reset", "hpmc_msd_update", "hpmc_msd_read", "hpmc_debug_fail_alloc",
-    "hpmc_pair_test_warp3d", "hpmc_set_cell_width_min",
+    "hpmc_pair_test_warp3d", "hpmc_set_cell_width_min", "hpmc_measure_fma_peak", "hpmc_pressure",
 ]
 
 
@@ -50,6 +50,14 @@ class Counters(ctypes.Structure):
 
     def as_dict(self):
         return {n: int(getattr(self, n)) for n, _ in self._fields_}
+
+
+class PressureOut(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_double) for n in (
+        "beta_P_over_rho", "beta_P_over_rho_err", "P_star", "P_star_err", "h0", "h0_err")]
+
+    def as_dict(self):
+        return {n: float(getattr(self, n)) for n, _ in self._fields_}
 
 
 class ReplicaDesc(ctypes.Structure):
@@ -107,6 +115,9 @@ def _load():
         "hpmc_msd_update": [ctypes.c_void_p],
         "hpmc_msd_read": [ctypes.c_void_p, ctypes.c_int32, dp],
         "hpmc_debug_fail_alloc": [ctypes.c_int32],
+        "hpmc_measure_fma_peak": [ctypes.c_int, u32, ctypes.c_int, dp, dp],
+        "hpmc_pressure": [ctypes.POINTER(u64), u32, u64, ctypes.c_double, u64, ctypes.c_double, ctypes.c_int,
+                          ctypes.c_int, ctypes.c_double, ctypes.POINTER(PressureOut)],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -411,6 +422,26 @@ def from_systems(systems):
     reps = [dict(box=s.L, pos=s.pos, orient=s.orient, seed=s.seed, d=s.d, a=s.a, nselect=s.nselect)
             for s in systems]
     return Batch(s0.dim, s0.verts, reps, w_min=s0.w_min)
+
+
+def pressure(hist, n_samples, x_max, N, volume, dim, sigma=1.0, deg=3):
+    """hpmc_pressure on a host histogram (counts of hpmc_sdf): a dict with
+    beta_P_over_rho, P_star, h0 and their standard errors."""
+    h = np.ascontiguousarray(np.rint(np.asarray(hist, dtype=np.float64)).astype(np.uint64))
+    out = PressureOut()
+    _ck(_lib.hpmc_pressure(h.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)), h.size, int(n_samples),
+                           float(x_max), int(N), float(volume), int(dim), int(deg), float(sigma),
+                           ctypes.byref(out)), "hpmc_pressure")
+    return out.as_dict()
+
+
+def measure_fma_peak(fp64, iters, reps=3):
+    """Measured fused multiply-add rate of the FP64 (fp64=True) or FP32 pipe
+    on the current device: (flop/s, ms of the best launch)."""
+    f, ms = ctypes.c_double(), ctypes.c_double()
+    _ck(_lib.hpmc_measure_fma_peak(1 if fp64 else 0, int(iters), int(reps), ctypes.byref(f), ctypes.byref(ms)),
+        "hpmc_measure_fma_peak")
+    return f.value, ms.value
 
 
 def debug_fail_alloc(n):

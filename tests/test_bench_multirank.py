@@ -79,7 +79,9 @@ def test_reference_arm_line_on_one_process(monkeypatch, capsys):
 
     class A:
         steps, warmup = 1, 3
-    bench.run_reference(A())
+    from paper_1509_04692_gb300 import inputs
+    small = inputs.large2d(42, N=1 << 14)            # the headline recipe on a smaller box
+    bench.run_reference(A(), system=small, melt=3)
     lines = capsys.readouterr().out.strip().splitlines()
     assert len(lines) == 1
     d = json.loads(lines[0])
@@ -90,7 +92,9 @@ def test_reference_arm_line_on_one_process(monkeypatch, capsys):
     assert d["cpu_baseline"]["host"]["nproc"] >= 1 and d["cpu_baseline"]["host"]["model"]
     assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0,
                         "d2h_bytes_per_step": 0}
-    assert d["config"]["workload"].startswith("pentagon fluid N=4096")
+    assert d["config"]["workload"] == small.name and d["config"]["melt_sweeps"] == 3
+    assert d["cpu_baseline"]["cores"] == os.cpu_count()
+    assert bench.WORKLOAD.startswith("2^24 regular pentagons")
 
 
 def test_clock_sampler_keeps_samples_of_the_timed_region(tmp_path, monkeypatch):
