@@ -14,8 +14,9 @@ the same melted state (its accept / reject counts must equal the filtered
 form's, else the run stops), and every other configuration in both forms
 with the same check: 1024 pentagons from their random-sequential-addition
 start, the 4096-pentagon fluid, 32768 cubes and 32000 dodecahedra at volume
-fraction 0.50, and the batch of 512 independent replicas (N ~ U{256..8192},
-phi ~ U[0.40, 0.70]).  `roofline`: the set kernel's algorithmic flops over
+fraction 0.50, the batch of 512 independent pentagon replicas (N ~
+U{256..8192}, phi ~ U[0.40, 0.70]) and a batch of 32 cube replicas (N ~
+U{2048..16384}, phi ~ U[0.40, 0.55]).  `roofline`: the set kernel's algorithmic flops over
 its CUDA-event duration against the FP32 fused multiply-add rate measured in
 the same run.  `e2e`: the same metric through hpmc_run_host with host
 buffers (H2D + sweeps + D2H inside the timed region).  `cpu_baseline`: the C
@@ -472,6 +473,11 @@ def run_ours(args):
             reps = inputs.replica_systems(512)
             pair("batched512", lambda: hpmc.from_systems(reps), MELT, 200, 5, 8)
             forms["batched512_fp32_filtered"].update(replicas=512, particles=int(sum(r.N for r in reps)))
+        if not args.no_batched and not args.no_cubes:
+            creps = inputs.cube_replica_systems()
+            pair("batched_cubes32", lambda: hpmc.from_systems(creps), MELT, 100, 5, 4)
+            forms["batched_cubes32_fp32_filtered"].update(replicas=len(creps),
+                                                          particles=int(sum(r.N for r in creps)))
 
         # ---- CPU baseline: the oracle on the host cores, bounded sample of
         # the headline workload (from the GPU's melted state: a timing sample)

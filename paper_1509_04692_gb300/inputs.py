@@ -254,6 +254,23 @@ def cubes32768(seed: int = 42) -> System:
                        d=CUBES32768_D, a=CUBES32768_A, nselect=4)
 
 
+def cube_replica_params(n_replicas: int = 32, gen_seed: int = 2025, n_lo: int = 2048, n_hi: int = 16384,
+                        phi_lo: float = 0.40, phi_hi: float = 0.55):
+    """(N_r, phi_r, seed_r = 1000 + r) for a batch of independent cube
+    replicas of uneven size and density (all N drawn before all densities)."""
+    rng = np.random.default_rng(gen_seed)
+    Ns = rng.integers(n_lo, n_hi + 1, size=n_replicas)
+    phis = rng.uniform(phi_lo, phi_hi, size=n_replicas)
+    return [(int(Ns[r]), float(phis[r]), 1000 + r) for r in range(n_replicas)]
+
+
+def cube_replica_systems(n_replicas: int = 32, gen_seed: int = 2025, **kw):
+    """Independent replicas of unit cubes on their simple cubic lattices, with
+    the 32768-cube system's move sizes (acceptance then varies with density)."""
+    return [cube_system(N, phi, seed, name=f"cube replica{r}", d=CUBES32768_D, a=CUBES32768_A, nselect=4)
+            for r, (N, phi, seed) in enumerate(cube_replica_params(n_replicas, gen_seed, **kw))]
+
+
 # The large 2D system: 2^24 pentagons at area fraction 0.60 with cells no
 # narrower than 1.99, i.e. a 2048 x 2048 cell list (about 4 shapes per cell).
 # Same shape and density as the 4096-pentagon fluid, so the same move sizes

@@ -14,7 +14,9 @@ Systems and lengths (the benchmark's melts):
   * 2^24 pentagons at area fraction 0.60, 2048^2 cells: 200-sweep melt + 2;
   * 32768 cubes and 32000 dodecahedra at volume fraction 0.50: 1000 + 50;
   * 512 replicas (N ~ U{256..8192}, phi ~ U[0.40, 0.70]): 1000 + 20, sampled
-    replicas compared.
+    replicas compared;
+  * 32 cube replicas (N ~ U{2048..16384}, phi ~ U[0.40, 0.55]): 1000 + 20,
+    sampled replicas compared, both forms.
 """
 import os
 
@@ -42,8 +44,8 @@ def _oracle(s, n):
 
 def _gpu_as_timed(make, mode, melt, n, n_tune):
     """The benchmark's sequence: melt, autotune (state restored), then n
-    sweeps in the tuned configuration.  Returns per replica (pos, orient,
-    counters) for the replicas asked, and the tuned configuration."""
+    sweeps in the tuned configuration.  Returns the batch and the tuned
+    (lanes per cell, warps per block)."""
     b = make()
     b.set_precision(mode)
     b.sweep(melt, graph=True)
@@ -119,3 +121,21 @@ def test_replica_batch_melted_state_sampled():
         assert _counters3(b.counters(r)) == rc, (r, cfg)
         _same(gp, gq, p, q, f"replica {r} config {cfg}")
     b.close()
+
+
+def test_cube_replica_batch_melted_state_sampled_both_forms():
+    systems = inputs.cube_replica_systems()
+    melt, n = 1000, 20
+    Ns = np.array([x.N for x in systems])
+    phis = np.array([x.phi for x in systems])
+    sample = sorted({0, 31, int(Ns.argmax()), int(phis.argmax())})
+    refs = {r: _oracle(systems[r], melt + n) for r in sample}
+    for mode in (F32, F64):
+        b, cfg = _gpu_as_timed(lambda: hpmc.from_systems(systems), mode, melt, n, 4)
+        for r in sample:
+            p, q, rc = refs[r]
+            gp, gq, sw = b.get_state(r)
+            assert sw == melt + n
+            assert _counters3(b.counters(r)) == rc, (r, mode, cfg)
+            _same(gp, gq, p, q, f"cube replica {r} mode {mode} config {cfg}")
+        b.close()

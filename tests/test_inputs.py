@@ -74,3 +74,19 @@ def test_cube_and_disk_starts():
     d -= s.L[0] * np.round(d / s.L[0])
     r = np.hypot(d[..., 0], d[..., 1]) + np.eye(s.N) * 10
     assert r.min() >= 1.0 and abs(s.N * np.pi / 4 / s.L[0] ** 2 - 0.65) < 1e-12
+
+
+def test_cube_replica_batch_recipe():
+    params = inputs.cube_replica_params()
+    Ns = np.array([p[0] for p in params])
+    phis = np.array([p[1] for p in params])
+    assert len(params) == 32 and Ns.min() >= 2048 and Ns.max() <= 16384
+    assert phis.min() >= 0.40 and phis.max() <= 0.55
+    assert [p[2] for p in params] == [1000 + r for r in range(32)]
+    assert params == inputs.cube_replica_params()            # seeded
+    systems = inputs.cube_replica_systems()
+    for s, (N, phi, _) in zip(systems, params):
+        assert s.N == N and abs(N / s.L[0] ** 3 - phi) < 1e-12 and s.notes["spacing"] >= 1.0
+        assert s.d == s.a == inputs.CUBES32768_D and s.nselect == 4
+        assert np.allclose(s.orient, [1.0, 0.0, 0.0, 0.0])   # aligned cubes, spacing >= edge
+        assert tuple(orc.OracleSystem(3, s.L, s.verts).geometry()["nc"]) >= (4, 4, 4)
