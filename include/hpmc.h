@@ -145,10 +145,15 @@ int hpmc_set_precision(hpmc_t h, int mode);
 
 /*
  * hpmc_set_group_size -- lanes per active cell in the set kernel (1, 2, 4, 8,
- * 16 or 32) and warps per block (1..16, at most the kernel's launch bound:
- * 8 warps for 8+ lanes per cell in 2D, 6 for fewer, 8 in 3D; INVALID_ARG
- * beyond it).  Does not change the trajectory.  hpmc_autotune picks them by
- * timing.
+ * 16 or 32; or 0: the 2D direct kernel of the FP32-filtered form, one lane
+ * per cell reading its neighbours without shared-memory staging and
+ * skipping the stencil layers a trial cannot reach -- INVALID_ARG in 3D or
+ * in the plain FP64 form, and a later switch to FP64 makes the next sweep
+ * return INVALID_ARG until another size is set) and warps per block (1..16,
+ * at most the kernel's launch bound: 8 warps for 8+ lanes per cell in 2D and
+ * for the direct kernel, 6 for fewer, 8 in 3D; INVALID_ARG beyond it).  The
+ * checkerboard schedule of Sec. 2.5.2 is the same for every choice, so the
+ * trajectory does not change.  hpmc_autotune picks them by timing.
  */
 int hpmc_set_group_size(hpmc_t h, int lanes_per_cell, int warps_per_block);
 
@@ -217,7 +222,14 @@ int hpmc_set_state(hpmc_t h, int32_t r, const double* pos, const double* orient,
  * replica order, tag order inside: pos[Ntot*dim], orient[Ntot*(2|4)], Ntot
  * the batch's particle count), run n sweeps, download the result into
  * pos_out/orient_out (same sizes, caller-owned) and the summed counters into
- * *out (may be NULL).  Synchronous.
+ * *out (may be NULL).  The state is what Sec. 2.1 evolves (positions and
+ * orientations); the sweeps are those of hpmc_sweep_graph.  Each array moves
+ * in one copy on `stream` (direct DMA when the caller's buffers are pinned)
+ * through a device staging area of Ntot*(dim + (2|4)) doubles that the first
+ * call allocates and the handle keeps; the layout change runs on the device.
+ * The sweep counter continues from the handle's.  Synchronous.  Errors:
+ * INVALID_ARG (null pointers), OOM (staging area), CUDA, and device errors
+ * of the sweeps.
  */
 int hpmc_run_host(hpmc_t h, const double* pos, const double* orient, uint32_t n,
                   double* pos_out, double* orient_out, hpmc_counters_t* out, void* stream);

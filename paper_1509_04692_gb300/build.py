@@ -20,7 +20,7 @@ LIB = os.path.join(BUILD, "libhpmc.so")
 # trace variant (-DHPMC_TRACE): per-warp clock64() phase stamps in the set kernels
 BUILD_TRACE = os.path.join(HERE, "_build_trace")
 LIB_TRACE = os.path.join(BUILD_TRACE, "libhpmc.so")
-UNITS = ["hpmc.cu", "set2d_f32.cu", "set2d_f64.cu", "set3d.cu", "set3d_f32.cu", "set3d_f64.cu",
+UNITS = ["hpmc.cu", "set2d_f32.cu", "set2d_direct.cu", "set2d_f64.cu", "set3d.cu", "set3d_f32.cu", "set3d_f64.cu",
          "set3d_f32_nv20.cu", "set3d_f64_nv20.cu", "selects.cu", "noalloc.cu", "pairtest.cu", "peaks.cu", "pressure.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-fmad=false", "-Xcompiler", "-fPIC,-ffp-contract=off",

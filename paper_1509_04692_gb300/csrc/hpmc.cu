@@ -26,13 +26,22 @@ int hpmc_check3d_launch(const hpmc::Dev& dv, const hpmc::Shape3& sh, int b, int3
 
 namespace {
 
-constexpr int kGroupSizes[6] = { 1, 2, 4, 8, 16, 32 };
+// lanes per cell of the set kernels; 0 is the 2D direct kernel (one lane per
+// cell, neighbours read through L1 without staging)
+constexpr int kNumGroups = 7;
+constexpr int kGroupSizes[kNumGroups] = { 1, 2, 4, 8, 16, 32, 0 };
 
 int gidx_of(int G)
 {
-    for (int i = 0; i < 6; ++i)
+    for (int i = 0; i < kNumGroups; ++i)
         if (kGroupSizes[i] == G) return i;
     return -1;
+}
+
+// cells of a strip of one work item
+int cells_per_item(int G)
+{
+    return G ? 32 / G : 32;
 }
 
 struct HostRep {
@@ -88,8 +97,8 @@ struct hpmc_batch {
     int precision = HPMC_FP32_FILTERED;
     int G = 4, wpb = 4;
     int num_sms = 0;
-    uint32_t* item_base_dev = nullptr;   // [6][R + 1]
-    std::vector<uint32_t> items_per_set; // [6] totals
+    uint32_t* item_base_dev = nullptr;   // [kNumGroups][R + 1]
+    std::vector<uint32_t> items_per_set; // [kNumGroups] totals
     std::vector<void*> allocs;
     cudaStream_t last_stream = nullptr;
     int pending_error = 0;
@@ -113,6 +122,10 @@ struct hpmc_batch {
     uint32_t sel_grid = 0;
     cudaStream_t side = nullptr;
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    // device copy of a host configuration for hpmc_run_host (positions then
+    // orientations, interleaved per particle as the caller holds them),
+    // allocated on the first call
+    double* stage = nullptr;
 };
 
 namespace {
@@ -258,6 +271,19 @@ int rep_geometry(const hpmc_batch* h, const HostRep& hr, Rep& rp)
         rp.ins32 = r2 > 0.0 ? f32_down(r2 * r2 - g.e_cull) : -1.0f;
     }
     rp.cull_skip = f32_up(h->rc2 + g.e_cull);
+    // Reach of a trial across the walls of its cell.  A particle of the
+    // lower neighbour layer on axis a lies below the cell's lower wall (up to
+    // a few FP64 ulps of L from the cell rule), so the contract's |Delta_a|
+    // exceeds rel'_exact minus those ulps and its own rounding; rel'_exact is
+    // within e_in / 2 of the FP32 trial coordinate.  When the FP32 trial
+    // coordinate exceeds 2R (1 + 4 u64) + e_in, every pair with that layer has
+    // |Delta_a| >= 2R (1 + 2 u64), so |Delta|^2 rounds above (2R)^2 and the
+    // contract culls it.  Likewise for the upper layer below w - reach.
+    for (int a = 0; a < 3; ++a) {
+        const double reach = h->Rc * 2.0 * (1.0 + 4.0 * kU64) + g.e_in;
+        rp.reach_lo[a] = f32_up(reach);
+        rp.reach_hi[a] = f32_down(rp.w[a] - reach);
+    }
     rp.sat_e = f32_up(g.e_sat);
     rp.e_dlt32 = f32_up(g.e_dlt);
     rp.e_ori32 = f32_up(g.e_ori);
@@ -300,10 +326,10 @@ int check_config(int dim, const HostRep& hr, const double* pos, const double* or
 // recomputed; items per set depend only on the cell grid
 void build_item_tables(hpmc_batch* h, std::vector<uint32_t>& tab)
 {
-    tab.assign(6 * (h->R + 1), 0);
-    h->items_per_set.assign(6, 0);
-    for (int gi = 0; gi < 6; ++gi) {
-        const int S = 32 / kGroupSizes[gi];
+    tab.assign(kNumGroups * (h->R + 1), 0);
+    h->items_per_set.assign(kNumGroups, 0);
+    for (int gi = 0; gi < kNumGroups; ++gi) {
+        const int S = cells_per_item(kGroupSizes[gi]);
         uint32_t acc = 0;
         for (uint32_t r = 0; r < h->R; ++r) {
             tab[gi * (h->R + 1) + r] = acc;
@@ -345,8 +371,10 @@ SetKernel pick_kernel(const hpmc_batch* h)
     const bool f32 = h->precision == HPMC_FP32_FILTERED;
     if (h->dim == 2) {
         const bool fixed = h->nv == 5;
+        if (h->G == 0) return f32 ? set2d_direct_kernel(fixed) : SetKernel{ nullptr, 0 };
         return f32 ? set2d_f32_kernel(h->G, fixed) : set2d_f64_kernel(h->G, fixed);
     }
+    if (h->G == 0) return SetKernel{ nullptr, 0 };
     return f32 ? set3d_f32_kernel(h->G, h->nv) : set3d_f64_kernel(h->G, h->nv);
 }
 
@@ -406,6 +434,12 @@ int enqueue_rebuild(hpmc_batch* h, cudaStream_t st, bool with_shift)
     return 0;
 }
 
+// the set kernels that read their first selects from the sweep's table
+bool uses_select_table(int G)
+{
+    return G >= 8 || G == 0;
+}
+
 // Select table for the latency-regime kernels: one record for each of the
 // first min(nselect, G) selects of every cell of every replica (the chunk in
 // which idle lanes would otherwise carry the FP64 steps), grown (never
@@ -413,11 +447,12 @@ int enqueue_rebuild(hpmc_batch* h, cudaStream_t st, bool with_shift)
 // configuration is rebuilt, outside any stream capture of this library.
 int prepare_selects(hpmc_batch* h)
 {
-    h->use_selects = h->G >= 8;
+    h->use_selects = uses_select_table(h->G);
     if (!h->use_selects) return 0;
     uint32_t stride = 1;
     for (const HostRep& r : h->hr) stride = std::max(stride, r.nselect);
-    stride = std::min<uint32_t>(stride, (uint32_t)h->G);
+    // the direct kernel takes up to 8 selects of a cell from the table
+    stride = std::min<uint32_t>(stride, (uint32_t)(h->G ? h->G : 8));
     const uint64_t need = (uint64_t)h->ctot * stride;
     const size_t rec = select_record_bytes(h->dim);
     if (need > h->msel_cap) {
@@ -525,6 +560,45 @@ __global__ void k_unsort(Dev dv, int cur)
         D.pz[o] = S.pz[i];
         D.q2[o] = S.q2[i];
         D.q3[o] = S.q3[i];
+    }
+}
+
+// interleaved tag-order state (stage: pos[ntot * dim], then orient[ntot * qd])
+// into buffer cur, with identity tags
+__global__ void k_from_interleaved(Dev dv, int cur, const double* __restrict__ stage)
+{
+    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= dv.ntot) return;
+    const Bufs& B = dv.buf[cur];
+    const size_t n = dv.ntot;
+    if (dv.dim == 2) {
+        const double2 p = reinterpret_cast<const double2*>(stage)[i];
+        const double2 q = reinterpret_cast<const double2*>(stage + 2 * n)[i];
+        B.px[i] = p.x; B.py[i] = p.y;
+        B.q0[i] = q.x; B.q1[i] = q.y;
+    } else {
+        B.px[i] = stage[3 * (size_t)i]; B.py[i] = stage[3 * (size_t)i + 1]; B.pz[i] = stage[3 * (size_t)i + 2];
+        const double* q = stage + 3 * n + 4 * (size_t)i;
+        B.q0[i] = q[0]; B.q1[i] = q[1]; B.q2[i] = q[2]; B.q3[i] = q[3];
+    }
+    B.tag[i] = i - dv.reps[dv.rep_of[i]].pbase;
+}
+
+// buffer cur (cell-sorted, with tags) into the interleaved tag-order layout
+__global__ void k_to_interleaved(Dev dv, int cur, double* __restrict__ stage)
+{
+    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= dv.ntot) return;
+    const Bufs& B = dv.buf[cur];
+    const size_t n = dv.ntot;
+    const size_t o = dv.reps[dv.rep_of[i]].pbase + B.tag[i];
+    if (dv.dim == 2) {
+        reinterpret_cast<double2*>(stage)[o] = make_double2(B.px[i], B.py[i]);
+        reinterpret_cast<double2*>(stage + 2 * n)[o] = make_double2(B.q0[i], B.q1[i]);
+    } else {
+        stage[3 * o] = B.px[i]; stage[3 * o + 1] = B.py[i]; stage[3 * o + 2] = B.pz[i];
+        double* q = stage + 3 * n + 4 * o;
+        q[0] = B.q0[i]; q[1] = B.q1[i]; q[2] = B.q2[i]; q[3] = B.q3[i];
     }
 }
 
@@ -668,7 +742,7 @@ int hpmc_batch_create(int dim, const double* verts, uint32_t nv, double w_min, u
         (rc = dalloc(h, &dv.slot, h->ntot)) || (rc = dalloc(h, &dv.tmp_tag, h->ntot)) ||
         (rc = dalloc(h, &dv.shift, 3 * (size_t)R)) || (rc = dalloc(h, &dv.sweep, R)) ||
         (rc = dalloc(h, &dv.counters, (size_t)R * kNumCounters)) || (rc = dalloc(h, &dv.error, 1)) ||
-        (rc = dalloc(h, &h->item_base_dev, 6 * ((size_t)R + 1))) || (rc = dalloc(h, &h->check_out, 1)))
+        (rc = dalloc(h, &h->item_base_dev, kNumGroups * ((size_t)R + 1))) || (rc = dalloc(h, &h->check_out, 1)))
         return fail(rc);
 #ifdef HPMC_TRACE
     dv.trace_warps = 65536;
@@ -1275,40 +1349,21 @@ int hpmc_run_host(hpmc_t h, const double* pos, const double* orient, uint32_t n,
     cudaStream_t st = (cudaStream_t)stream;
     const int dim = h->dim, qd = dim == 2 ? 2 : 4;
     const size_t N = h->ntot;
-    // upload (tag order) into the current buffer
-    Bufs& B = h->dv.buf[h->cur];
-    double* dst_p[3] = { B.px, B.py, B.pz };
-    double* dst_q[4] = { B.q0, B.q1, B.q2, B.q3 };
-    std::vector<double> col(N);
-    for (int a = 0; a < dim; ++a) {
-        for (size_t i = 0; i < N; ++i) col[i] = pos[i * dim + a];
-        CK(cudaMemcpyAsync(dst_p[a], col.data(), N * sizeof(double), cudaMemcpyHostToDevice, st));
-        CK(cudaStreamSynchronize(st));
-    }
-    for (int a = 0; a < qd; ++a) {
-        for (size_t i = 0; i < N; ++i) col[i] = orient[i * qd + a];
-        CK(cudaMemcpyAsync(dst_q[a], col.data(), N * sizeof(double), cudaMemcpyHostToDevice, st));
-        CK(cudaStreamSynchronize(st));
-    }
-    k_identity_tags<<<(h->ntot + 255) / 256, 256, 0, st>>>(h->dv, h->cur);
+    int rc = 0;
+    if (!h->stage && (rc = dalloc(h, &h->stage, N * (size_t)(dim + qd)))) return rc;
+    // one copy per array as the caller holds it (a direct DMA when the host
+    // buffers are pinned), then the layout change on the device
+    CK(cudaMemcpyAsync(h->stage, pos, N * dim * sizeof(double), cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(h->stage + N * dim, orient, N * qd * sizeof(double), cudaMemcpyHostToDevice, st));
+    k_from_interleaved<<<(h->ntot + 255) / 256, 256, 0, st>>>(h->dv, h->cur, h->stage);
     CK(cudaGetLastError());
-    int rc = hpmc_sweep_graph(h, n, stream);
+    rc = hpmc_sweep_graph(h, n, stream);
     if (rc) return rc;
-    k_unsort<<<(h->ntot + 255) / 256, 256, 0, st>>>(h->dv, h->cur);
+    k_to_interleaved<<<(h->ntot + 255) / 256, 256, 0, st>>>(h->dv, h->cur, h->stage);
     CK(cudaGetLastError());
-    const Bufs& D = h->dv.buf[h->cur ^ 1];
-    const double* src_p[3] = { D.px, D.py, D.pz };
-    const double* src_q[4] = { D.q0, D.q1, D.q2, D.q3 };
-    for (int a = 0; a < dim; ++a) {
-        CK(cudaMemcpyAsync(col.data(), src_p[a], N * sizeof(double), cudaMemcpyDeviceToHost, st));
-        CK(cudaStreamSynchronize(st));
-        for (size_t i = 0; i < N; ++i) pos_out[i * dim + a] = col[i];
-    }
-    for (int a = 0; a < qd; ++a) {
-        CK(cudaMemcpyAsync(col.data(), src_q[a], N * sizeof(double), cudaMemcpyDeviceToHost, st));
-        CK(cudaStreamSynchronize(st));
-        for (size_t i = 0; i < N; ++i) orient_out[i * qd + a] = col[i];
-    }
+    CK(cudaMemcpyAsync(pos_out, h->stage, N * dim * sizeof(double), cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(orient_out, h->stage + N * dim, N * qd * sizeof(double), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
     if (out) return hpmc_counters(h, -1, out);
     return read_error(h);
 }
@@ -1457,7 +1512,7 @@ int hpmc_autotune(hpmc_t h, uint32_t n_trial, int* best_lanes, int* best_warps)
     cudaError_t ce = ev.create();
     if (ce != cudaSuccess) return fail(ce);
     const int wpbs[4] = { 1, 2, 4, 8 };
-    for (int gi = 0; gi < 6; ++gi) {
+    for (int gi = 0; gi < kNumGroups; ++gi) {
         for (int wi = 0; wi < 4; ++wi) {
             if (hpmc_set_group_size(h, kGroupSizes[gi], wpbs[wi]) != 0) continue;
             int rc = hpmc_sweep(h, 1, nullptr);      // warm-up
@@ -1532,7 +1587,7 @@ int hpmc_geometry(hpmc_t h, int32_t r, int32_t* nc, double* w, double* R)
 int hpmc_launches_per_sweep(hpmc_t h, uint32_t* n)
 {
     if (!h || !n) return HPMC_ERR_INVALID_ARG;
-    *n = 5 + (h->ntiles > 1 ? 2 : 0) + (1u << h->dim) + (h->G >= 8 ? 1 : 0);
+    *n = 5 + (h->ntiles > 1 ? 2 : 0) + (1u << h->dim) + (uses_select_table(h->G) ? 1 : 0);
     return 0;
 }
 

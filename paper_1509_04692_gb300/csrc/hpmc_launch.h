@@ -12,7 +12,7 @@ struct SetKernel {
     size_t smem_per_warp;    // dynamic shared memory per warp
 };
 
-// lanes per cell G in {1, 2, 4, 8, 16, 32}.  2D fixed_nv: specialised on 5
+// lanes per cell G in {1, 2, 4, 8, 16, 32}; G = 0 selects the 2D direct kernel.  2D fixed_nv: specialised on 5
 // vertices (pentagons).  3D nv: specialised kernels for 8 (cubes) and 20
 // (dodecahedra) vertices, the generic one otherwise.
 SetKernel set2d_f32_kernel(int G, bool fixed_nv);
@@ -20,6 +20,8 @@ SetKernel set2d_f64_kernel(int G, bool fixed_nv);
 SetKernel set3d_f32_kernel(int G, int nv);
 SetKernel set3d_f64_kernel(int G, int nv);
 SetKernel set3d_f32_nv20(int G);
+// 2D direct kernel (one lane per cell, no staging), FP32-filtered form
+SetKernel set2d_direct_kernel(bool fixed_nv);
 SetKernel set3d_f64_nv20(int G);
 
 // select table of the latency-regime set kernels (selects.cu): bytes of one

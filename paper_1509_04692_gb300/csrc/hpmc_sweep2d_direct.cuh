@@ -1,0 +1,372 @@
+// hpmc_sweep2d_direct.cuh -- one checkerboard set of the 2D sweep (Sec. 2.5.2)
+// with one lane per active cell and no shared-memory staging (the
+// throughput regime of large systems, where every SM has thousands of cells).
+//
+// Work unit: one warp takes 32 consecutive active cells of one row of one
+// replica, one lane per cell.  A lane reads the begins and sizes of its 3 x 3
+// stencil cells once per set and then runs its cell's nselect trial moves in
+// sequence.  For every move it walks the stencil cell by cell, reading the
+// FP32 mirror of each neighbour straight from the cell-sorted buffer (the
+// stencils of the 32 cells of a warp overlap, so most reads hit L1), and
+// culls by circumsphere.  Survivors of all lanes go to a warp-wide pair queue
+// (ballot compaction) that the warp drains 32 pairs at a time, one
+// separating-axis test per lane, skipping pairs of moves already known to
+// overlap (the early exit of Sec. 2.1).
+//
+// Columns and rows of the stencil that a trial cannot reach are not read:
+// every particle of the lower neighbour column lies below the cell's lower
+// wall, so when the trial sits farther than the circumdiameter above that
+// wall (plus the certified FP32 error and the FP64 rounding of the cell
+// rule), the FP64 contract culls every pair with that column; likewise for
+// the upper column and the two neighbour rows.  With cells of twice the
+// circumdiameter (the 2^24-pentagon system) a trial needs 4 of the 9 cells on
+// average.  The decisions are the contract's either way.
+//
+// The picks and move deltas come from the sweep's select table (selects.cu);
+// FP64 arithmetic runs for accepted moves and for the rare FP32 verdicts the
+// certified margins cannot decide, exactly as in the other set kernels.
+#pragma once
+#include "hpmc_sweep2d.cuh"
+
+namespace hpmc {
+
+struct __align__(16) Direct2Warp {
+    static constexpr int QCAP = 64;
+    float2 qd[QCAP];                  // queued Delta32 (B relative to the trial)
+    float2 qz[QCAP];                  // queued B orientation (FP32 mirror)
+    uint32_t qe[QCAP];                // queued B slot in the sorted buffer
+    uint8_t qg[QCAP];                 // queued owner lane
+    float2 tz[32];                    // FP32 trial orientation of each lane's move
+    uint32_t ea[32];                  // sorted slot of each lane's moving particle
+    uint32_t sb[9][32];               // stencil cell q of each lane: sorted begin
+    uint32_t sn[9][32];               // and size
+    unsigned int ovmask;              // lanes whose move overlaps
+};
+
+// The select record of select k of a cell: from the sweep's table, or
+// computed here for selects beyond the table's stride.  The FP32 part (pick
+// word and FP32 deltas) is needed to propose, the FP64 part (contract
+// deltas) only once the move is decided, so they are read separately.
+struct Sel32 {
+    float fdx, fdy, fcd, fsd;
+    uint32_t r0;
+};
+
+__device__ __forceinline__ Sel32 direct_sel32(const MoveData* __restrict__ msel, uint32_t mstride,
+                                              const Rep& rp, uint64_t sweep, int sigma, uint32_t cglob,
+                                              uint32_t cell, uint32_t k)
+{
+    if (k < mstride) {
+        const MoveData* p = msel + (size_t)cglob * mstride + k;
+        const float4 v = *reinterpret_cast<const float4*>(&p->fdx);
+        return { v.x, v.y, v.z, v.w, p->r0 };
+    }
+    const MoveData m = precompute_select(rp, rp.seed, sweep, (uint32_t)sigma, cell, k);
+    return { m.fdx, m.fdy, m.fcd, m.fsd, m.r0 };
+}
+
+__device__ __forceinline__ MoveData direct_sel64(const MoveData* __restrict__ msel, uint32_t mstride,
+                                                 const Rep& rp, uint64_t sweep, int sigma, uint32_t cglob,
+                                                 uint32_t cell, uint32_t k)
+{
+    MoveData m{};
+    if (k < mstride) {
+        const MoveData* p = msel + (size_t)cglob * mstride + k;
+        const double2 a = *reinterpret_cast<const double2*>(&p->dx);
+        const double2 b = *reinterpret_cast<const double2*>(&p->cd);
+        m.dx = a.x; m.dy = a.y; m.cd = b.x; m.sd = b.y;
+        return m;
+    }
+    return precompute_select(rp, rp.seed, sweep, (uint32_t)sigma, cell, k);
+}
+
+// The rare FP64 paths stay out of line, so that their registers do not
+// weigh on the common path of the kernel.  Each takes the moving particle's
+// slot gA and recomputes the contract's trial from its select record.
+
+// in-cell test of the FP64 contract trial (FP32 verdict not certified)
+__device__ __noinline__ bool direct_in_cell64(const Rep& rp, const Bufs& B, const MoveData* __restrict__ msel,
+                                              uint32_t mstride, uint64_t sweep, int sigma, uint32_t cell,
+                                              uint32_t k, uint32_t gA, double shx, double shy, int ix, int iy)
+{
+    const MoveData m = direct_sel64(msel, mstride, rp, sweep, sigma, rp.cbase + cell, cell, k);
+    const Trial2 t2 = apply64(rp, B.px[gA], B.py[gA], B.q0[gA], B.q1[gA], m);
+    return cell_axis(t2.x, shx, rp.L[0], rp.inv_w[0], rp.nc[0]) == ix &&
+           cell_axis(t2.y, shy, rp.L[1], rp.inv_w[1], rp.nc[1]) == iy;
+}
+
+// circumsphere cull of the FP64 contract (FP32 verdict not certified)
+__device__ __noinline__ bool direct_keep64(const Rep& rp, double rc2, const Bufs& B,
+                                           const MoveData* __restrict__ msel, uint32_t mstride, uint64_t sweep,
+                                           int sigma, uint32_t cell, uint32_t k, uint32_t gA, uint32_t gB)
+{
+    const MoveData m = direct_sel64(msel, mstride, rp, sweep, sigma, rp.cbase + cell, cell, k);
+    const Trial2 t2 = apply64(rp, B.px[gA], B.py[gA], B.q0[gA], B.q1[gA], m);
+    const double Dx = min_image(B.px[gB] - t2.x, rp.L[0], rp.halfL[0]);
+    const double Dy = min_image(B.py[gB] - t2.y, rp.L[1], rp.halfL[1]);
+    return (Dx * Dx + Dy * Dy) <= rc2;
+}
+
+// separating-axis test of the FP64 contract on a queued pair (FP32 verdict
+// not certified)
+template <int NV>
+__device__ __noinline__ bool direct_overlap64(const Shape2& sh, const Rep& rp, const Bufs& B,
+                                              const MoveData* __restrict__ msel, uint32_t mstride,
+                                              uint64_t sweep, int sigma, uint32_t cell, uint32_t k,
+                                              uint32_t gA, uint32_t gB)
+{
+    const MoveData mo = direct_sel64(msel, mstride, rp, sweep, sigma, rp.cbase + cell, cell, k);
+    const Trial2 t2 = apply64(rp, B.px[gA], B.py[gA], B.q0[gA], B.q1[gA], mo);
+    const double Dx = min_image(B.px[gB] - t2.x, rp.L[0], rp.halfL[0]);
+    const double Dy = min_image(B.py[gB] - t2.y, rp.L[1], rp.halfL[1]);
+    return overlap2d64<NV>(sh, Dx, Dy, t2.c, t2.s, B.q0[gB], B.q1[gB]);
+}
+
+template <int NV>
+__global__ void __launch_bounds__(256, 2)
+k_set2d_direct(Dev dv, Shape2 sh, int nxt, int sigma, const uint32_t* __restrict__ item_base)
+{
+    pdl_wait();
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    Direct2Warp& ws = reinterpret_cast<Direct2Warp*>(smem_raw)[threadIdx.x >> 5];
+    const int lane = threadIdx.x & 31;
+    const unsigned FULL = 0xffffffffu;
+    const unsigned lt_mask = (1u << lane) - 1u;
+    const Bufs B = dv.buf[nxt];
+    const uint32_t* __restrict__ start = dv.start;
+    const uint32_t nitems = item_base[dv.R];
+    const uint32_t wpb = blockDim.x >> 5;
+    const MoveData* __restrict__ msel = static_cast<const MoveData*>(dv.msel);
+    const uint32_t mstride = dv.msel_stride;
+
+    for (uint32_t item = blockIdx.x * wpb + (threadIdx.x >> 5); item < nitems; item += gridDim.x * wpb) {
+        // ---- replica and strip of this work item
+        uint32_t lo = 0, hi = dv.R;
+        while (hi - lo > 1) {
+            const uint32_t mid = (lo + hi) >> 1;
+            if (__ldg(item_base + mid) <= item) lo = mid; else hi = mid;
+        }
+        const uint32_t r = lo;
+        const Rep& rp = dv.reps[r];
+        const int nc0 = rp.nc[0], nc1 = rp.nc[1];
+        const int nax = nc0 >> 1;
+        const int spr = (nax + 31) / 32;
+        const uint32_t local = item - __ldg(item_base + r);
+        const int row = (int)(local / spr);
+        const int strip = (int)(local - (uint32_t)row * spr);
+        const int iy = 2 * row + ((sigma >> 1) & 1);
+        const int jx = strip * 32 + lane;
+        const bool valid = jx < nax;
+        const int ix = (sigma & 1) + 2 * jx;
+        const uint64_t sweep = dv.sweep[r] - 1;           // the running sweep
+        const double shx = dv.shift[3 * r], shy = dv.shift[3 * r + 1];
+        const uint32_t nsel = rp.nselect;
+        const uint32_t cell_local = (uint32_t)ix + (uint32_t)nc0 * (uint32_t)iy;
+        const uint32_t cglob = rp.cbase + cell_local;
+        const float wx = rp.w32[0], wy = rp.w32[1];
+        // cell origins i * w of the relative coordinates (as in k_place)
+        const double iwx = (double)ix * rp.w[0];
+        const double iwy = (double)iy * rp.w[1];
+
+        // ---- stencil cells, q = 3 (oy + 1) + (ox + 1): sorted begin and size
+        uint32_t T = 0, cb = 0, n_c = 0;
+        __syncwarp();
+#pragma unroll
+        for (int q = 0; q < 9; ++q) {
+            uint32_t b = 0u, n = 0u;
+            if (valid) {
+                const int ox = q % 3 - 1, oy = q / 3 - 1;
+                int cx = ix + ox, cy = iy + oy;
+                cx = cx < 0 ? cx + nc0 : (cx >= nc0 ? cx - nc0 : cx);
+                cy = cy < 0 ? cy + nc1 : (cy >= nc1 ? cy - nc1 : cy);
+                const uint32_t c = rp.cbase + (uint32_t)cx + (uint32_t)nc0 * (uint32_t)cy;
+                b = start[c];
+                n = start[c + 1] - b;
+            }
+            ws.sb[q][lane] = b;
+            ws.sn[q][lane] = n;
+            T += n;
+            if (q == 4) { cb = b; n_c = n; }
+        }
+        const bool live_cell = valid && n_c > 0;
+        unsigned c_moves = 0, c_acc = 0, c_rov = 0, c_rbd = 0, c_cull = 0, c_chk = 0, c_rechk = 0;
+
+#pragma unroll 1
+        for (uint32_t k = 0; k < nsel; ++k) {
+            // ---- propose: FP32 trial from the select record
+            int status = 0;                                // 0 idle, 1 in the cell, 2 left it
+            uint32_t eA = 0;
+            float4 tr = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (live_cell) {
+                c_moves += 1;
+                const Sel32 m = direct_sel32(msel, mstride, rp, sweep, sigma, cglob, cell_local, k);
+                eA = cb + __umulhi(m.r0, n_c);
+                // a plain load: this lane may have written the slot earlier in the set
+                const float4 f = B.f4a[eA];
+                const float rx = __fadd_rn(f.x, m.fdx), ry = __fadd_rn(f.y, m.fdy);
+                const float cz = __fmaf_rn(f.z, m.fcd, -__fmul_rn(f.w, m.fsd));
+                const float sz = __fmaf_rn(f.z, m.fsd, __fmul_rn(f.w, m.fcd));
+                tr = make_float4(rx, ry, cz, sz);
+                const bool out = rx < rp.out_lo || ry < rp.out_lo || rx > rp.out_hi[0] || ry > rp.out_hi[1];
+                const bool in = rx > rp.in_lo && ry > rp.in_lo && rx < rp.in_hi[0] && ry < rp.in_hi[1];
+                if (out) {
+                    status = 2;
+                } else if (in) {
+                    status = 1;
+                } else {
+                    c_rechk += 1;
+                    status = direct_in_cell64(rp, B, msel, mstride, sweep, sigma, cell_local, k, eA, shx, shy, ix,
+                                              iy) ? 1 : 2;
+                }
+                ws.tz[lane] = make_float2(cz, sz);
+                ws.ea[lane] = eA;
+            }
+            if (lane == 0) ws.ovmask = 0u;
+            __syncwarp();
+
+            // ---- stencil columns and rows within reach of the trial
+            const bool need_l = !(tr.x > rp.reach_lo[0]), need_r = !(tr.x < rp.reach_hi[0]);
+            const bool need_b = !(tr.y > rp.reach_lo[1]), need_t = !(tr.y < rp.reach_hi[1]);
+            if (status == 1) c_cull += T - 1u;             // the stencil's candidates (self excluded)
+            bool ov = false;                               // this lane's move overlaps
+            int qn = 0;
+
+            // drain np queued pairs, one separating-axis test per lane
+            auto drain = [&](int np) {
+                if (lane < np) {
+                    const int g2 = ws.qg[lane];
+                    if (!((ws.ovmask >> g2) & 1u)) {
+                        c_chk += 1;
+                        const float2 d2 = ws.qd[lane], zb = ws.qz[lane], za = ws.tz[g2];
+                        const int v = sat32<NV>(sh, rp.sat_e, d2.x, d2.y, za.x, za.y, zb.x, zb.y);
+                        bool pov = v == 1;
+                        if (v == 2) {
+                            // not certified: the FP64 contract on the owner's trial
+                            c_rechk += 1;
+                            const int ixo = (sigma & 1) + 2 * (strip * 32 + g2);
+                            const uint32_t clo = (uint32_t)ixo + (uint32_t)nc0 * (uint32_t)iy;
+                            pov = direct_overlap64<NV>(sh, rp, B, msel, mstride, sweep, sigma, clo, k, ws.ea[g2],
+                                                       ws.qe[lane]);
+                        }
+                        if (pov) atomicOr(&ws.ovmask, 1u << g2);
+                    }
+                }
+                __syncwarp();
+                // the unprocessed tail to the front
+                const int rest = qn - np;
+                float2 td = make_float2(0.f, 0.f), tz = make_float2(0.f, 0.f);
+                uint32_t te = 0;
+                uint8_t tg = 0;
+                if (lane < rest) {
+                    td = ws.qd[np + lane]; tz = ws.qz[np + lane]; te = ws.qe[np + lane]; tg = ws.qg[np + lane];
+                }
+                __syncwarp();
+                if (lane < rest) { ws.qd[lane] = td; ws.qz[lane] = tz; ws.qe[lane] = te; ws.qg[lane] = tg; }
+                qn = rest;
+                ov = ov || ((ws.ovmask >> lane) & 1u);
+                __syncwarp();
+            };
+
+            // ---- cull over the reachable stencil cells into the pair queue
+#pragma unroll 1
+            for (int q = 0; q < 9; ++q) {
+                const int ox = q % 3 - 1, oy = q / 3 - 1;
+                const bool need = (ox < 0 ? need_l : (ox > 0 ? need_r : true)) &&
+                                  (oy < 0 ? need_b : (oy > 0 ? need_t : true));
+                const uint32_t nq = (status == 1 && need && !ov) ? ws.sn[q][lane] : 0u;
+                const uint32_t bq = ws.sb[q][lane];
+                const uint32_t trips = __reduce_max_sync(FULL, nq);
+                const float offx = ox < 0 ? -wx : (ox > 0 ? wx : 0.f);
+                const float offy = oy < 0 ? -wy : (oy > 0 ? wy : 0.f);
+#pragma unroll 1
+                for (uint32_t i = 0; i < trips; ++i) {
+                    const uint32_t e = bq + i;
+                    const bool live = i < nq && !ov && e != eA;
+                    bool keep = false;
+                    float dlx = 0.f, dly = 0.f;
+                    float2 zb = make_float2(0.f, 0.f);
+                    if (live) {
+                        const float4 f = B.f4a[e];
+                        const float Px = __fadd_rn(f.x, offx);
+                        const float Py = __fadd_rn(f.y, offy);
+                        dlx = __fsub_rn(Px, tr.x);
+                        dly = __fsub_rn(Py, tr.y);
+                        zb = make_float2(f.z, f.w);
+                        const float q32 = __fmaf_rn(dlx, dlx, __fmul_rn(dly, dly));
+                        if (q32 < rp.cull_keep) {
+                            keep = true;
+                        } else if (q32 > rp.cull_skip) {
+                            keep = false;
+                        } else {
+                            c_rechk += 1;
+                            keep = direct_keep64(rp, sh.rc2, B, msel, mstride, sweep, sigma, cell_local, k, eA, e);
+                        }
+                        if (NV == 0 && sh.round && keep) {       // disks: a kept pair is the overlap
+                            keep = false;
+                            c_chk += 1;
+                            ov = true;
+                        }
+                    }
+                    const unsigned bal = __ballot_sync(FULL, keep);
+                    if (keep) {
+                        const int p = qn + __popc(bal & lt_mask);
+                        ws.qd[p] = make_float2(dlx, dly);
+                        ws.qz[p] = zb;
+                        ws.qe[p] = e;
+                        ws.qg[p] = (uint8_t)lane;
+                    }
+                    qn += __popc(bal);
+                    if (qn >= 32) {
+                        __syncwarp();
+                        drain(32);
+                    }
+                }
+            }
+            while (qn > 0) {
+                __syncwarp();
+                drain(min(qn, 32));
+            }
+
+            // ---- accept or reject
+            if (status == 2) {
+                c_rbd += 1;
+            } else if (status == 1) {
+                if (ov) {
+                    c_rov += 1;
+                } else {
+                    c_acc += 1;
+                    const MoveData m = direct_sel64(msel, mstride, rp, sweep, sigma, cglob, cell_local, k);
+                    const Trial2 t2 = apply64(rp, B.px[eA], B.py[eA], B.q0[eA], B.q1[eA], m);
+                    B.px[eA] = t2.x;
+                    B.py[eA] = t2.y;
+                    B.q0[eA] = t2.c;
+                    B.q1[eA] = t2.s;
+                    B.f4a[eA] = make_float4((float)(cell_coord_bits(t2.x, shx, rp.L[0]) - iwx),
+                                            (float)(cell_coord_bits(t2.y, shy, rp.L[1]) - iwy), (float)t2.c,
+                                            (float)t2.s);
+                }
+            }
+            __syncwarp();
+        }
+        // ---- counters of this item
+        c_moves = __reduce_add_sync(FULL, c_moves);
+        c_acc = __reduce_add_sync(FULL, c_acc);
+        c_rov = __reduce_add_sync(FULL, c_rov);
+        c_rbd = __reduce_add_sync(FULL, c_rbd);
+        c_cull = __reduce_add_sync(FULL, c_cull);
+        c_chk = __reduce_add_sync(FULL, c_chk);
+        c_rechk = __reduce_add_sync(FULL, c_rechk);
+        if (lane == 0) {
+            unsigned long long* C = dv.counters + (size_t)r * kNumCounters;
+            atomicAdd(C + CNT_MOVES, (unsigned long long)c_moves);
+            atomicAdd(C + CNT_ACCEPT, (unsigned long long)c_acc);
+            atomicAdd(C + CNT_REJ_OVERLAP, (unsigned long long)c_rov);
+            atomicAdd(C + CNT_REJ_BOUNDARY, (unsigned long long)c_rbd);
+            atomicAdd(C + CNT_CULL, (unsigned long long)c_cull);
+            atomicAdd(C + CNT_CHECKS, (unsigned long long)c_chk);
+            if (c_rechk) atomicAdd(C + CNT_RECHECK, (unsigned long long)c_rechk);
+        }
+    }
+}
+
+}  // namespace hpmc

@@ -68,6 +68,8 @@ struct Rep {
     float e_va32;            // 3D: |fl32(v) - v| per component of A's local vertices
     float tau3;              // 3D: certificate band (depth / extra gap a certificate needs)
     float ins32;             // |D32|^2 < ins32 -> certain overlap (inscribed balls meet)
+    float reach_lo[3];       // trial rel' > reach_lo[a]: the lower neighbour layer on axis a is beyond the cull
+    float reach_hi[3];       // trial rel' < reach_hi[a]: the upper neighbour layer is beyond the cull
     double ins64;            // the same test on the FP64 |D|^2
     double e_in, e_cull, e_sat;  // the same margins in FP64 (reporting)
 };

@@ -90,7 +90,9 @@ def _tri_lattice_dims(N: int, L: float):
             continue
         nx = -(-N // ny)
         ax, ay = L / nx, L / ny
-        dmin = min(ax, math.hypot(0.5 * ax, ay))
+        # neighbours along a row, in the next row (offset by half a column)
+        # and two rows apart (same column)
+        dmin = min(ax, math.hypot(0.5 * ax, ay), 2.0 * ay)
         if best is None or dmin > best[0]:
             best = (dmin, nx, ny)
     return best

@@ -90,3 +90,12 @@ def test_cube_replica_batch_recipe():
         assert s.d == s.a == inputs.CUBES32768_D and s.nselect == 4
         assert np.allclose(s.orient, [1.0, 0.0, 0.0, 0.0])   # aligned cubes, spacing >= edge
         assert tuple(orc.OracleSystem(3, s.L, s.verts).geometry()["nc"]) >= (4, 4, 4)
+
+
+def test_tiny_lattices_are_overlap_free():
+    # a handful of sites in a small box: the lattice search must count the
+    # distance between rows two apart (same column) too
+    for N, phi, seed in [(3, 0.05, 2), (7, 0.1, 1), (12, 0.30, 3), (30, 0.30, 3), (60, 0.5, 4)]:
+        s = inputs.pentagon_system(N, phi, seed)
+        assert s.notes["site_distance"] >= 1.0
+        assert bf.pairwise_overlaps_2d(s.verts, s.L[0], s.pos, s.orient) == []
