@@ -530,7 +530,7 @@ def run_profile(args):
     else:
         b = hpmc.from_system(inputs.fluid4096(42))
     b.set_precision(hpmc.HPMC_FP64 if args.profile_fp64 else hpmc.HPMC_FP32_FILTERED)
-    if args.lanes:
+    if args.lanes >= 0:
         b.set_group_size(args.lanes, args.warps)
     b.sweep(args.profile_melt, graph=True)
     b.sweep(args.profile_sweeps)
@@ -715,7 +715,8 @@ def main():
     ap.add_argument("--profile-fp64", action="store_true")
     ap.add_argument("--profile-n", type=int, default=0, help="N of the large2d profile case")
     ap.add_argument("--profile-melt", type=int, default=20, help="graph-replayed sweeps before profiling")
-    ap.add_argument("--lanes", type=int, default=0)
+    ap.add_argument("--lanes", type=int, default=-1,
+                    help="lanes per cell of the profiled set kernel (0: the 2D direct kernel; default: as created)")
     ap.add_argument("--warps", type=int, default=4)
     ap.add_argument("--trace", action="store_true", help="with --profile-sweeps: per-warp phase stamps")
     ap.add_argument("--gpus", type=int, default=1)

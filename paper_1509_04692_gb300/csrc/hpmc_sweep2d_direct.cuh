@@ -32,6 +32,11 @@ namespace hpmc {
 
 struct __align__(16) Direct2Warp {
     static constexpr int QCAP = 64;
+    static constexpr int KPRE = 4;    // selects of an item whose records are staged at its start
+    float4 rec[KPRE][32];             // staged FP32 part of the select records (fdx, fdy, fcd, fsd)
+    uint32_t r0[KPRE][32];            // and their pick words
+    double acc[8][32];                // operands of the accept: contract deltas dx, dy, cd, sd and the
+                                      // moving particle's FP64 x, y, c, s (asynchronous copies)
     float2 qd[QCAP];                  // queued Delta32 (B relative to the trial)
     float2 qz[QCAP];                  // queued B orientation (FP32 mirror)
     uint32_t qe[QCAP];                // queued B slot in the sorted buffer
@@ -42,6 +47,36 @@ struct __align__(16) Direct2Warp {
     uint32_t sn[9][32];               // and size
     unsigned int ovmask;              // lanes whose move overlaps
 };
+
+// asynchronous global -> shared copies of the issuing thread (cp.async);
+// the thread's own later wait makes them visible to it
+__device__ __forceinline__ void cp_async4(void* smem, const void* gmem)
+{
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(s), "l"(gmem) : "memory");
+}
+
+__device__ __forceinline__ void cp_async8(void* smem, const void* gmem)
+{
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(s), "l"(gmem) : "memory");
+}
+
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem)
+{
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 16;" ::"r"(s), "l"(gmem) : "memory");
+}
+
+__device__ __forceinline__ void cp_async_commit()
+{
+    asm volatile("cp.async.commit_group;" ::: "memory");
+}
+
+__device__ __forceinline__ void cp_async_wait_all()
+{
+    asm volatile("cp.async.wait_all;" ::: "memory");
+}
 
 // The select record of select k of a cell: from the sweep's table, or
 // computed here for selects beyond the table's stride.  The FP32 part (pick
@@ -127,8 +162,9 @@ __global__ void __launch_bounds__(256, 2)
 k_set2d_direct(Dev dv, Shape2 sh, int nxt, int sigma, const uint32_t* __restrict__ item_base)
 {
     pdl_wait();
+    using W = Direct2Warp;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    Direct2Warp& ws = reinterpret_cast<Direct2Warp*>(smem_raw)[threadIdx.x >> 5];
+    W& ws = reinterpret_cast<W*>(smem_raw)[threadIdx.x >> 5];
     const int lane = threadIdx.x & 31;
     const unsigned FULL = 0xffffffffu;
     const unsigned lt_mask = (1u << lane) - 1u;
@@ -159,18 +195,24 @@ k_set2d_direct(Dev dv, Shape2 sh, int nxt, int sigma, const uint32_t* __restrict
         const bool valid = jx < nax;
         const int ix = (sigma & 1) + 2 * jx;
         const uint64_t sweep = dv.sweep[r] - 1;           // the running sweep
-        const double shx = dv.shift[3 * r], shy = dv.shift[3 * r + 1];
         const uint32_t nsel = rp.nselect;
         const uint32_t cell_local = (uint32_t)ix + (uint32_t)nc0 * (uint32_t)iy;
         const uint32_t cglob = rp.cbase + cell_local;
         const float wx = rp.w32[0], wy = rp.w32[1];
-        // cell origins i * w of the relative coordinates (as in k_place)
-        const double iwx = (double)ix * rp.w[0];
-        const double iwy = (double)iy * rp.w[1];
+        const uint32_t kpre = min(min(nsel, mstride), (uint32_t)W::KPRE);
 
-        // ---- stencil cells, q = 3 (oy + 1) + (ox + 1): sorted begin and size
+        // ---- stencil cells, q = 3 (oy + 1) + (ox + 1): sorted begin and size;
+        // the records of the first selects staged asynchronously
         uint32_t T = 0, cb = 0, n_c = 0;
         __syncwarp();
+        if (valid) {
+            for (uint32_t k = 0; k < kpre; ++k) {
+                const MoveData* p = msel + (size_t)cglob * mstride + k;
+                cp_async16(&ws.rec[k][lane], &p->fdx);
+                cp_async4(&ws.r0[k][lane], &p->r0);
+            }
+        }
+        cp_async_commit();
 #pragma unroll
         for (int q = 0; q < 9; ++q) {
             uint32_t b = 0u, n = 0u;
@@ -190,6 +232,7 @@ k_set2d_direct(Dev dv, Shape2 sh, int nxt, int sigma, const uint32_t* __restrict
         }
         const bool live_cell = valid && n_c > 0;
         unsigned c_moves = 0, c_acc = 0, c_rov = 0, c_rbd = 0, c_cull = 0, c_chk = 0, c_rechk = 0;
+        uint32_t eA_prev = 0xffffffffu;                    // slot this lane moved in its last select
 
 #pragma unroll 1
         for (uint32_t k = 0; k < nsel; ++k) {
@@ -197,12 +240,35 @@ k_set2d_direct(Dev dv, Shape2 sh, int nxt, int sigma, const uint32_t* __restrict
             int status = 0;                                // 0 idle, 1 in the cell, 2 left it
             uint32_t eA = 0;
             float4 tr = make_float4(0.f, 0.f, 0.f, 0.f);
+            cp_async_wait_all();                           // staged records / last accept's operands
             if (live_cell) {
                 c_moves += 1;
-                const Sel32 m = direct_sel32(msel, mstride, rp, sweep, sigma, cglob, cell_local, k);
+                Sel32 m;
+                if (k < kpre) {
+                    const float4 v = ws.rec[k][lane];
+                    m = { v.x, v.y, v.z, v.w, ws.r0[k][lane] };
+                } else {
+                    m = direct_sel32(msel, mstride, rp, sweep, sigma, cglob, cell_local, k);
+                }
                 eA = cb + __umulhi(m.r0, n_c);
                 // a plain load: this lane may have written the slot earlier in the set
                 const float4 f = B.f4a[eA];
+                // the accept's FP64 operands, copied while the move is decided
+                // (a slot this lane just moved is already staged, with its new state)
+                if (k < mstride) {
+                    const MoveData* p = msel + (size_t)cglob * mstride + k;
+                    cp_async8(&ws.acc[0][lane], &p->dx);
+                    cp_async8(&ws.acc[1][lane], &p->dy);
+                    cp_async8(&ws.acc[2][lane], &p->cd);
+                    cp_async8(&ws.acc[3][lane], &p->sd);
+                }
+                if (eA != eA_prev) {
+                    cp_async8(&ws.acc[4][lane], B.px + eA);
+                    cp_async8(&ws.acc[5][lane], B.py + eA);
+                    cp_async8(&ws.acc[6][lane], B.q0 + eA);
+                    cp_async8(&ws.acc[7][lane], B.q1 + eA);
+                }
+                cp_async_commit();
                 const float rx = __fadd_rn(f.x, m.fdx), ry = __fadd_rn(f.y, m.fdy);
                 const float cz = __fmaf_rn(f.z, m.fcd, -__fmul_rn(f.w, m.fsd));
                 const float sz = __fmaf_rn(f.z, m.fsd, __fmul_rn(f.w, m.fcd));
@@ -215,8 +281,8 @@ k_set2d_direct(Dev dv, Shape2 sh, int nxt, int sigma, const uint32_t* __restrict
                     status = 1;
                 } else {
                     c_rechk += 1;
-                    status = direct_in_cell64(rp, B, msel, mstride, sweep, sigma, cell_local, k, eA, shx, shy, ix,
-                                              iy) ? 1 : 2;
+                    status = direct_in_cell64(rp, B, msel, mstride, sweep, sigma, cell_local, k, eA,
+                                              dv.shift[3 * r], dv.shift[3 * r + 1], ix, iy) ? 1 : 2;
                 }
                 ws.tz[lane] = make_float2(cz, sz);
                 ws.ea[lane] = eA;
@@ -224,10 +290,24 @@ k_set2d_direct(Dev dv, Shape2 sh, int nxt, int sigma, const uint32_t* __restrict
             if (lane == 0) ws.ovmask = 0u;
             __syncwarp();
 
-            // ---- stencil columns and rows within reach of the trial
-            const bool need_l = !(tr.x > rp.reach_lo[0]), need_r = !(tr.x < rp.reach_hi[0]);
-            const bool need_b = !(tr.y > rp.reach_lo[1]), need_t = !(tr.y < rp.reach_hi[1]);
-            if (status == 1) c_cull += T - 1u;             // the stencil's candidates (self excluded)
+            // ---- the stencil cells within reach of the trial, and their candidates
+            uint32_t mask = 0u, Tn = 0u;
+            if (status == 1) {
+                const bool need_l = !(tr.x > rp.reach_lo[0]), need_r = !(tr.x < rp.reach_hi[0]);
+                const bool need_b = !(tr.y > rp.reach_lo[1]), need_t = !(tr.y < rp.reach_hi[1]);
+#pragma unroll
+                for (int q = 0; q < 9; ++q) {
+                    const int ox = q % 3 - 1, oy = q / 3 - 1;
+                    const bool need = (ox < 0 ? need_l : (ox > 0 ? need_r : true)) &&
+                                      (oy < 0 ? need_b : (oy > 0 ? need_t : true));
+                    const uint32_t n = ws.sn[q][lane];
+                    if (need && n) {
+                        mask |= 1u << q;
+                        Tn += n;
+                    }
+                }
+                c_cull += T - 1u;                          // the stencil's candidates (self excluded)
+            }
             bool ov = false;                               // this lane's move overlaps
             int qn = 0;
 
@@ -267,59 +347,72 @@ k_set2d_direct(Dev dv, Shape2 sh, int nxt, int sigma, const uint32_t* __restrict
                 __syncwarp();
             };
 
-            // ---- cull over the reachable stencil cells into the pair queue
+            // ---- cull: a cursor over the lane's candidates, cell by cell of its
+            // mask, the next candidate's data loaded one trip ahead
+            const uint32_t trips = __reduce_max_sync(FULL, Tn);
+            uint32_t m_left = mask;
+            int kc = 0;
+            uint32_t ec = 0, eend = 0;
+            float4 fc = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (Tn) {
+                kc = __ffs(m_left) - 1;
+                m_left &= m_left - 1u;
+                ec = ws.sb[kc][lane];
+                eend = ec + ws.sn[kc][lane];
+                fc = B.f4a[ec];
+            }
 #pragma unroll 1
-            for (int q = 0; q < 9; ++q) {
-                const int ox = q % 3 - 1, oy = q / 3 - 1;
-                const bool need = (ox < 0 ? need_l : (ox > 0 ? need_r : true)) &&
-                                  (oy < 0 ? need_b : (oy > 0 ? need_t : true));
-                const uint32_t nq = (status == 1 && need && !ov) ? ws.sn[q][lane] : 0u;
-                const uint32_t bq = ws.sb[q][lane];
-                const uint32_t trips = __reduce_max_sync(FULL, nq);
-                const float offx = ox < 0 ? -wx : (ox > 0 ? wx : 0.f);
-                const float offy = oy < 0 ? -wy : (oy > 0 ? wy : 0.f);
-#pragma unroll 1
-                for (uint32_t i = 0; i < trips; ++i) {
-                    const uint32_t e = bq + i;
-                    const bool live = i < nq && !ov && e != eA;
-                    bool keep = false;
-                    float dlx = 0.f, dly = 0.f;
-                    float2 zb = make_float2(0.f, 0.f);
-                    if (live) {
-                        const float4 f = B.f4a[e];
-                        const float Px = __fadd_rn(f.x, offx);
-                        const float Py = __fadd_rn(f.y, offy);
-                        dlx = __fsub_rn(Px, tr.x);
-                        dly = __fsub_rn(Py, tr.y);
-                        zb = make_float2(f.z, f.w);
-                        const float q32 = __fmaf_rn(dlx, dlx, __fmul_rn(dly, dly));
-                        if (q32 < rp.cull_keep) {
-                            keep = true;
-                        } else if (q32 > rp.cull_skip) {
-                            keep = false;
-                        } else {
-                            c_rechk += 1;
-                            keep = direct_keep64(rp, sh.rc2, B, msel, mstride, sweep, sigma, cell_local, k, eA, e);
-                        }
-                        if (NV == 0 && sh.round && keep) {       // disks: a kept pair is the overlap
-                            keep = false;
-                            c_chk += 1;
-                            ov = true;
-                        }
+            for (uint32_t i = 0; i < trips; ++i) {
+                const bool live = i < Tn && !ov;
+                const uint32_t e = ec;
+                const int kq = kc;
+                const float4 f = fc;
+                if (live && i + 1 < Tn) {                  // advance and prefetch
+                    ec += 1u;
+                    if (ec == eend) {
+                        kc = __ffs(m_left) - 1;
+                        m_left &= m_left - 1u;
+                        ec = ws.sb[kc][lane];
+                        eend = ec + ws.sn[kc][lane];
                     }
-                    const unsigned bal = __ballot_sync(FULL, keep);
-                    if (keep) {
-                        const int p = qn + __popc(bal & lt_mask);
-                        ws.qd[p] = make_float2(dlx, dly);
-                        ws.qz[p] = zb;
-                        ws.qe[p] = e;
-                        ws.qg[p] = (uint8_t)lane;
+                    fc = B.f4a[ec];
+                }
+                bool keep = false;
+                float dlx = 0.f, dly = 0.f;
+                if (live && e != eA) {
+                    const int qy = (kq * 11) >> 5;         // kq / 3 for kq < 9
+                    const int qx = kq - 3 * qy;
+                    const float offx = qx == 0 ? -wx : (qx == 2 ? wx : 0.f);
+                    const float offy = qy == 0 ? -wy : (qy == 2 ? wy : 0.f);
+                    dlx = __fsub_rn(__fadd_rn(f.x, offx), tr.x);
+                    dly = __fsub_rn(__fadd_rn(f.y, offy), tr.y);
+                    const float q32 = __fmaf_rn(dlx, dlx, __fmul_rn(dly, dly));
+                    if (q32 < rp.cull_keep) {
+                        keep = true;
+                    } else if (q32 > rp.cull_skip) {
+                        keep = false;
+                    } else {
+                        c_rechk += 1;
+                        keep = direct_keep64(rp, sh.rc2, B, msel, mstride, sweep, sigma, cell_local, k, eA, e);
                     }
-                    qn += __popc(bal);
-                    if (qn >= 32) {
-                        __syncwarp();
-                        drain(32);
+                    if (NV == 0 && sh.round && keep) {     // disks: a kept pair is the overlap
+                        keep = false;
+                        c_chk += 1;
+                        ov = true;
                     }
+                }
+                const unsigned bal = __ballot_sync(FULL, keep);
+                if (keep) {
+                    const int p = qn + __popc(bal & lt_mask);
+                    ws.qd[p] = make_float2(dlx, dly);
+                    ws.qz[p] = make_float2(f.z, f.w);
+                    ws.qe[p] = e;
+                    ws.qg[p] = (uint8_t)lane;
+                }
+                qn += __popc(bal);
+                if (qn >= 32) {
+                    __syncwarp();
+                    drain(32);
                 }
             }
             while (qn > 0) {
@@ -328,6 +421,7 @@ k_set2d_direct(Dev dv, Shape2 sh, int nxt, int sigma, const uint32_t* __restrict
             }
 
             // ---- accept or reject
+            eA_prev = 0xffffffffu;
             if (status == 2) {
                 c_rbd += 1;
             } else if (status == 1) {
@@ -335,12 +429,30 @@ k_set2d_direct(Dev dv, Shape2 sh, int nxt, int sigma, const uint32_t* __restrict
                     c_rov += 1;
                 } else {
                     c_acc += 1;
-                    const MoveData m = direct_sel64(msel, mstride, rp, sweep, sigma, cglob, cell_local, k);
-                    const Trial2 t2 = apply64(rp, B.px[eA], B.py[eA], B.q0[eA], B.q1[eA], m);
+                    cp_async_wait_all();
+                    MoveData m{};
+                    if (k < mstride) {
+                        m.dx = ws.acc[0][lane]; m.dy = ws.acc[1][lane];
+                        m.cd = ws.acc[2][lane]; m.sd = ws.acc[3][lane];
+                    } else {
+                        m = direct_sel64(msel, mstride, rp, sweep, sigma, cglob, cell_local, k);
+                    }
+                    const Trial2 t2 = apply64(rp, ws.acc[4][lane], ws.acc[5][lane], ws.acc[6][lane],
+                                              ws.acc[7][lane], m);
                     B.px[eA] = t2.x;
                     B.py[eA] = t2.y;
                     B.q0[eA] = t2.c;
                     B.q1[eA] = t2.s;
+                    // keep the new state staged for a next select of the same particle
+                    ws.acc[4][lane] = t2.x;
+                    ws.acc[5][lane] = t2.y;
+                    ws.acc[6][lane] = t2.c;
+                    ws.acc[7][lane] = t2.s;
+                    eA_prev = eA;
+                    // cell origins i * w of the relative coordinates (as in k_place)
+                    const double shx = dv.shift[3 * r], shy = dv.shift[3 * r + 1];
+                    const double iwx = (double)ix * rp.w[0];
+                    const double iwy = (double)iy * rp.w[1];
                     B.f4a[eA] = make_float4((float)(cell_coord_bits(t2.x, shx, rp.L[0]) - iwx),
                                             (float)(cell_coord_bits(t2.y, shy, rp.L[1]) - iwy), (float)t2.c,
                                             (float)t2.s);
@@ -348,6 +460,7 @@ k_set2d_direct(Dev dv, Shape2 sh, int nxt, int sigma, const uint32_t* __restrict
             }
             __syncwarp();
         }
+        cp_async_wait_all();
         // ---- counters of this item
         c_moves = __reduce_add_sync(FULL, c_moves);
         c_acc = __reduce_add_sync(FULL, c_acc);
