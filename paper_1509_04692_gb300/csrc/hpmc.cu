@@ -434,10 +434,11 @@ int enqueue_rebuild(hpmc_batch* h, cudaStream_t st, bool with_shift)
     return 0;
 }
 
-// the set kernels that read their first selects from the sweep's table
+// the set kernels that read their first selects from the sweep's table (the
+// latency regime; the direct kernel draws its selects itself)
 bool uses_select_table(int G)
 {
-    return G >= 8 || G == 0;
+    return G >= 8;
 }
 
 // Select table for the latency-regime kernels: one record for each of the
@@ -451,8 +452,7 @@ int prepare_selects(hpmc_batch* h)
     if (!h->use_selects) return 0;
     uint32_t stride = 1;
     for (const HostRep& r : h->hr) stride = std::max(stride, r.nselect);
-    // the direct kernel takes up to 8 selects of a cell from the table
-    stride = std::min<uint32_t>(stride, (uint32_t)(h->G ? h->G : 8));
+    stride = std::min<uint32_t>(stride, (uint32_t)h->G);
     const uint64_t need = (uint64_t)h->ctot * stride;
     const size_t rec = select_record_bytes(h->dim);
     if (need > h->msel_cap) {

@@ -22,9 +22,12 @@
 // circumdiameter (the 2^24-pentagon system) a trial needs 4 of the 9 cells on
 // average.  The decisions are the contract's either way.
 //
-// The picks and move deltas come from the sweep's select table (selects.cu);
-// FP64 arithmetic runs for accepted moves and for the rare FP32 verdicts the
-// certified margins cannot decide, exactly as in the other set kernels.
+// Each lane draws its select's Philox words itself (every lane has a move, so
+// no lane idles through them), keeps the words for the FP64 contract, and
+// proposes in FP32.  FP64 arithmetic runs for accepted moves and for the
+// rare FP32 verdicts the certified margins cannot decide, exactly as in the
+// other set kernels; it needs no select table, so no table kernel competes
+// with the cell-list rebuild for the FP64 pipe.
 #pragma once
 #include "hpmc_sweep2d.cuh"
 
@@ -32,11 +35,8 @@ namespace hpmc {
 
 struct __align__(16) Direct2Warp {
     static constexpr int QCAP = 64;
-    static constexpr int KPRE = 4;    // selects of an item whose records are staged at its start
-    float4 rec[KPRE][32];             // staged FP32 part of the select records (fdx, fdy, fcd, fsd)
-    uint32_t r0[KPRE][32];            // and their pick words
-    double acc[8][32];                // operands of the accept: contract deltas dx, dy, cd, sd and the
-                                      // moving particle's FP64 x, y, c, s (asynchronous copies)
+    uint32_t wd[6][32];               // Philox words r1..r6 of each lane's select
+    double acc[4][32];                // the moving particle's FP64 x, y, c, s (asynchronous copies)
     float2 qd[QCAP];                  // queued Delta32 (B relative to the trial)
     float2 qz[QCAP];                  // queued B orientation (FP32 mirror)
     uint32_t qe[QCAP];                // queued B slot in the sorted buffer
@@ -50,22 +50,10 @@ struct __align__(16) Direct2Warp {
 
 // asynchronous global -> shared copies of the issuing thread (cp.async);
 // the thread's own later wait makes them visible to it
-__device__ __forceinline__ void cp_async4(void* smem, const void* gmem)
-{
-    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(s), "l"(gmem) : "memory");
-}
-
 __device__ __forceinline__ void cp_async8(void* smem, const void* gmem)
 {
     const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
     asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(s), "l"(gmem) : "memory");
-}
-
-__device__ __forceinline__ void cp_async16(void* smem, const void* gmem)
-{
-    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 16;" ::"r"(s), "l"(gmem) : "memory");
 }
 
 __device__ __forceinline__ void cp_async_commit()
@@ -78,65 +66,24 @@ __device__ __forceinline__ void cp_async_wait_all()
     asm volatile("cp.async.wait_all;" ::: "memory");
 }
 
-// The select record of select k of a cell: from the sweep's table, or
-// computed here for selects beyond the table's stride.  The FP32 part (pick
-// word and FP32 deltas) is needed to propose, the FP64 part (contract
-// deltas) only once the move is decided, so they are read separately.
-struct Sel32 {
-    float fdx, fdy, fcd, fsd;
-    uint32_t r0;
-};
-
-__device__ __forceinline__ Sel32 direct_sel32(const MoveData* __restrict__ msel, uint32_t mstride,
-                                              const Rep& rp, uint64_t sweep, int sigma, uint32_t cglob,
-                                              uint32_t cell, uint32_t k)
-{
-    if (k < mstride) {
-        const MoveData* p = msel + (size_t)cglob * mstride + k;
-        const float4 v = *reinterpret_cast<const float4*>(&p->fdx);
-        return { v.x, v.y, v.z, v.w, p->r0 };
-    }
-    const MoveData m = precompute_select(rp, rp.seed, sweep, (uint32_t)sigma, cell, k);
-    return { m.fdx, m.fdy, m.fcd, m.fsd, m.r0 };
-}
-
-__device__ __forceinline__ MoveData direct_sel64(const MoveData* __restrict__ msel, uint32_t mstride,
-                                                 const Rep& rp, uint64_t sweep, int sigma, uint32_t cglob,
-                                                 uint32_t cell, uint32_t k)
-{
-    MoveData m{};
-    if (k < mstride) {
-        const MoveData* p = msel + (size_t)cglob * mstride + k;
-        const double2 a = *reinterpret_cast<const double2*>(&p->dx);
-        const double2 b = *reinterpret_cast<const double2*>(&p->cd);
-        m.dx = a.x; m.dy = a.y; m.cd = b.x; m.sd = b.y;
-        return m;
-    }
-    return precompute_select(rp, rp.seed, sweep, (uint32_t)sigma, cell, k);
-}
-
 // The rare FP64 paths stay out of line, so that their registers do not
-// weigh on the common path of the kernel.  Each takes the moving particle's
-// slot gA and recomputes the contract's trial from its select record.
+// weigh on the common path of the kernel.  Each recomputes the contract's
+// trial of the moving particle (slot gA) from its select's words w[0..5].
 
 // in-cell test of the FP64 contract trial (FP32 verdict not certified)
-__device__ __noinline__ bool direct_in_cell64(const Rep& rp, const Bufs& B, const MoveData* __restrict__ msel,
-                                              uint32_t mstride, uint64_t sweep, int sigma, uint32_t cell,
-                                              uint32_t k, uint32_t gA, double shx, double shy, int ix, int iy)
+__device__ __noinline__ bool direct_in_cell64(const Rep& rp, const Bufs& B, const uint32_t* w, uint32_t gA,
+                                              double shx, double shy, int ix, int iy)
 {
-    const MoveData m = direct_sel64(msel, mstride, rp, sweep, sigma, rp.cbase + cell, cell, k);
-    const Trial2 t2 = apply64(rp, B.px[gA], B.py[gA], B.q0[gA], B.q1[gA], m);
+    const Trial2 t2 = propose2d(rp, B.px[gA], B.py[gA], B.q0[gA], B.q1[gA], w[0], w[1], w[2], w[3], w[4], w[5]);
     return cell_axis(t2.x, shx, rp.L[0], rp.inv_w[0], rp.nc[0]) == ix &&
            cell_axis(t2.y, shy, rp.L[1], rp.inv_w[1], rp.nc[1]) == iy;
 }
 
 // circumsphere cull of the FP64 contract (FP32 verdict not certified)
-__device__ __noinline__ bool direct_keep64(const Rep& rp, double rc2, const Bufs& B,
-                                           const MoveData* __restrict__ msel, uint32_t mstride, uint64_t sweep,
-                                           int sigma, uint32_t cell, uint32_t k, uint32_t gA, uint32_t gB)
+__device__ __noinline__ bool direct_keep64(const Rep& rp, double rc2, const Bufs& B, const uint32_t* w, uint32_t gA,
+                                           uint32_t gB)
 {
-    const MoveData m = direct_sel64(msel, mstride, rp, sweep, sigma, rp.cbase + cell, cell, k);
-    const Trial2 t2 = apply64(rp, B.px[gA], B.py[gA], B.q0[gA], B.q1[gA], m);
+    const Trial2 t2 = propose2d(rp, B.px[gA], B.py[gA], B.q0[gA], B.q1[gA], w[0], w[1], w[2], w[3], w[4], w[5]);
     const double Dx = min_image(B.px[gB] - t2.x, rp.L[0], rp.halfL[0]);
     const double Dy = min_image(B.py[gB] - t2.y, rp.L[1], rp.halfL[1]);
     return (Dx * Dx + Dy * Dy) <= rc2;
@@ -145,13 +92,10 @@ __device__ __noinline__ bool direct_keep64(const Rep& rp, double rc2, const Bufs
 // separating-axis test of the FP64 contract on a queued pair (FP32 verdict
 // not certified)
 template <int NV>
-__device__ __noinline__ bool direct_overlap64(const Shape2& sh, const Rep& rp, const Bufs& B,
-                                              const MoveData* __restrict__ msel, uint32_t mstride,
-                                              uint64_t sweep, int sigma, uint32_t cell, uint32_t k,
+__device__ __noinline__ bool direct_overlap64(const Shape2& sh, const Rep& rp, const Bufs& B, const uint32_t* w,
                                               uint32_t gA, uint32_t gB)
 {
-    const MoveData mo = direct_sel64(msel, mstride, rp, sweep, sigma, rp.cbase + cell, cell, k);
-    const Trial2 t2 = apply64(rp, B.px[gA], B.py[gA], B.q0[gA], B.q1[gA], mo);
+    const Trial2 t2 = propose2d(rp, B.px[gA], B.py[gA], B.q0[gA], B.q1[gA], w[0], w[1], w[2], w[3], w[4], w[5]);
     const double Dx = min_image(B.px[gB] - t2.x, rp.L[0], rp.halfL[0]);
     const double Dy = min_image(B.py[gB] - t2.y, rp.L[1], rp.halfL[1]);
     return overlap2d64<NV>(sh, Dx, Dy, t2.c, t2.s, B.q0[gB], B.q1[gB]);
@@ -172,8 +116,6 @@ k_set2d_direct(Dev dv, Shape2 sh, int nxt, int sigma, const uint32_t* __restrict
     const uint32_t* __restrict__ start = dv.start;
     const uint32_t nitems = item_base[dv.R];
     const uint32_t wpb = blockDim.x >> 5;
-    const MoveData* __restrict__ msel = static_cast<const MoveData*>(dv.msel);
-    const uint32_t mstride = dv.msel_stride;
 
     for (uint32_t item = blockIdx.x * wpb + (threadIdx.x >> 5); item < nitems; item += gridDim.x * wpb) {
         // ---- replica and strip of this work item
@@ -197,22 +139,12 @@ k_set2d_direct(Dev dv, Shape2 sh, int nxt, int sigma, const uint32_t* __restrict
         const uint64_t sweep = dv.sweep[r] - 1;           // the running sweep
         const uint32_t nsel = rp.nselect;
         const uint32_t cell_local = (uint32_t)ix + (uint32_t)nc0 * (uint32_t)iy;
-        const uint32_t cglob = rp.cbase + cell_local;
         const float wx = rp.w32[0], wy = rp.w32[1];
-        const uint32_t kpre = min(min(nsel, mstride), (uint32_t)W::KPRE);
+        const uint64_t seed = rp.seed;
 
-        // ---- stencil cells, q = 3 (oy + 1) + (ox + 1): sorted begin and size;
-        // the records of the first selects staged asynchronously
+        // ---- stencil cells, q = 3 (oy + 1) + (ox + 1): sorted begin and size
         uint32_t T = 0, cb = 0, n_c = 0;
         __syncwarp();
-        if (valid) {
-            for (uint32_t k = 0; k < kpre; ++k) {
-                const MoveData* p = msel + (size_t)cglob * mstride + k;
-                cp_async16(&ws.rec[k][lane], &p->fdx);
-                cp_async4(&ws.r0[k][lane], &p->r0);
-            }
-        }
-        cp_async_commit();
 #pragma unroll
         for (int q = 0; q < 9; ++q) {
             uint32_t b = 0u, n = 0u;
@@ -240,38 +172,37 @@ k_set2d_direct(Dev dv, Shape2 sh, int nxt, int sigma, const uint32_t* __restrict
             int status = 0;                                // 0 idle, 1 in the cell, 2 left it
             uint32_t eA = 0;
             float4 tr = make_float4(0.f, 0.f, 0.f, 0.f);
-            cp_async_wait_all();                           // staged records / last accept's operands
+            cp_async_wait_all();                           // the last accept's operands
             if (live_cell) {
                 c_moves += 1;
-                Sel32 m;
-                if (k < kpre) {
-                    const float4 v = ws.rec[k][lane];
-                    m = { v.x, v.y, v.z, v.w, ws.r0[k][lane] };
-                } else {
-                    m = direct_sel32(msel, mstride, rp, sweep, sigma, cglob, cell_local, k);
-                }
-                eA = cb + __umulhi(m.r0, n_c);
+                // Philox words of select k of this cell (Sec. 2.5: one stream per trial move)
+                const uint4 b0 = move_block(seed, sweep, (uint32_t)sigma, cell_local, k, 0);
+                const uint4 b1 = move_block(seed, sweep, (uint32_t)sigma, cell_local, k, 1);
+                eA = cb + __umulhi(b0.x, n_c);
                 // a plain load: this lane may have written the slot earlier in the set
                 const float4 f = B.f4a[eA];
                 // the accept's FP64 operands, copied while the move is decided
                 // (a slot this lane just moved is already staged, with its new state)
-                if (k < mstride) {
-                    const MoveData* p = msel + (size_t)cglob * mstride + k;
-                    cp_async8(&ws.acc[0][lane], &p->dx);
-                    cp_async8(&ws.acc[1][lane], &p->dy);
-                    cp_async8(&ws.acc[2][lane], &p->cd);
-                    cp_async8(&ws.acc[3][lane], &p->sd);
-                }
                 if (eA != eA_prev) {
-                    cp_async8(&ws.acc[4][lane], B.px + eA);
-                    cp_async8(&ws.acc[5][lane], B.py + eA);
-                    cp_async8(&ws.acc[6][lane], B.q0 + eA);
-                    cp_async8(&ws.acc[7][lane], B.q1 + eA);
+                    cp_async8(&ws.acc[0][lane], B.px + eA);
+                    cp_async8(&ws.acc[1][lane], B.py + eA);
+                    cp_async8(&ws.acc[2][lane], B.q0 + eA);
+                    cp_async8(&ws.acc[3][lane], B.q1 + eA);
                 }
                 cp_async_commit();
-                const float rx = __fadd_rn(f.x, m.fdx), ry = __fadd_rn(f.y, m.fdy);
-                const float cz = __fmaf_rn(f.z, m.fcd, -__fmul_rn(f.w, m.fsd));
-                const float sz = __fmaf_rn(f.z, m.fsd, __fmul_rn(f.w, m.fcd));
+                ws.wd[0][lane] = b0.y; ws.wd[1][lane] = b0.z; ws.wd[2][lane] = b0.w;
+                ws.wd[3][lane] = b1.x; ws.wd[4][lane] = b1.y; ws.wd[5][lane] = b1.z;
+                // FP32 trial (the deltas as the select table computes them)
+                const float fdx = __fmul_rn(rp.d32, m24(b0.y));
+                const float fdy = __fmul_rn(rp.d32, m24(b0.w));
+                const float ft = __fmul_rn(rp.tau32, m24(b1.y));
+                const float ftt = __fmul_rn(ft, ft);
+                const float finv = __frcp_rn(__fadd_rn(1.0f, ftt));
+                const float fcd = __fmul_rn(__fsub_rn(1.0f, ftt), finv);
+                const float fsd = __fmul_rn(__fadd_rn(ft, ft), finv);
+                const float rx = __fadd_rn(f.x, fdx), ry = __fadd_rn(f.y, fdy);
+                const float cz = __fmaf_rn(f.z, fcd, -__fmul_rn(f.w, fsd));
+                const float sz = __fmaf_rn(f.z, fsd, __fmul_rn(f.w, fcd));
                 tr = make_float4(rx, ry, cz, sz);
                 const bool out = rx < rp.out_lo || ry < rp.out_lo || rx > rp.out_hi[0] || ry > rp.out_hi[1];
                 const bool in = rx > rp.in_lo && ry > rp.in_lo && rx < rp.in_hi[0] && ry < rp.in_hi[1];
@@ -281,8 +212,8 @@ k_set2d_direct(Dev dv, Shape2 sh, int nxt, int sigma, const uint32_t* __restrict
                     status = 1;
                 } else {
                     c_rechk += 1;
-                    status = direct_in_cell64(rp, B, msel, mstride, sweep, sigma, cell_local, k, eA,
-                                              dv.shift[3 * r], dv.shift[3 * r + 1], ix, iy) ? 1 : 2;
+                    const uint32_t w[6] = { b0.y, b0.z, b0.w, b1.x, b1.y, b1.z };
+                    status = direct_in_cell64(rp, B, w, eA, dv.shift[3 * r], dv.shift[3 * r + 1], ix, iy) ? 1 : 2;
                 }
                 ws.tz[lane] = make_float2(cz, sz);
                 ws.ea[lane] = eA;
@@ -323,10 +254,9 @@ k_set2d_direct(Dev dv, Shape2 sh, int nxt, int sigma, const uint32_t* __restrict
                         if (v == 2) {
                             // not certified: the FP64 contract on the owner's trial
                             c_rechk += 1;
-                            const int ixo = (sigma & 1) + 2 * (strip * 32 + g2);
-                            const uint32_t clo = (uint32_t)ixo + (uint32_t)nc0 * (uint32_t)iy;
-                            pov = direct_overlap64<NV>(sh, rp, B, msel, mstride, sweep, sigma, clo, k, ws.ea[g2],
-                                                       ws.qe[lane]);
+                            const uint32_t w[6] = { ws.wd[0][g2], ws.wd[1][g2], ws.wd[2][g2],
+                                                    ws.wd[3][g2], ws.wd[4][g2], ws.wd[5][g2] };
+                            pov = direct_overlap64<NV>(sh, rp, B, w, ws.ea[g2], ws.qe[lane]);
                         }
                         if (pov) atomicOr(&ws.ovmask, 1u << g2);
                     }
@@ -393,7 +323,9 @@ k_set2d_direct(Dev dv, Shape2 sh, int nxt, int sigma, const uint32_t* __restrict
                         keep = false;
                     } else {
                         c_rechk += 1;
-                        keep = direct_keep64(rp, sh.rc2, B, msel, mstride, sweep, sigma, cell_local, k, eA, e);
+                        const uint32_t w[6] = { ws.wd[0][lane], ws.wd[1][lane], ws.wd[2][lane],
+                                                ws.wd[3][lane], ws.wd[4][lane], ws.wd[5][lane] };
+                        keep = direct_keep64(rp, sh.rc2, B, w, eA, e);
                     }
                     if (NV == 0 && sh.round && keep) {     // disks: a kept pair is the overlap
                         keep = false;
@@ -430,24 +362,18 @@ k_set2d_direct(Dev dv, Shape2 sh, int nxt, int sigma, const uint32_t* __restrict
                 } else {
                     c_acc += 1;
                     cp_async_wait_all();
-                    MoveData m{};
-                    if (k < mstride) {
-                        m.dx = ws.acc[0][lane]; m.dy = ws.acc[1][lane];
-                        m.cd = ws.acc[2][lane]; m.sd = ws.acc[3][lane];
-                    } else {
-                        m = direct_sel64(msel, mstride, rp, sweep, sigma, cglob, cell_local, k);
-                    }
-                    const Trial2 t2 = apply64(rp, ws.acc[4][lane], ws.acc[5][lane], ws.acc[6][lane],
-                                              ws.acc[7][lane], m);
+                    const Trial2 t2 = propose2d(rp, ws.acc[0][lane], ws.acc[1][lane], ws.acc[2][lane],
+                                                ws.acc[3][lane], ws.wd[0][lane], ws.wd[1][lane], ws.wd[2][lane],
+                                                ws.wd[3][lane], ws.wd[4][lane], ws.wd[5][lane]);
                     B.px[eA] = t2.x;
                     B.py[eA] = t2.y;
                     B.q0[eA] = t2.c;
                     B.q1[eA] = t2.s;
                     // keep the new state staged for a next select of the same particle
-                    ws.acc[4][lane] = t2.x;
-                    ws.acc[5][lane] = t2.y;
-                    ws.acc[6][lane] = t2.c;
-                    ws.acc[7][lane] = t2.s;
+                    ws.acc[0][lane] = t2.x;
+                    ws.acc[1][lane] = t2.y;
+                    ws.acc[2][lane] = t2.c;
+                    ws.acc[3][lane] = t2.s;
                     eA_prev = eA;
                     // cell origins i * w of the relative coordinates (as in k_place)
                     const double shx = dv.shift[3 * r], shy = dv.shift[3 * r + 1];
