@@ -281,39 +281,38 @@ k_set2d_direct(Dev dv, Shape2 sh, int nxt, int sigma, const uint32_t* __restrict
             // mask, the next candidate's data loaded one trip ahead
             const uint32_t trips = __reduce_max_sync(FULL, Tn);
             uint32_t m_left = mask;
-            int kc = 0;
             uint32_t ec = 0, eend = 0;
+            float oxc = 0.f, oyc = 0.f;                    // FP32 offset of the cursor's cell
             float4 fc = make_float4(0.f, 0.f, 0.f, 0.f);
-            if (Tn) {
-                kc = __ffs(m_left) - 1;
+            // the cell the cursor enters next: its range and offset
+            auto enter = [&]() {
+                const int kq = __ffs(m_left) - 1;
                 m_left &= m_left - 1u;
-                ec = ws.sb[kc][lane];
-                eend = ec + ws.sn[kc][lane];
+                ec = ws.sb[kq][lane];
+                eend = ec + ws.sn[kq][lane];
+                const int qy = (kq * 11) >> 5;             // kq / 3 for kq < 9
+                const int qx = kq - 3 * qy;
+                oxc = qx == 0 ? -wx : (qx == 2 ? wx : 0.f);
+                oyc = qy == 0 ? -wy : (qy == 2 ? wy : 0.f);
+            };
+            if (Tn) {
+                enter();
                 fc = B.f4a[ec];
             }
 #pragma unroll 1
             for (uint32_t i = 0; i < trips; ++i) {
                 const bool live = i < Tn && !ov;
                 const uint32_t e = ec;
-                const int kq = kc;
+                const float offx = oxc, offy = oyc;
                 const float4 f = fc;
                 if (live && i + 1 < Tn) {                  // advance and prefetch
                     ec += 1u;
-                    if (ec == eend) {
-                        kc = __ffs(m_left) - 1;
-                        m_left &= m_left - 1u;
-                        ec = ws.sb[kc][lane];
-                        eend = ec + ws.sn[kc][lane];
-                    }
+                    if (ec == eend) enter();
                     fc = B.f4a[ec];
                 }
                 bool keep = false;
                 float dlx = 0.f, dly = 0.f;
                 if (live && e != eA) {
-                    const int qy = (kq * 11) >> 5;         // kq / 3 for kq < 9
-                    const int qx = kq - 3 * qy;
-                    const float offx = qx == 0 ? -wx : (qx == 2 ? wx : 0.f);
-                    const float offy = qy == 0 ? -wy : (qy == 2 ? wy : 0.f);
                     dlx = __fsub_rn(__fadd_rn(f.x, offx), tr.x);
                     dly = __fsub_rn(__fadd_rn(f.y, offy), tr.y);
                     const float q32 = __fmaf_rn(dlx, dlx, __fmul_rn(dly, dly));
