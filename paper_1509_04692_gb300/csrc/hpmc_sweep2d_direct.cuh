@@ -9,7 +9,7 @@
 // FP32 mirror of each neighbour straight from the cell-sorted buffer (the
 // stencils of the 32 cells of a warp overlap, so most reads hit L1), and
 // culls by circumsphere.  Survivors of all lanes go to a warp-wide pair queue
-// (ballot compaction) that the warp drains 32 pairs at a time, one
+// (ballot compaction) that the warp drains once the cull is done, 32 pairs at a time, one
 // separating-axis test per lane, skipping pairs of moves already known to
 // overlap (the early exit of Sec. 2.1).
 //
@@ -34,7 +34,7 @@
 namespace hpmc {
 
 struct __align__(16) Direct2Warp {
-    static constexpr int QCAP = 64;
+    static constexpr int QCAP = 192;
     uint32_t wd[6][32];               // Philox words r1..r6 of each lane's select
     double acc[4][32];                // the moving particle's FP64 x, y, c, s (asynchronous copies)
     float2 qd[QCAP];                  // queued Delta32 (B relative to the trial)
@@ -99,6 +99,45 @@ __device__ __noinline__ bool direct_overlap64(const Shape2& sh, const Rep& rp, c
     const double Dx = min_image(B.px[gB] - t2.x, rp.L[0], rp.halfL[0]);
     const double Dy = min_image(B.py[gB] - t2.y, rp.L[1], rp.halfL[1]);
     return overlap2d64<NV>(sh, Dx, Dy, t2.c, t2.s, B.q0[gB], B.q1[gB]);
+}
+
+// One round of the pair queue: the np entries [base, base + np), one per lane,
+// each a certified FP32 separating-axis test (the FP64 contract when the
+// FP32 verdict is not certified); a pair whose owner already overlaps is
+// skipped.  Adds the tests run and the FP64 re-checks to chk, rechk.
+template <int NV>
+__device__ __forceinline__ void direct_drain_round(Direct2Warp& ws, int lane, int base, int np, const Shape2& sh,
+                                                   const Rep& rp, const Bufs& B, unsigned& chk, unsigned& rechk)
+{
+    if (lane < np) {
+        const int p = base + lane;
+        const int g2 = ws.qg[p];
+        if (!((ws.ovmask >> g2) & 1u)) {
+            chk += 1;
+            const float2 d2 = ws.qd[p], zb = ws.qz[p], za = ws.tz[g2];
+            const int v = sat32<NV>(sh, rp.sat_e, d2.x, d2.y, za.x, za.y, zb.x, zb.y);
+            bool pov = v == 1;
+            if (v == 2) {
+                rechk += 1;
+                const uint32_t w[6] = { ws.wd[0][g2], ws.wd[1][g2], ws.wd[2][g2],
+                                        ws.wd[3][g2], ws.wd[4][g2], ws.wd[5][g2] };
+                pov = direct_overlap64<NV>(sh, rp, B, w, ws.ea[g2], ws.qe[p]);
+            }
+            if (pov) atomicOr(&ws.ovmask, 1u << g2);
+        }
+    }
+    __syncwarp();
+}
+
+// the same round out of line, for a queue about to overflow inside the cull
+// loop (rare): the loop then carries no separating-axis registers
+template <int NV>
+__device__ __noinline__ uint2 direct_drain_round_out(Direct2Warp& ws, int lane, int base, int np, const Shape2& sh,
+                                                     const Rep& rp, const Bufs& B)
+{
+    unsigned chk = 0, rechk = 0;
+    direct_drain_round<NV>(ws, lane, base, np, sh, rp, B, chk, rechk);
+    return make_uint2(chk, rechk);
 }
 
 template <int NV>
@@ -242,40 +281,6 @@ k_set2d_direct(Dev dv, Shape2 sh, int nxt, int sigma, const uint32_t* __restrict
             bool ov = false;                               // this lane's move overlaps
             int qn = 0;
 
-            // drain np queued pairs, one separating-axis test per lane
-            auto drain = [&](int np) {
-                if (lane < np) {
-                    const int g2 = ws.qg[lane];
-                    if (!((ws.ovmask >> g2) & 1u)) {
-                        c_chk += 1;
-                        const float2 d2 = ws.qd[lane], zb = ws.qz[lane], za = ws.tz[g2];
-                        const int v = sat32<NV>(sh, rp.sat_e, d2.x, d2.y, za.x, za.y, zb.x, zb.y);
-                        bool pov = v == 1;
-                        if (v == 2) {
-                            // not certified: the FP64 contract on the owner's trial
-                            c_rechk += 1;
-                            const uint32_t w[6] = { ws.wd[0][g2], ws.wd[1][g2], ws.wd[2][g2],
-                                                    ws.wd[3][g2], ws.wd[4][g2], ws.wd[5][g2] };
-                            pov = direct_overlap64<NV>(sh, rp, B, w, ws.ea[g2], ws.qe[lane]);
-                        }
-                        if (pov) atomicOr(&ws.ovmask, 1u << g2);
-                    }
-                }
-                __syncwarp();
-                // the unprocessed tail to the front
-                const int rest = qn - np;
-                float2 td = make_float2(0.f, 0.f), tz = make_float2(0.f, 0.f);
-                uint32_t te = 0;
-                uint8_t tg = 0;
-                if (lane < rest) {
-                    td = ws.qd[np + lane]; tz = ws.qz[np + lane]; te = ws.qe[np + lane]; tg = ws.qg[np + lane];
-                }
-                __syncwarp();
-                if (lane < rest) { ws.qd[lane] = td; ws.qz[lane] = tz; ws.qe[lane] = te; ws.qg[lane] = tg; }
-                qn = rest;
-                ov = ov || ((ws.ovmask >> lane) & 1u);
-                __syncwarp();
-            };
 
             // ---- cull: a cursor over the lane's candidates, cell by cell of its
             // mask, the next candidate's data loaded one trip ahead
@@ -341,15 +346,24 @@ k_set2d_direct(Dev dv, Shape2 sh, int nxt, int sigma, const uint32_t* __restrict
                     ws.qg[p] = (uint8_t)lane;
                 }
                 qn += __popc(bal);
-                if (qn >= 32) {
+                if (qn > W::QCAP - 32) {                   // room for one more trip's survivors
                     __syncwarp();
-                    drain(32);
+                    const uint2 cr = direct_drain_round_out<NV>(ws, lane, qn - 32, 32, sh, rp, B);
+                    c_chk += cr.x;
+                    c_rechk += cr.y;
+                    qn -= 32;
+                    ov = ov || ((ws.ovmask >> lane) & 1u);
                 }
             }
+            // ---- separating-axis tests of the queued pairs, 32 at a time
+            __syncwarp();
             while (qn > 0) {
-                __syncwarp();
-                drain(min(qn, 32));
+                const int np = min(qn, 32);
+                direct_drain_round<NV>(ws, lane, qn - np, np, sh, rp, B, c_chk, c_rechk);
+                qn -= np;
             }
+            ov = ov || ((ws.ovmask >> lane) & 1u);
+            __syncwarp();
 
             // ---- accept or reject
             eA_prev = 0xffffffffu;
