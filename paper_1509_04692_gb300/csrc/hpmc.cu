@@ -284,6 +284,20 @@ int rep_geometry(const hpmc_batch* h, const HostRep& hr, Rep& rp)
         rp.reach_lo[a] = f32_up(reach);
         rp.reach_hi[a] = f32_down(rp.w[a] - reach);
     }
+    // FP32 cell rule of the rebuild: x and s truncated to FP32 (relative
+    // error below 2^-23), y32 = x32 - s32 (+ L32), t32 = y32 * inv_w32 (each
+    // rounding 2^-24 of its magnitude; L32 and inv_w32 within 2^-24).  Then
+    // |y32 - (x - s)| < (2^-23 + 2^-24) L + 2^-23 w before the wrap, and
+    // |t32 - t64| < 7 2^-24 nc + 2^-23 in cells, t64 the contract's product
+    // (within 3 u64 nc of the exact one).  Both bounds are doubled.
+    for (int a = 0; a < 3; ++a) {
+        rp.L32[a] = (float)rp.L[a];
+        rp.inv_w32[a] = (float)rp.inv_w[a];
+        const double ey = (0x1.0p-23 + 0x1.0p-24) * rp.L[a] + 0x1.0p-23 * rp.w[a] + 0x1.0p-126;
+        const double et = 7.0 * 0x1.0p-24 * (double)rp.nc[a] + 0x1.0p-23 + 3.0 * kU64 * (double)rp.nc[a];
+        rp.cell_ey[a] = f32_up(2.0 * ey);
+        rp.cell_et[a] = f32_up(2.0 * et);
+    }
     rp.sat_e = f32_up(g.e_sat);
     rp.e_dlt32 = f32_up(g.e_dlt);
     rp.e_ori32 = f32_up(g.e_ori);

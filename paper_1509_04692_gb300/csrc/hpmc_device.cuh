@@ -139,14 +139,6 @@ __device__ __forceinline__ double min_image(double d, double L, double halfL)
     return d;
 }
 
-// relative coordinate of x inside cell i (FP64 difference, cast later)
-__device__ __forceinline__ double rel_in_cell(double x, double s, double L, double w, int i)
-{
-    double y = x - s;
-    if (y < 0.0) y = y + L;
-    return y - (double)i * w;
-}
-
 // ------------------------------------------------- contract: trial moves
 // 2D translation + Cayley rotation from the words r1..r6 of a select.
 struct Trial2 { double x, y, c, s; };

@@ -53,6 +53,37 @@ __device__ __forceinline__ uint32_t local_cell(const Dev& dv, const Rep& rp, con
     return (uint32_t)ix + (uint32_t)rp.nc[0] * ((uint32_t)iy + (uint32_t)rp.nc[1] * (uint32_t)iz);
 }
 
+// A non-negative double truncated to FP32 from its bit pattern (integer
+// operations only: on this GPU every FP64 instruction, conversions included,
+// takes the slow FP64 pipe).  Relative error below 2^-23; values below 2^-126
+// give 0.  A negative zero reads as zero.
+__device__ __forceinline__ float f32_trunc_nonneg(double x)
+{
+    const uint32_t hi = (uint32_t)__double2hiint(x) & 0x7fffffffu, lo = (uint32_t)__double2loint(x);
+    const int e = (int)(hi >> 20) - 1023 + 127;
+    if (e <= 0) return 0.0f;
+    return __uint_as_float(((uint32_t)e << 23) | ((hi & 0xfffffu) << 3) | (lo >> 29));
+}
+
+// The contract's cell index on axis a (cell_axis: y = x - s, + L when
+// negative, truncation of y * inv_w, clamp to nc - 1) evaluated in FP32:
+// the result is certified when the FP32 y is farther than cell_ey from 0 and
+// the FP32 product farther than cell_et from the nearest integer (the
+// bounds of the FP32 error, see the host's derivation); otherwise -1, and
+// the caller takes the FP64 rule.
+__device__ __forceinline__ int cell_axis_f32(const Rep& rp, int a, double x, float s32)
+{
+    float y = __fsub_rn(f32_trunc_nonneg(x), s32);
+    if (!(fabsf(y) > rp.cell_ey[a])) return -1;
+    if (y < 0.0f) y = __fadd_rn(y, rp.L32[a]);
+    const float t = __fmul_rn(y, rp.inv_w32[a]);
+    const float fi = floorf(t);
+    const float fr = t - fi;                       // exact
+    const float et = rp.cell_et[a];
+    if (!(fr > et && fr < 1.0f - et)) return -1;
+    return min((int)fi, rp.nc[a] - 1);
+}
+
 // Cell of every particle of buffer `cur` and its arrival slot in the cell.
 __global__ void k_count(Dev dv, int cur)
 {
@@ -61,7 +92,15 @@ __global__ void k_count(Dev dv, int cur)
     if (i >= dv.ntot) return;
     const uint32_t r = dv.rep_of[i];
     const Rep& rp = dv.reps[r];
-    const uint32_t c = rp.cbase + local_cell(dv, rp, dv.buf[cur], i, dv.shift + 3 * r);
+    const Bufs& S = dv.buf[cur];
+    const double* sh = dv.shift + 3 * r;
+    uint32_t lc;
+    // the FP32 rule first (2D); the FP64 rule where it is not certified
+    const int ix = dv.dim == 2 ? cell_axis_f32(rp, 0, S.px[i], f32_trunc_nonneg(sh[0])) : -1;
+    const int iy = ix >= 0 ? cell_axis_f32(rp, 1, S.py[i], f32_trunc_nonneg(sh[1])) : -1;
+    if (iy >= 0) lc = (uint32_t)ix + (uint32_t)rp.nc[0] * (uint32_t)iy;
+    else lc = local_cell(dv, rp, S, i, sh);
+    const uint32_t c = rp.cbase + lc;
     dv.cellid[i] = c;
     dv.slot[i] = atomicAdd(dv.count + c, 1u);
 }
@@ -172,6 +211,32 @@ __global__ void k_scatter_tags(Dev dv, int cur)
     dv.tmp_tag[dv.start[dv.cellid[i]] + dv.slot[i]] = dv.buf[cur].tag[i];
 }
 
+// A finite double rounded to FP32, to nearest with ties to even, from its bit
+// pattern (integer operations only, the FP64 pipe being slow on this GPU):
+// the same value as the hardware conversion for results in the normal FP32
+// range; magnitudes below 2^-126 give a zero of the same sign.
+__device__ __forceinline__ float f32_rn_bits(double x)
+{
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    const uint32_t sign = (uint32_t)(b >> 32) & 0x80000000u;
+    const int e = (int)((b >> 52) & 0x7ffu) - 1023 + 127;
+    if (e <= 0) return __uint_as_float(sign);
+    const uint32_t mant = (uint32_t)((b >> 29) & 0x7fffffu);
+    const uint32_t rest = (uint32_t)(b & 0x1fffffffu);
+    uint32_t r = ((uint32_t)e << 23) | mant;
+    if (rest > 0x10000000u || (rest == 0x10000000u && (mant & 1u))) r += 1u;   // a carry raises the exponent
+    return __uint_as_float(sign | r);
+}
+
+// FP32 mirror coordinate of x in cell i of an axis: rel = (x - s, + L when
+// negative) - i w with the product and difference in one fused multiply-add,
+// then rounded to FP32 (within the certified bound of the mirror: a few FP64
+// roundings of magnitude L, then the cast).
+__device__ __forceinline__ float mirror_rel(double x, double s, double L, double w, int i)
+{
+    return f32_rn_bits(__fma_rn(-(double)i, w, cell_coord_bits(x, s, L)));
+}
+
 // Gather of particle i (tag t) of replica r, cell c, into slot o of buffer
 // cur ^ 1, with the FP32 mirror (cell-relative coordinate, orientation).
 __device__ __forceinline__ void place_at(const Dev& dv, int cur, uint32_t i, uint32_t t, uint32_t r, uint32_t c,
@@ -187,22 +252,22 @@ __device__ __forceinline__ void place_at(const Dev& dv, int cur, uint32_t i, uin
     D.px[o] = x;
     D.py[o] = y;
     D.tag[o] = t;
-    const float rx = (float)rel_in_cell(x, dv.shift[3 * r], rp.L[0], rp.w[0], ix);
-    const float ry = (float)rel_in_cell(y, dv.shift[3 * r + 1], rp.L[1], rp.w[1], iy);
+    const float rx = mirror_rel(x, dv.shift[3 * r], rp.L[0], rp.w[0], ix);
+    const float ry = mirror_rel(y, dv.shift[3 * r + 1], rp.L[1], rp.w[1], iy);
     if (dv.dim == 2) {
         const double c0 = S.q0[i], s0 = S.q1[i];
         D.q0[o] = c0;
         D.q1[o] = s0;
-        D.f4a[o] = make_float4(rx, ry, (float)c0, (float)s0);
+        D.f4a[o] = make_float4(rx, ry, f32_rn_bits(c0), f32_rn_bits(s0));
     } else {
         const int iz = (int)(lc / ((uint32_t)rp.nc[0] * (uint32_t)rp.nc[1]));
         const double z = S.pz[i];
         D.pz[o] = z;
-        const float rz = (float)rel_in_cell(z, dv.shift[3 * r + 2], rp.L[2], rp.w[2], iz);
+        const float rz = mirror_rel(z, dv.shift[3 * r + 2], rp.L[2], rp.w[2], iz);
         const double w0 = S.q0[i], w1 = S.q1[i], w2 = S.q2[i], w3 = S.q3[i];
         D.q0[o] = w0; D.q1[o] = w1; D.q2[o] = w2; D.q3[o] = w3;
-        D.f4a[o] = make_float4(rx, ry, rz, (float)w0);
-        D.f4b[o] = make_float4((float)w1, (float)w2, (float)w3, 0.0f);
+        D.f4a[o] = make_float4(rx, ry, rz, f32_rn_bits(w0));
+        D.f4b[o] = make_float4(f32_rn_bits(w1), f32_rn_bits(w2), f32_rn_bits(w3), 0.0f);
     }
 }
 

@@ -70,6 +70,10 @@ struct Rep {
     float ins32;             // |D32|^2 < ins32 -> certain overlap (inscribed balls meet)
     float reach_lo[3];       // trial rel' > reach_lo[a]: the lower neighbour layer on axis a is beyond the cull
     float reach_hi[3];       // trial rel' < reach_hi[a]: the upper neighbour layer is beyond the cull
+    // FP32 cell rule of the rebuild (certified; see cell_axis_f32)
+    float L32[3], inv_w32[3];
+    float cell_ey[3];        // bound on |y32 - (x - s)| (the sign test)
+    float cell_et[3];        // bound on |t32 - t64| in cells (the boundary test)
     double ins64;            // the same test on the FP64 |D|^2
     double e_in, e_cull, e_sat;  // the same margins in FP64 (reporting)
 };
