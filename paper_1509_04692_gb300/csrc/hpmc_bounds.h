@@ -111,6 +111,64 @@ inline double sat2_margin(const Margins& g, double R, double vm, double nm, doub
     return 2.0 * (e32 + e64);
 }
 
+// rot(q, x) as the 3D kernels evaluate it in FP32 (t = 2 q_v x x, o = (x +
+// w t) + q_v x t), |x|_2 <= X, component errors ex, quaternion component
+// errors eq, per-rounding unit u: bound on the output components' error.
+inline double rot3_err(double X, double ex, double eq, double u)
+{
+    const double e_cross1 = 2.0 * (ex + X * eq + ex * eq) + 3.0 * u * X;   // q_v x x, per component
+    const double et = 2.0 * e_cross1;                                      // times 2 (exact)
+    const double T = 2.0 * X * 1.000001;
+    const double e_wt = et + T * eq + et * eq + u * T;                     // w t
+    const double e_s1 = ex + e_wt + u * 3.0 * X;                           // x + w t
+    const double e_cross2 = 2.0 * (et + T * eq + et * eq) + 3.0 * u * T;   // q_v x t
+    return e_s1 + e_cross2 + u * 5.0 * X;
+}
+
+// 3D boxes (half extents h): margins of the certified separating-axis test
+// (box32_sat).  The FP32 test sees l = rot(conj(qA), Delta) with per-component
+// error e_l and B's axes M (the closed-form rotation matrix of qr = conj(qA)
+// qB) with per-entry error e_u.  Along one of its axes n (the FP32 vector) it
+// computes s = |l.n| - sum_k h_k |n_k| - extent_B, extent_B from M's
+// orthonormal identities.  E_sep bounds |s - s*(n)|, s*(n) the same quantity
+// for the exact boxes along the same n; E_ov adds |s*(n) - s*(n*)| for the
+// exact candidate axis n* the FP32 n stands for (|n - n*|_1 <= 3 e_u, times
+// the Lipschitz constant of s* in the 1-norm).  Returned, doubled, with:
+//   sep = 2 E_sep + 4e-6 2R |n|_2: s > sep leaves the exact boxes more than
+//         4e-6 2R apart along n, far outside the zone near contact where the
+//         FP64 GJK may answer overlap for separated shapes;
+//   ov  = 2 E_ov + tau |n|_2: -s > ov on all 15 axes gives every exact
+//         candidate axis an overlap deeper than tau, so the exact boxes
+//         intersect at depth > tau, where the FP64 GJK answers overlap.
+struct BoxMargins {
+    double sep, ov;
+};
+
+inline BoxMargins box_sat_margins(const Margins& g, double R, const double h[3], double tau)
+{
+    const double u = kU32 * 1.0001;
+    const double r3 = std::sqrt(3.0);
+    const double ea = g.e_ori, eb = kU32 * 1.000001 + 1e-15;   // quaternion component errors
+    const double e_qr = 2.0 * (ea + eb) + 2.0 * ea * eb + 4.0 * u * 1.000001;
+    const double X_D = 2.0 * R * (1.0 + 1e-9) + 2.0 * g.e_dlt;          // |Delta| of a culled pair
+    const double e_l = rot3_err(X_D, g.e_dlt, ea, u);
+    // entries 2(ab +- cd) and 1 - 2(a^2 + b^2) of components within e_qr
+    const double e_u = 8.0 * e_qr * (1.0 + e_qr) + 8.0 * u;
+    const double e64 = 1e-12;       // the FP64 quaternions' departure from a rotation (~1e-15)
+    const double N1 = r3 * (1.0 + 2.0 * e_u);                           // |n|_1 of any axis
+    const double N2 = 1.0 + 2.0 * e_u;                                  // |n|_2 of any axis
+    const double Lm = (X_D + r3 * e_l) * N2;                            // |l.n|
+    const double hsum = h[0] + h[1] + h[2];
+    const double hmax = std::max(h[0], std::max(h[1], h[2]));
+    const double e_c = N1 * e_l + 3.0 * u * Lm;                         // l.n
+    const double e_A = 4.01 * u * hmax * N1;                            // sum h_k |n_k|, h rounded to FP32
+    const double e_B = hsum * ((1.0 + r3) * e_u * 1.001 + e64 + 5.0 * u * (1.0 + e_u));
+    const double e_s = 2.0 * u * (Lm + 2.0 * hsum * N2) * 1.001;        // the two subtractions
+    const double E_sep = e_c + e_A + e_B + e_s;
+    const double E_ov = E_sep + (X_D + hmax + hsum) * 3.0 * (e_u + e64) * 1.001;
+    return { 2.0 * E_sep + 4e-6 * 2.0 * R * N2, 2.0 * E_ov + tau * N2 };
+}
+
 // 3D: bound on |pb32 - pb| per component for B's vertices moved into A's
 // frame (qr = conj(qA) qB, l = rot(conj(qA), Delta), pb = rot(qr, v) + l),
 // where pb is the exact transform of the FP64 contract's inputs and pb32 the
@@ -125,18 +183,7 @@ inline double gjk3_vertex_margin(const Margins& g, double R, double vm)
     // qr = conj(qA) qB: each component a signed sum of four products with
     // sum |a_i b_j| <= |a| |b| <= 1 (plus slack); sum |a_i| <= 2 for unit a
     const double e_qr = 2.0 * (ea + eb) + 2.0 * ea * eb + 4.0 * u * 1.000001;
-    // rot(q, x) for |x|_2 <= X, component errors ex, quaternion errors eq:
-    // t = 2 q_v x x (|t| <= 2X); o = (x + w t) + q_v x t (|o| <= 5X before the
-    // cancellations of an exact rotation)
-    auto rot_err = [&](double X, double ex, double eq) {
-        const double e_cross1 = 2.0 * (ex + X * eq + ex * eq) + 3.0 * u * X;   // q_v x x, per component
-        const double et = 2.0 * e_cross1;                                      // times 2 (exact)
-        const double T = 2.0 * X * 1.000001;
-        const double e_wt = et + T * eq + et * eq + u * T;                     // w t
-        const double e_s1 = ex + e_wt + u * 3.0 * X;                           // x + w t
-        const double e_cross2 = 2.0 * (et + T * eq + et * eq) + 3.0 * u * T;   // q_v x t
-        return e_s1 + e_cross2 + u * 5.0 * X;
-    };
+    auto rot_err = [&](double X, double ex, double eq) { return rot3_err(X, ex, eq, u); };
     const double X_D = 2.0 * R * (1.0 + 1e-9) + 2.0 * g.e_dlt;
     const double e_l = rot_err(X_D, g.e_dlt, ea);
     const double X_v = std::sqrt(3.0) * vm;

@@ -93,6 +93,27 @@ inline int build_shapes(int dim, const double* verts, uint32_t nv, Shape2& s2, S
             }
         s.rc2 = rc2;
         s.frc2 = (float)rc2;
+        // a box centred on the origin and aligned with the local axes: every
+        // vertex is (+-h0, +-h1, +-h2) and all 8 sign patterns occur
+        if (nv == 8) {
+            double h[3] = { 0.0, 0.0, 0.0 };
+            for (uint32_t k = 0; k < 8; ++k)
+                for (int a = 0; a < 3; ++a) h[a] = std::fmax(h[a], std::fabs(s.v[k][a]));
+            unsigned seen = 0;
+            bool ok = h[0] > 0.0 && h[1] > 0.0 && h[2] > 0.0;
+            for (uint32_t k = 0; k < 8 && ok; ++k) {
+                unsigned pat = 0;
+                for (int a = 0; a < 3; ++a) {
+                    if (std::fabs(s.v[k][a]) != h[a]) ok = false;
+                    if (s.v[k][a] > 0.0) pat |= 1u << a;
+                }
+                seen |= 1u << pat;
+            }
+            if (ok && seen == 0xffu) {
+                s.box = 1;
+                for (int a = 0; a < 3; ++a) s.bh[a] = (float)h[a];
+            }
+        }
     }
     return 0;
 }

@@ -482,10 +482,14 @@ k_set3d(Dev dv, const __grid_constant__ Shape3 sh, int nxt, int sigma, const uin
                                     const float4 d2 = ws.qd[lane];
                                     const float4 a1 = ws.tra[g2], a2 = ws.trb[g2];
                                     const float4 b1 = ws.ea[e2], b2 = ws.eb[e2];
-                                    const int v = gjk32_cert<NV>(sh, d2.x, d2.y, d2.z,
-                                                                 make_float4(a1.w, a2.x, a2.y, a2.z),
-                                                                 make_float4(b1.w, b2.x, b2.y, b2.z), rp.e_pb32,
-                                                                 rp.e_va32, rp.tau3);
+                                    const float4 qa = make_float4(a1.w, a2.x, a2.y, a2.z);
+                                    const float4 qb = make_float4(b1.w, b2.x, b2.y, b2.z);
+                                    int v;
+                                    if ((NV == 8 || NV == 0) && sh.box)
+                                        v = box32_sat(sh, d2.x, d2.y, d2.z, qa, qb, rp.box_esep, rp.box_eov);
+                                    else
+                                        v = gjk32_cert<NV>(sh, d2.x, d2.y, d2.z, qa, qb, rp.e_pb32, rp.e_va32,
+                                                           rp.tau3);
                                     need64 = v >= GJK32_UNCERTAIN;
                                     ov = (v == GJK32_OVERLAP);
                                 } else {

@@ -74,6 +74,8 @@ struct Rep {
     float L32[3], inv_w32[3];
     float cell_ey[3];        // bound on |y32 - (x - s)| (the sign test)
     float cell_et[3];        // bound on |t32 - t64| in cells (the boundary test)
+    float box_esep;          // 3D boxes: a separating-axis gap above this certifies separation
+    float box_eov;           // 3D boxes: overlaps above this on all 15 axes certify overlap
     double ins64;            // the same test on the FP64 |D|^2
     double e_in, e_cull, e_sat;  // the same margins in FP64 (reporting)
 };
@@ -94,6 +96,8 @@ struct Shape2 {
 struct Shape3 {
     int nv;
     int round;               // 1: hard sphere (nv = 0), overlap iff |D|^2 <= rc2
+    int box;                 // 1: the 8 vertices are (+-h0, +-h1, +-h2), a box centred on the origin
+    float bh[3];             // its half extents (FP32)
     double v[kMaxV3][3];
     float fv[kMaxV3][3];
     double rc2;

@@ -30,8 +30,9 @@ __global__ void k_pairs2d(Shape2 sh, float E, uint32_t n, const double* D, const
     o32[i] = v == 1 ? 1 : (v == 0 ? 0 : 2);
 }
 
-__global__ void k_pairs3d(const __grid_constant__ Shape3 sh, float e_pb, float e_va, float tau, uint32_t n, const double* D,
-                          const double* qA, const double* qB, int32_t* o64, int32_t* o32)
+__global__ void k_pairs3d(const __grid_constant__ Shape3 sh, float e_pb, float e_va, float tau, float box_sep,
+                          float box_ov, uint32_t n, const double* D, const double* qA, const double* qB, int32_t* o64,
+                          int32_t* o32)
 {
     const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
@@ -43,7 +44,8 @@ __global__ void k_pairs3d(const __grid_constant__ Shape3 sh, float e_pb, float e
     if (sh.round) { o32[i] = 2; return; }            // spheres: the set kernels' cull decides
     const float4 fa = make_float4((float)a[0], (float)a[1], (float)a[2], (float)a[3]);
     const float4 fb = make_float4((float)b[0], (float)b[1], (float)b[2], (float)b[3]);
-    const int v = gjk32_cert<0>(sh, (float)d[0], (float)d[1], (float)d[2], fa, fb, e_pb, e_va, tau);
+    const int v = sh.box ? box32_sat(sh, (float)d[0], (float)d[1], (float)d[2], fa, fb, box_sep, box_ov)
+                         : gjk32_cert<0>(sh, (float)d[0], (float)d[1], (float)d[2], fa, fb, e_pb, e_va, tau);
     o32[i] = v;   // 0, 1, or the reason it is uncertain (>= 2)
 }
 
@@ -118,8 +120,19 @@ extern "C" int hpmc_pair_test(int dim, const double* verts, uint32_t nv, uint32_
             k_pairs2d<<<(n + T - 1) / T, T>>>(s2, E, n, dD, dA, dB, d64, d32);
         } else {
             const float epb = up32(gjk3_vertex_margin(g, Rc, vm));
-            k_pairs3d<<<(n + T - 1) / T, T>>>(s3, epb, up32(2.0 * kU32 * vm), up32(1e-9 * 2.0 * Rc), n, dD, dA,
-                                              dB, d64, d32);
+            const float tau = up32(1e-9 * 2.0 * Rc);
+            // the box margins assume |D| <= 2R: here R covers the longest D
+            // given (the sweeps only test pairs their cull keeps)
+            double dm = 0.0;
+            for (uint32_t i = 0; i < n; ++i)
+                dm = std::fmax(dm, std::sqrt(D[3 * i] * D[3 * i] + D[3 * i + 1] * D[3 * i + 1] + D[3 * i + 2] * D[3 * i + 2]));
+            const double Rb = std::fmax(Rc, 0.5 * dm * (1.0 + 1e-6));
+            Margins gb = g;
+            gb.e_dlt = kU32 * 2.0 * Rb * 1.01;
+            const double bh[3] = { std::fabs(s3.v[0][0]), std::fabs(s3.v[0][1]), std::fabs(s3.v[0][2]) };
+            const BoxMargins bm = box_sat_margins(gb, Rb, bh, (double)tau);
+            k_pairs3d<<<(n + T - 1) / T, T>>>(s3, epb, up32(2.0 * kU32 * vm), tau, up32(bm.sep), up32(bm.ov), n, dD,
+                                              dA, dB, d64, d32);
         }
         e = cudaGetLastError();
     }
