@@ -523,6 +523,8 @@ def run_profile(args):
         b = hpmc.from_systems(inputs.replica_systems(512))
     elif args.profile_workload == "cubes":
         b = hpmc.from_system(inputs.cubes32768(42))
+    elif args.profile_workload == "batched_cubes":
+        b = hpmc.from_systems(inputs.cube_replica_systems())
     elif args.profile_workload == "dodecahedra":
         b = hpmc.from_system(inputs.dodecahedra32000(42))
     elif args.profile_workload == "large2d":
@@ -711,7 +713,7 @@ def main():
     ap.add_argument("--profile-sweeps", type=int, default=0,
                     help="run the small ncu case instead of the benchmark")
     ap.add_argument("--profile-workload", default="fluid4096",
-                    choices=["fluid4096", "batched", "cubes", "dodecahedra", "large2d"])
+                    choices=["fluid4096", "batched", "cubes", "batched_cubes", "dodecahedra", "large2d"])
     ap.add_argument("--profile-fp64", action="store_true")
     ap.add_argument("--profile-n", type=int, default=0, help="N of the large2d profile case")
     ap.add_argument("--profile-melt", type=int, default=20, help="graph-replayed sweeps before profiling")

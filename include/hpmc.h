@@ -394,6 +394,19 @@ int hpmc_pair_test(int dim, const double* verts, uint32_t nv, uint32_t n, const 
 int hpmc_pair_test_warp3d(const double* verts, uint32_t nv, uint32_t n, const double* D, const double* qA,
                           const double* qB, int32_t* out64, int32_t* iters);
 
+/*
+ * hpmc_pair_test_box64 -- the FP64 separating-axis certificate the
+ * FP32-filtered 3D sweep applies to box pairs (vertices (+-h0, +-h1, +-h2))
+ * before re-deciding them with the FP64 GJK of the contract (Sec. 2.3 /
+ * Eq. 2): one warp per pair.  Inputs as hpmc_pair_test with dim = 3; out[n]
+ * receives 0 (certified separated: the boxes are more than 4e-6 of the
+ * circumdiameter apart), 1 (certified overlap: deeper than 1e-9 of it) or 2
+ * (left to the GJK).  INVALID_ARG when the shape is not such a box.  For
+ * validation; synchronous; allocates and frees its own device buffers.
+ */
+int hpmc_pair_test_box64(const double* verts, uint32_t nv, uint32_t n, const double* D, const double* qA,
+                         const double* qB, int32_t* out);
+
 /* Geometry of replica r: cells per axis, cell width, circumradius. */
 int hpmc_geometry(hpmc_t h, int32_t r, int32_t* nc, double* w, double* R);
 

@@ -255,11 +255,15 @@ int rep_geometry(const hpmc_batch* h, const HostRep& hr, Rep& rp)
     // the size) where the FP64 GJK may conservatively answer overlap.
     rp.tau3 = f32_up(1e-9 * 2.0 * h->Rc);
     rp.box_esep = rp.box_eov = 0.0f;
+    rp.box_sep64 = rp.box_ov64 = 0.0;
     if (h->dim == 3 && h->sh3.box) {
         const double bh[3] = { std::fabs(h->sh3.v[0][0]), std::fabs(h->sh3.v[0][1]), std::fabs(h->sh3.v[0][2]) };
         const BoxMargins bm = box_sat_margins(g, h->Rc, bh, (double)rp.tau3);
         rp.box_esep = f32_up(bm.sep);
         rp.box_eov = f32_up(bm.ov);
+        const BoxMargins b64 = box_sat_margins64(h->Rc, bh, (double)rp.tau3);
+        rp.box_sep64 = b64.sep;
+        rp.box_ov64 = b64.ov;
     }
     rp.in_lo = f32_up(g.e_in);
     rp.out_lo = f32_down(-g.e_in);

@@ -169,6 +169,35 @@ inline BoxMargins box_sat_margins(const Margins& g, double R, const double h[3],
     return { 2.0 * E_sep + 4e-6 * 2.0 * R * N2, 2.0 * E_ov + tau * N2 };
 }
 
+// The same test in FP64 (box64_sat_warp) on the FP64 contract's inputs
+// themselves: only its own roundings (unit u64) separate its values from the
+// exact ones, plus the departure of the FP64 quaternions from unit length
+// (~1e-15, taken as 1e-12) in the face normals of B.  Returned like
+// box_sat_margins: sep = 2 E + 4e-6 2R |n|_2, ov = 2 (E + Lipschitz term) +
+// tau |n|_2; both are the floors to within ~1e-11 of the size.
+inline BoxMargins box_sat_margins64(double R, const double h[3], double tau)
+{
+    const double u = kU64 * 1.01;
+    const double r3 = std::sqrt(3.0);
+    const double e_qr = 4.0 * u * 1.000001;
+    const double X_D = 2.0 * R * (1.0 + 1e-9);
+    const double e_l = rot3_err(X_D, 0.0, 0.0, u);
+    const double e_u = 8.0 * e_qr * (1.0 + e_qr) + 8.0 * u;
+    const double e64 = 1e-12;
+    const double N1 = r3 * (1.0 + 2.0 * e_u + e64);
+    const double N2 = 1.0 + 2.0 * e_u + e64;
+    const double Lm = (X_D + r3 * e_l) * N2;
+    const double hsum = h[0] + h[1] + h[2];
+    const double hmax = std::max(h[0], std::max(h[1], h[2]));
+    const double e_c = N1 * e_l + 3.0 * u * Lm;
+    const double e_A = 3.0 * u * hmax * N1;
+    const double e_B = hsum * (N1 * e_u + 6.0 * u * N1 * N2);
+    const double e_s = 2.0 * u * (Lm + 2.0 * hsum * N1);
+    const double E = e_c + e_A + e_B + e_s;
+    const double lip = (X_D + hmax + hsum * N2) * 3.0 * (e_u + e64) * 1.001;
+    return { 2.0 * E + 4e-6 * 2.0 * R * N2, 2.0 * (E + lip) + tau * N2 };
+}
+
 // 3D: bound on |pb32 - pb| per component for B's vertices moved into A's
 // frame (qr = conj(qA) qB, l = rot(conj(qA), Delta), pb = rot(qr, v) + l),
 // where pb is the exact transform of the FP64 contract's inputs and pb32 the

@@ -249,4 +249,109 @@ __device__ __noinline__ bool overlap3d64_warp(const Shape3& sh, const double D[3
     return true;
 }
 
+// Boxes (Shape3::box): an FP64 separating-axis certificate tried before the
+// warp GJK on the pairs the FP32 test leaves uncertain.  The 15 axes of two
+// boxes decide their overlap exactly, and FP64 rounding moves the 15 values
+// by ~1e-14 of the size, so almost every pair of that FP32 band is decided
+// here: s_max > sep (the exact boxes apart by more than 4e-6 2R along an
+// axis, where the FP64 GJK answers "separated") or s_max < -ov (every
+// candidate axis overlapping deeper than tau, where it answers overlap).
+// Only pairs within that band of contact reach the GJK, whose verdict there
+// no geometric test reproduces.
+//
+// Lanes share the work: lane c computes qr component c (c < 4), l component
+// c (c < 3) and entry c of B's axes M[r][j] = (R(qr) e_j)_r (c < 9); lane a
+// < 15 then takes axis a (A's faces e_k, B's faces u_j, the crosses e_i x
+// u_j) as a vector n and evaluates s = |l.n| - sum_k h_k |n_k| - sum_j h_j
+// |n.u_j| (B's extent along n from its edge vectors u_j, no orthonormality
+// assumed); a max-reduction gives s_max on every lane.  Returns 0
+// (separated), 1 (overlap) or 2 (left to the GJK).  Call convergently from
+// all 32 lanes with the same arguments.
+static __device__ __noinline__ int box64_sat_warp(const Shape3& sh, const double D[3], const double qA[4],
+                                                  const double qB[4], double sep, double ov)
+{
+    const unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    const double qAc[4] = { qA[0], -qA[1], -qA[2], -qA[3] };
+    double qr[4];
+    {
+        const int c = lane & 3;
+        const int neg = (0x2147 >> (4 * c)) & 7;
+        double acc = qAc[0] * sel4(c, qB[0], qB[1], qB[2], qB[3]);
+        acc = acc + ((neg & 1) ? -qAc[1] : qAc[1]) * sel4(c ^ 1, qB[0], qB[1], qB[2], qB[3]);
+        acc = acc + ((neg & 2) ? -qAc[2] : qAc[2]) * sel4(c ^ 2, qB[0], qB[1], qB[2], qB[3]);
+        acc = acc + ((neg & 4) ? -qAc[3] : qAc[3]) * sel4(c ^ 3, qB[0], qB[1], qB[2], qB[3]);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) qr[k] = __shfl_sync(FULL, acc, k);
+    }
+    double l[3];
+    {
+        const int c = lane % 3;
+        const double qa = sel3(c, qAc[2], qAc[3], qAc[1]);
+        const double qb = sel3(c, qAc[3], qAc[1], qAc[2]);
+        const double t = 2.0 * (qa * sel3(c, D[2], D[0], D[1]) - qb * sel3(c, D[1], D[2], D[0]));
+        const double t0 = __shfl_sync(FULL, t, 0);
+        const double t1 = __shfl_sync(FULL, t, 1);
+        const double t2 = __shfl_sync(FULL, t, 2);
+        const double o = (sel3(c, D[0], D[1], D[2]) + qAc[0] * sel3(c, t0, t1, t2)) +
+                         (qa * sel3(c, t2, t0, t1) - qb * sel3(c, t1, t2, t0));
+        l[0] = __shfl_sync(FULL, o, 0);
+        l[1] = __shfl_sync(FULL, o, 1);
+        l[2] = __shfl_sync(FULL, o, 2);
+    }
+    double M[3][3];
+    {
+        // entry (r, j) on lane 3 r + j: 1 - 2 (v_i1^2 + v_i2^2) on the
+        // diagonal, 2 (v_r v_j +- w v_k) off it (+ when r - j = 1 mod 3)
+        const int e = lane % 9, r = e / 3, j = e - 3 * r;
+        const double x = qr[1], y = qr[2], z = qr[3];
+        double m;
+        if (r == j) {
+            const double a = sel3((r + 1) % 3, x, y, z), b = sel3((r + 2) % 3, x, y, z);
+            m = 1.0 - 2.0 * (a * a + b * b);
+        } else {
+            const double vr = sel3(r, x, y, z), vj = sel3(j, x, y, z);
+            const double wk = qr[0] * sel3(3 - r - j, x, y, z);
+            m = ((r - j + 3) % 3 == 1) ? 2.0 * (vr * vj + wk) : 2.0 * (vr * vj - wk);
+        }
+#pragma unroll
+        for (int t = 0; t < 9; ++t) M[t / 3][t % 3] = __shfl_sync(FULL, m, t);
+    }
+    const double h[3] = { fabs(sh.v[0][0]), fabs(sh.v[0][1]), fabs(sh.v[0][2]) };
+    double s = -1.0e300;
+    if (lane < 15) {
+        double n[3];
+        if (lane < 3) {
+            n[0] = lane == 0 ? 1.0 : 0.0;
+            n[1] = lane == 1 ? 1.0 : 0.0;
+            n[2] = lane == 2 ? 1.0 : 0.0;
+        } else if (lane < 6) {
+            const int j = lane - 3;
+            n[0] = sel3(j, M[0][0], M[0][1], M[0][2]);
+            n[1] = sel3(j, M[1][0], M[1][1], M[1][2]);
+            n[2] = sel3(j, M[2][0], M[2][1], M[2][2]);
+        } else {
+            // e_i x u_j = (0, -u_z, u_y), (u_z, 0, -u_x), (-u_y, u_x, 0)
+            const int i = (lane - 6) / 3, j = (lane - 6) % 3;
+            const double u0 = sel3(j, M[0][0], M[0][1], M[0][2]);
+            const double u1 = sel3(j, M[1][0], M[1][1], M[1][2]);
+            const double u2 = sel3(j, M[2][0], M[2][1], M[2][2]);
+            n[0] = sel3(i, 0.0, u2, -u1);
+            n[1] = sel3(i, -u2, 0.0, u0);
+            n[2] = sel3(i, u1, -u0, 0.0);
+        }
+        const double c = (l[0] * n[0] + l[1] * n[1]) + l[2] * n[2];
+        const double ea = (h[0] * fabs(n[0]) + h[1] * fabs(n[1])) + h[2] * fabs(n[2]);
+        double eb = 0.0;
+#pragma unroll
+        for (int j = 0; j < 3; ++j) eb = eb + h[j] * fabs((n[0] * M[0][j] + n[1] * M[1][j]) + n[2] * M[2][j]);
+        s = (fabs(c) - ea) - eb;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s = fmax(s, __shfl_xor_sync(FULL, s, o));
+    if (s > sep) return 0;
+    if (-s > ov) return 1;
+    return 2;
+}
+
 }  // namespace hpmc

@@ -69,6 +69,13 @@ struct Warp3 {
 
     uint16_t beg[S][27];
     uint16_t pfx[S][28];
+    // FP32 form: stencil position t of the strip's cell g -> staged entry e
+    // and stencil cell q, as e | q << 10 at tab[tb[g] + t] (e < CAP <= 1024,
+    // q < 27).  The cells' stencils overlap in one column, so they hold at
+    // most twice the staged entries.
+    uint16_t tab[F32 ? 2 * CAP : 1];
+    uint16_t tb[S];
+    float4 qoff[F32 ? 27 : 1];                        // FP32 offsets (ox w, oy w, oz w) of stencil cell q
     float4 qd[QCAP];                                  // queued Delta32
     uint16_t qe[QCAP];
     uint8_t qg[QCAP];
@@ -236,19 +243,43 @@ k_set3d(Dev dv, const __grid_constant__ Shape3 sh, int nxt, int sigma, const uin
             }
             if (lane == 0) ws.rowinfo[9][0] = off;
             __syncwarp();
-            // ---- stage every entry of the nine rows (one pass of loads)
-            for (uint32_t t = lane; t < off; t += 32) {
+            // ---- stage every entry of the nine rows: four entries a lane in
+            // flight (all loads issued before the first store)
+            auto entry_of = [&](uint32_t t) {
                 int q = 0;
 #pragma unroll
                 for (int qq = 1; qq < 9; ++qq) q += (t >= ws.rowinfo[qq][0]) ? 1 : 0;
                 const uint32_t u = t - ws.rowinfo[q][0];
                 const uint32_t la = ws.rowinfo[q][1];
-                const uint32_t gi = u < la ? ws.rowinfo[q][2] + u : ws.rowinfo[q][3] + (u - la);
-                ws.gidx[t] = gi;
-                if (F32) {
-                    ws.ea[t] = B.f4a[gi];
-                    ws.eb[t] = B.f4b[gi];
-                } else {
+                return u < la ? ws.rowinfo[q][2] + u : ws.rowinfo[q][3] + (u - la);
+            };
+            if constexpr (F32) {
+                for (uint32_t t0 = lane; t0 < off; t0 += 128) {
+                    uint32_t gi[4];
+                    float4 fa[4], fb[4];
+#pragma unroll
+                    for (int k4 = 0; k4 < 4; ++k4) {
+                        const uint32_t t = t0 + 32u * k4;
+                        if (t < off) {
+                            gi[k4] = entry_of(t);
+                            fa[k4] = B.f4a[gi[k4]];
+                            fb[k4] = B.f4b[gi[k4]];
+                        }
+                    }
+#pragma unroll
+                    for (int k4 = 0; k4 < 4; ++k4) {
+                        const uint32_t t = t0 + 32u * k4;
+                        if (t < off) {
+                            ws.gidx[t] = gi[k4];
+                            ws.ea[t] = fa[k4];
+                            ws.eb[t] = fb[k4];
+                        }
+                    }
+                }
+            } else {
+                for (uint32_t t = lane; t < off; t += 32) {
+                    const uint32_t gi = entry_of(t);
+                    ws.gidx[t] = gi;
                     ws.ep[t][0] = B.px[gi]; ws.ep[t][1] = B.py[gi]; ws.ep[t][2] = B.pz[gi];
                     ws.eq[t][0] = B.q0[gi]; ws.eq[t][1] = B.q1[gi];
                     ws.eq[t][2] = B.q2[gi]; ws.eq[t][3] = B.q3[gi];
@@ -279,6 +310,30 @@ k_set3d(Dev dv, const __grid_constant__ Shape3 sh, int nxt, int sigma, const uin
             const uint32_t cb = valid ? ws.sbeg[4][mc] : 0;    // centre row (y, z) = q 4
             const uint32_t n_c = valid ? (uint32_t)ws.sbeg[4][mc + 1] - cb : 0;
             const int T = ws.pfx[grp][27];
+            uint32_t tbase = 0;
+            if constexpr (F32) {
+                // the entry table, once per sub-strip instead of a search of
+                // the 27 stencil prefixes for every candidate of every select
+                if (lane == 0) {
+                    uint32_t acc = 0;
+                    for (int g = 0; g < S; ++g) {
+                        ws.tb[g] = (uint16_t)acc;
+                        acc += ws.pfx[g][27];
+                    }
+                }
+                if (lane < 27)
+                    ws.qoff[lane] = make_float4((float)(lane % 3 - 1) * rp.w32[0], (float)((lane / 3) % 3 - 1) * rp.w32[1],
+                                                (float)(lane / 9 - 1) * rp.w32[2], 0.f);
+                __syncwarp();
+                tbase = ws.tb[grp];
+                for (int t = sl; t < T; t += G) {
+                    int q = 0;
+#pragma unroll
+                    for (int qq = 1; qq < 27; ++qq) q += (t >= (int)ws.pfx[grp][qq]) ? 1 : 0;
+                    ws.tab[tbase + t] = (uint16_t)((ws.beg[grp][q] + (t - ws.pfx[grp][q])) | (q << 10));
+                }
+                __syncwarp();
+            }
             const bool live_cell = valid && n_c > 0;
 
 #pragma unroll 1
@@ -412,17 +467,23 @@ k_set3d(Dev dv, const __grid_constant__ Shape3 sh, int nxt, int sigma, const uin
                     int e = 0;
                     if (live) {
                         int q = 0;
+                        if constexpr (F32) {
+                            const uint32_t te = ws.tab[tbase + t];
+                            e = (int)(te & 1023u);
+                            q = (int)(te >> 10);
+                        } else {
 #pragma unroll
-                        for (int qq = 1; qq < 27; ++qq) q += (t >= (int)ws.pfx[grp][qq]) ? 1 : 0;
-                        e = ws.beg[grp][q] + (t - ws.pfx[grp][q]);
+                            for (int qq = 1; qq < 27; ++qq) q += (t >= (int)ws.pfx[grp][qq]) ? 1 : 0;
+                            e = ws.beg[grp][q] + (t - ws.pfx[grp][q]);
+                        }
                         if (e != myA) {
                             c_cull += 1;
-                            const int ox = q % 3 - 1, oy = (q / 3) % 3 - 1, oz = q / 9 - 1;
                             if (F32) {
                                 const float4 f = ws.ea[e];
-                                dl.x = __fsub_rn(__fadd_rn(f.x, (float)ox * rp.w32[0]), ta.x);
-                                dl.y = __fsub_rn(__fadd_rn(f.y, (float)oy * rp.w32[1]), ta.y);
-                                dl.z = __fsub_rn(__fadd_rn(f.z, (float)oz * rp.w32[2]), ta.z);
+                                const float4 o = ws.qoff[q];
+                                dl.x = __fsub_rn(__fadd_rn(f.x, o.x), ta.x);
+                                dl.y = __fsub_rn(__fadd_rn(f.y, o.y), ta.y);
+                                dl.z = __fsub_rn(__fadd_rn(f.z, o.z), ta.z);
                                 const float q32 = __fmaf_rn(dl.x, dl.x, __fmaf_rn(dl.y, dl.y, __fmul_rn(dl.z, dl.z)));
                                 if (q32 < rp.ins32) {
                                     ins = true;                    // inscribed balls meet
@@ -526,7 +587,12 @@ k_set3d(Dev dv, const __grid_constant__ Shape3 sh, int nxt, int sigma, const uin
                                 const double qa[4] = { ws.tq[g2][0], ws.tq[g2][1], ws.tq[g2][2], ws.tq[g2][3] };
                                 const double qB[4] = { B.q0[gB], B.q1[gB], B.q2[gB], B.q3[gB] };
                                 int its = 0;
-                                const bool ov = overlap3d64_warp<NV>(sh, D, qa, qB, &its);
+                                bool ov;
+                                const int bv = ((NV == 8 || NV == 0) && sh.box)
+                                                   ? box64_sat_warp(sh, D, qa, qB, rp.box_sep64, rp.box_ov64)
+                                                   : 2;
+                                if (bv < 2) ov = bv == 1;
+                                else ov = overlap3d64_warp<NV>(sh, D, qa, qB, &its);
                                 if (lane == src) {
                                     c_rechk += 1;
                                     if (its > kGjkMaxIt) c_cap += 1;

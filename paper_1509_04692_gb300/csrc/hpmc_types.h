@@ -76,6 +76,7 @@ struct Rep {
     float cell_et[3];        // bound on |t32 - t64| in cells (the boundary test)
     float box_esep;          // 3D boxes: a separating-axis gap above this certifies separation
     float box_eov;           // 3D boxes: overlaps above this on all 15 axes certify overlap
+    double box_sep64, box_ov64;  // the same two margins of the FP64 separating-axis test
     double ins64;            // the same test on the FP64 |D|^2
     double e_in, e_cull, e_sat;  // the same margins in FP64 (reporting)
 };

@@ -67,6 +67,20 @@ __global__ void k_pairs3d_warp(const __grid_constant__ Shape3 sh, uint32_t n, co
     }
 }
 
+// one warp per pair: the FP64 box certificate of the FP32-filtered sweep's
+// re-checks (0 separated, 1 overlap, 2 left to the GJK)
+__global__ void k_pairs_box64(const __grid_constant__ Shape3 sh, double sep, double ov, uint32_t n, const double* D,
+                              const double* qA, const double* qB, int32_t* out)
+{
+    const uint32_t i = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (i >= n) return;                               // whole warps leave together
+    const double d[3] = { D[3 * i], D[3 * i + 1], D[3 * i + 2] };
+    const double a[4] = { qA[4 * i], qA[4 * i + 1], qA[4 * i + 2], qA[4 * i + 3] };
+    const double b[4] = { qB[4 * i], qB[4 * i + 1], qB[4 * i + 2], qB[4 * i + 3] };
+    const int v = box64_sat_warp(sh, d, a, b, sep, ov);
+    if ((threadIdx.x & 31) == 0) out[i] = v;
+}
+
 float up32(double x)
 {
     float f = (float)x;
@@ -182,6 +196,50 @@ extern "C" int hpmc_pair_test_warp3d(const double* verts, uint32_t nv, uint32_t 
     cudaFree(dB);
     cudaFree(d64);
     cudaFree(dit);
+    if (e != cudaSuccess) {
+        (void)cudaGetLastError();
+        return e == cudaErrorMemoryAllocation ? HPMC_ERR_OOM : HPMC_ERR_CUDA;
+    }
+    return 0;
+}
+
+extern "C" int hpmc_pair_test_box64(const double* verts, uint32_t nv, uint32_t n, const double* D, const double* qA,
+                                    const double* qB, int32_t* out)
+{
+    if (!D || !qA || !qB || !out) return HPMC_ERR_INVALID_ARG;
+    Shape2 s2{};
+    Shape3 s3{};
+    double Rc = 0.0, rc2 = 0.0;
+    int rc = build_shapes(3, verts, nv, s2, s3, Rc, rc2);
+    if (rc) return rc;
+    if (!s3.box) return HPMC_ERR_INVALID_ARG;
+    if (n == 0) return 0;
+    // margins for the longest D given (the sweeps only test culled pairs)
+    double dm = 0.0;
+    for (uint32_t i = 0; i < n; ++i)
+        dm = std::fmax(dm, std::sqrt(D[3 * i] * D[3 * i] + D[3 * i + 1] * D[3 * i + 1] + D[3 * i + 2] * D[3 * i + 2]));
+    const double Rb = std::fmax(Rc, 0.5 * dm * (1.0 + 1e-6));
+    const double bh[3] = { std::fabs(s3.v[0][0]), std::fabs(s3.v[0][1]), std::fabs(s3.v[0][2]) };
+    const BoxMargins bm = box_sat_margins64(Rb, bh, (double)up32(1e-9 * 2.0 * Rc));
+    double *dD = nullptr, *dA = nullptr, *dB = nullptr;
+    int32_t* dO = nullptr;
+    cudaError_t e = cudaMalloc(&dD, sizeof(double) * n * 3);
+    if (e == cudaSuccess) e = cudaMalloc(&dA, sizeof(double) * n * 4);
+    if (e == cudaSuccess) e = cudaMalloc(&dB, sizeof(double) * n * 4);
+    if (e == cudaSuccess) e = cudaMalloc(&dO, sizeof(int32_t) * n);
+    if (e == cudaSuccess) e = cudaMemcpy(dD, D, sizeof(double) * n * 3, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(dA, qA, sizeof(double) * n * 4, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(dB, qB, sizeof(double) * n * 4, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) {
+        const uint32_t wpb = 4;
+        k_pairs_box64<<<(n + wpb - 1) / wpb, 32 * wpb>>>(s3, bm.sep, bm.ov, n, dD, dA, dB, dO);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpy(out, dO, sizeof(int32_t) * n, cudaMemcpyDeviceToHost);
+    cudaFree(dD);
+    cudaFree(dA);
+    cudaFree(dB);
+    cudaFree(dO);
     if (e != cudaSuccess) {
         (void)cudaGetLastError();
         return e == cudaErrorMemoryAllocation ? HPMC_ERR_OOM : HPMC_ERR_CUDA;

@@ -34,6 +34,7 @@ EXPORTS = [
     "hpmc_trace_read", "hpmc_pair_test", "hpmc_sdf", "hpmc_box_move", "hpmc_get_box",
     "hpmc_tune_moves", "hpmc_msd_reset", "hpmc_msd_update", "hpmc_msd_read", "hpmc_debug_fail_alloc",
     "hpmc_pair_test_warp3d", "hpmc_set_cell_width_min", "hpmc_measure_fma_peak", "hpmc_pressure",
+    "hpmc_pair_test_box64",
 ]
 
 
@@ -105,6 +106,7 @@ def _load():
                            ctypes.POINTER(ctypes.c_int32)],
         "hpmc_pair_test_warp3d": [dp, u32, u32, dp, dp, dp, ctypes.POINTER(ctypes.c_int32),
                                   ctypes.POINTER(ctypes.c_int32)],
+        "hpmc_pair_test_box64": [dp, u32, u32, dp, dp, dp, ctypes.POINTER(ctypes.c_int32)],
         "hpmc_sdf": [ctypes.c_void_p, ctypes.c_int32, ctypes.c_double, u32, ctypes.POINTER(ctypes.c_uint64)],
         "hpmc_box_move": [ctypes.c_void_p, ctypes.c_int32, ctypes.c_double, ctypes.c_double,
                           ctypes.POINTER(ctypes.c_int)],
@@ -408,6 +410,20 @@ def pair_test_warp3d(verts, D, qA, qB):
     _ck(_lib.hpmc_pair_test_warp3d(_dp(v), nv, n, _dp(D), _dp(qA), _dp(qB), o64.ctypes.data_as(ip),
                                    its.ctypes.data_as(ip)), "hpmc_pair_test_warp3d")
     return o64, its
+
+
+def pair_test_box64(verts, D, qA, qB):
+    """The FP64 separating-axis certificate of box pairs (one warp per pair):
+    0 separated, 1 overlap, 2 left to the FP64 GJK."""
+    v = _c64(verts).reshape(-1, 3)
+    D = _c64(D).reshape(-1, 3)
+    n = D.shape[0]
+    qA = _sized(qA, n * 4, "pair_test_box64 qA").reshape(-1, 4)
+    qB = _sized(qB, n * 4, "pair_test_box64 qB").reshape(-1, 4)
+    out = np.zeros(n, dtype=np.int32)
+    _ck(_lib.hpmc_pair_test_box64(_dp(v), v.shape[0], n, _dp(D), _dp(qA), _dp(qB),
+                                  out.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))), "hpmc_pair_test_box64")
+    return out
 
 
 def from_system(sysm, w_min=None):

@@ -165,3 +165,61 @@ def test_warp_gjk_ties_and_spheres():
     ref = sph.overlap(D, qA, qB)
     got, git = hpmc.pair_test_warp3d(np.array(0.5), D, qA, qB)
     assert np.array_equal(got, ref) and not git.any()
+
+
+def _cuboid(hx, hy, hz):
+    return np.array([[sx * hx, sy * hy, sz * hz] for sz in (-1, 1) for sy in (-1, 1) for sx in (-1, 1)], float)
+
+
+@pytest.mark.parametrize("h", [(0.5, 0.5, 0.5), (0.7, 0.35, 0.2)])
+def test_box_certificates_never_contradict_the_contract(h):
+    # boxes take the FP32 separating-axis certificate in place of the FP32
+    # GJK, and their FP32-uncertain pairs the FP64 one before the FP64 GJK:
+    # every certified verdict equals the oracle's GJK, and the FP64 band of
+    # uncertain pairs is far narrower than the FP32 one
+    rng = np.random.default_rng(int(1000 * h[2]))
+    v = _cuboid(*h)
+    R = float(np.linalg.norm(h))
+    s = orc.OracleSystem(3, [50.0] * 3, v)
+    n = 60000
+    d = rng.normal(size=(n, 3))
+    d /= np.linalg.norm(d, axis=1)[:, None]
+    D = d * (2 * R * 1.02 * rng.uniform(0, 1, n) ** (1 / 3))[:, None]
+    qA, qB = _quats(rng, n), _quats(rng, n)
+    qB[:500] = qA[:500]                                    # parallel edges: degenerate crosses
+    ref, o32 = _check(3, v, D, qA, qB, 0.005)
+    assert 0.1 < ref.mean() < 0.9
+    b64 = hpmc.pair_test_box64(v, D, qA, qB)
+    cert = b64 < 2
+    assert np.array_equal(b64[cert], ref[cert]), np.nonzero(cert & (b64 != ref))[0][:10]
+    assert (~cert[500:]).mean() < 1e-3
+    # near contact along random directions
+    m = 20000
+    lo, hi = np.zeros(m), np.full(m, 2 * R * 1.001)
+    for _ in range(45):
+        mid = 0.5 * (lo + hi)
+        ov = s.overlap(d[:m] * mid[:, None], qA[:m], qB[:m]).astype(bool)
+        lo, hi = np.where(ov, mid, lo), np.where(ov, hi, mid)
+    # offsets log-uniform in [1e-10, 1e-2] (both signs) on the first half,
+    # uniform in [-1e-3, 1e-3] on the second (the bands' widths compared)
+    off = rng.choice([-1, 1], m) * 10.0 ** rng.uniform(-10, -2, m)
+    off[m // 2:] = rng.uniform(-1e-3, 1e-3, m - m // 2)
+    Dn = d[:m] * (0.5 * (lo + hi) + off)[:, None]
+    ref, o32 = _check(3, v, Dn, qA[:m], qB[:m], 1.0)
+    b64 = hpmc.pair_test_box64(v, Dn, qA[:m], qB[:m])
+    cert = b64 < 2
+    assert np.array_equal(b64[cert], ref[cert]), np.nonzero(cert & (b64 != ref))[0][:10]
+    far = np.abs(off) > 1e-4
+    far[:500] = False
+    assert (o32[far] >= 2).mean() < 0.5 and (b64[far] == 2).mean() < 0.05, (
+        (o32[far] >= 2).mean(), (b64[far] == 2).mean())
+    lin = slice(m // 2, m)
+    assert (b64[lin] == 2).sum() < 0.2 * (o32[lin] >= 2).sum(), ((b64[lin] == 2).sum(), (o32[lin] >= 2).sum())
+
+
+def test_box64_rejects_other_shapes():
+    rng = np.random.default_rng(8)
+    D = rng.normal(size=(4, 3))
+    q = _quats(rng, 4)
+    with pytest.raises(hpmc.HPMCError):
+        hpmc.pair_test_box64(_polyhedron("octahedron", rng), D, q, q)
