@@ -291,16 +291,10 @@ __device__ __forceinline__ bool cert_separated(int nv, const G32* pb, const Shap
 
 // Overlap: the origin lies strictly inside the tetrahedron of the four exact
 // vertex differences, farther than tau from each face plane.
-__device__ __forceinline__ bool cert_inside(const G32* pb, const Shape3& sh, const SPt sp[4], float e_pb, float e_va,
-                                            float tau)
+// The test on four points W[k] of B - A given with their error bounds (the
+// exact points, which the test is about, lie within them).
+__device__ __forceinline__ bool cert_inside_pts(const Fe3 W[4], float tau)
 {
-    Fe3 W[4];
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
-        const G32 b = pb[sp[k].ib], a = vA(sh, sp[k].ia);
-        W[k] = fe3_sub(Fe3{ { b.x, e_pb }, { b.y, e_pb }, { b.z, e_pb } },
-                       Fe3{ { a.x, e_va }, { a.y, e_va }, { a.z, e_va } });
-    }
 #pragma unroll 1
     for (int f = 0; f < 4; ++f) {
         const int i0 = (f == 3) ? 1 : 0, i1 = (f <= 1) ? 1 : 2, i2 = (f == 0) ? 2 : 3, i3 = 3 - f;
@@ -315,6 +309,22 @@ __device__ __forceinline__ bool cert_inside(const G32* pb, const Shape3& sh, con
         if (!(__fsub_rd(fabsf(so.v), so.e) > __fmul_ru(tau, n1))) return false;
     }
     return true;
+}
+
+__device__ __forceinline__ Fe3 fe3_vertex_diff(const G32* pb, const Shape3& sh, const SPt& q, float e_pb, float e_va)
+{
+    const G32 b = pb[q.ib], a = vA(sh, q.ia);
+    return fe3_sub(Fe3{ { b.x, e_pb }, { b.y, e_pb }, { b.z, e_pb } }, Fe3{ { a.x, e_va }, { a.y, e_va }, { a.z, e_va } });
+}
+
+// the tetrahedron of four exact vertex differences
+__device__ __forceinline__ bool cert_inside(const G32* pb, const Shape3& sh, const SPt sp[4], float e_pb, float e_va,
+                                            float tau)
+{
+    Fe3 W[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) W[k] = fe3_vertex_diff(pb, sh, sp[k], e_pb, e_va);
+    return cert_inside_pts(W, tau);
 }
 
 // GJK stops at the first tetrahedron that encloses the origin, which may
@@ -369,14 +379,12 @@ __device__ __noinline__ bool expand_inside(int nv, const G32* pb, const Shape3& 
     return false;
 }
 
-// FP32 GJK + certificate for A (orientation qA) and B at Delta (orientation
-// qB), in A's frame: GJK32_SEPARATED / GJK32_OVERLAP when certified about the
-// exact shapes with margin tau (where the FP64 contract decides the same),
-// GJK32_UNCERTAIN otherwise.
-// Quaternions as (w, x, y, z) in a float4's (x, y, z, w).
+// B placed in A's frame in FP32 (A with orientation qA, B at Delta with
+// orientation qB): its centre l and its vertices pb.  Quaternions as (w, x,
+// y, z) in a float4's (x, y, z, w).
 template <int NV>
-__device__ __forceinline__ int gjk32_cert(const Shape3& sh, float dx, float dy, float dz, float4 qA, float4 qB,
-                                          float e_pb, float e_va, float tau)
+__device__ __forceinline__ void gjk32_setup(const Shape3& sh, float dx, float dy, float dz, float4 qA, float4 qB,
+                                            G32& l, G32* pb)
 {
     const int nv = NV ? NV : sh.nv;
     // qr = conj(qA) qB, l = rot(conj(qA), Delta), pb = rot(qr, v) + l
@@ -393,8 +401,7 @@ __device__ __forceinline__ int gjk32_cert(const Shape3& sh, float dx, float dy, 
         return G32{ (v.x + w * tx) + (y * tz - z * ty), (v.y + w * ty) + (z * tx - x * tz),
                     (v.z + w * tz) + (x * ty - y * tx) };
     };
-    const G32 l = rot(a0, a1, a2, a3, G32{ dx, dy, dz });
-    G32 pb[NV ? NV : kMaxV3];
+    l = rot(a0, a1, a2, a3, G32{ dx, dy, dz });
     if constexpr (NV >= 16) {
 #pragma unroll 4
         for (int i = 0; i < NV; ++i) {
@@ -409,6 +416,16 @@ __device__ __forceinline__ int gjk32_cert(const Shape3& sh, float dx, float dy, 
             pb[i] = G32{ rr.x + l.x, rr.y + l.y, rr.z + l.z };
         }
     }
+}
+
+// FP32 GJK + certificate from B's vertices pb in A's frame and B's centre l
+// there: GJK32_SEPARATED / GJK32_OVERLAP when certified about the exact
+// shapes with margin tau (where the FP64 contract decides the same),
+// GJK32_UNCERTAIN (or a more specific reason >= 2) otherwise.
+template <int NV>
+__device__ __forceinline__ int gjk32_run(int nv, const G32* pb, const Shape3& sh, G32 l, float e_pb, float e_va,
+                                         float tau)
+{
     // the centre line first: well-separated pairs are certified without GJK
     if (cert_separated<NV>(nv, pb, sh, l, e_pb, e_va, tau)) return GJK32_SEPARATED;
     G32 d = g_neg(l);
@@ -446,6 +463,17 @@ __device__ __forceinline__ int gjk32_cert(const Shape3& sh, float dx, float dy, 
         if (rr == 2) return GJK32_UNC_DEGENERATE;
     }
     return GJK32_UNC_CAP;
+}
+
+// the same from Delta and the two orientations
+template <int NV>
+__device__ __forceinline__ int gjk32_cert(const Shape3& sh, float dx, float dy, float dz, float4 qA, float4 qB,
+                                          float e_pb, float e_va, float tau)
+{
+    G32 l;
+    G32 pb[NV ? NV : kMaxV3];
+    gjk32_setup<NV>(sh, dx, dy, dz, qA, qB, l, pb);
+    return gjk32_run<NV>(NV ? NV : sh.nv, pb, sh, l, e_pb, e_va, tau);
 }
 
 // Boxes (Shape3::box: vertices (+-h0, +-h1, +-h2)): the separating-axis

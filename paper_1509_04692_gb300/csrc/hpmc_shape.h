@@ -13,6 +13,8 @@ namespace hpmc {
 // circumradius R, cull threshold (2R)^2, polygon edge normals and A's own
 // projection intervals (2D), FP32 copies.  Validates the vertex list
 // (2D: convex, counter-clockwise).  Host only.
+inline double shape_inradius(int dim, const double* v, uint32_t nv);
+
 inline int build_shapes(int dim, const double* verts, uint32_t nv, Shape2& s2, Shape3& s3, double& Rc,
                         double& rc2)
 {
@@ -93,6 +95,7 @@ inline int build_shapes(int dim, const double* verts, uint32_t nv, Shape2& s2, S
             }
         s.rc2 = rc2;
         s.frc2 = (float)rc2;
+        s.mpr = shape_inradius(3, verts, nv) > 1e-3 * Rc ? 1 : 0;
         // a box centred on the origin and aligned with the local axes: every
         // vertex is (+-h0, +-h1, +-h2) and all 8 sign patterns occur
         if (nv == 8) {

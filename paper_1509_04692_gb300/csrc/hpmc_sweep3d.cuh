@@ -18,6 +18,7 @@
 #pragma once
 #include "hpmc_device.cuh"
 #include "hpmc_gjk32.cuh"
+#include "hpmc_mpr32.cuh"
 #include "hpmc_gjk64w.cuh"
 
 namespace hpmc {
@@ -548,6 +549,9 @@ k_set3d(Dev dv, const __grid_constant__ Shape3 sh, int nxt, int sigma, const uin
                                     int v;
                                     if ((NV == 8 || NV == 0) && sh.box)
                                         v = box32_sat(sh, d2.x, d2.y, d2.z, qa, qb, rp.box_esep, rp.box_eov);
+                                    else if (NV != 8 && sh.mpr)       // (8 vertices: boxes, else GJK)
+                                        v = mpr32_cert<NV>(sh, d2.x, d2.y, d2.z, qa, qb, rp.e_pb32, rp.e_va32,
+                                                           rp.tau3);
                                     else
                                         v = gjk32_cert<NV>(sh, d2.x, d2.y, d2.z, qa, qb, rp.e_pb32, rp.e_va32,
                                                            rp.tau3);

@@ -98,6 +98,7 @@ struct Shape3 {
     int nv;
     int round;               // 1: hard sphere (nv = 0), overlap iff |D|^2 <= rc2
     int box;                 // 1: the 8 vertices are (+-h0, +-h1, +-h2), a box centred on the origin
+    int mpr;                 // 1: the local origin is interior (the FP32 filter searches by portal refinement)
     float bh[3];             // its half extents (FP32)
     double v[kMaxV3][3];
     float fv[kMaxV3][3];

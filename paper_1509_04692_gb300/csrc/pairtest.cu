@@ -10,6 +10,7 @@
 #include "hpmc_device.cuh"
 #include "hpmc_filter.cuh"
 #include "hpmc_gjk32.cuh"
+#include "hpmc_mpr32.cuh"
 #include "hpmc_gjk64w.cuh"
 #include "hpmc_shape.h"
 
@@ -44,8 +45,10 @@ __global__ void k_pairs3d(const __grid_constant__ Shape3 sh, float e_pb, float e
     if (sh.round) { o32[i] = 2; return; }            // spheres: the set kernels' cull decides
     const float4 fa = make_float4((float)a[0], (float)a[1], (float)a[2], (float)a[3]);
     const float4 fb = make_float4((float)b[0], (float)b[1], (float)b[2], (float)b[3]);
-    const int v = sh.box ? box32_sat(sh, (float)d[0], (float)d[1], (float)d[2], fa, fb, box_sep, box_ov)
-                         : gjk32_cert<0>(sh, (float)d[0], (float)d[1], (float)d[2], fa, fb, e_pb, e_va, tau);
+    const float dx = (float)d[0], dy = (float)d[1], dz = (float)d[2];
+    const int v = sh.box  ? box32_sat(sh, dx, dy, dz, fa, fb, box_sep, box_ov)
+                  : sh.mpr ? mpr32_cert<0>(sh, dx, dy, dz, fa, fb, e_pb, e_va, tau)
+                           : gjk32_cert<0>(sh, dx, dy, dz, fa, fb, e_pb, e_va, tau);
     o32[i] = v;   // 0, 1, or the reason it is uncertain (>= 2)
 }
 

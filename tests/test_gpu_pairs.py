@@ -63,11 +63,15 @@ def test_pentagon_pairs_random_and_near_contact():
     assert (o32[far] >= 2).mean() < 0.05
 
 
-@pytest.mark.parametrize("shape", ["cube", "octahedron", "random12"])
+@pytest.mark.parametrize("shape", ["cube", "octahedron", "random12", "dodecahedron"])
 def test_polyhedron_pairs_random_and_near_contact(shape):
-    rng = np.random.default_rng({"cube": 2, "octahedron": 3, "random12": 4}[shape])
+    # cubes take the box test, octahedra and dodecahedra (origin interior)
+    # the portal refinement with the GJK behind it, random12 the GJK
+    rng = np.random.default_rng({"cube": 2, "octahedron": 3, "random12": 4, "dodecahedron": 5}[shape])
     if shape == "cube":
         v = inputs.cube(1.0)
+    elif shape == "dodecahedron":
+        v = inputs.dodecahedron(1.0)
     elif shape == "octahedron":
         v = np.array([[1, 0, 0], [-1, 0, 0], [0, 1, 0], [0, -1, 0], [0, 0, 1], [0, 0, -1]], float) * 0.6
     else:
