@@ -171,6 +171,40 @@ __device__ __forceinline__ SPt g_support(int nv, const G32* pb, const Shape3& sh
     return { g_sub(pb[ib], vA(sh, ia)), ib, ia };
 }
 
+// The same query for a centrally symmetric shape (fv ordered in pairs k,
+// k + NV / 2) from the first half: the partner's pb . d is 2 l.d - pb_k . d
+// and its vA . d is -vA_k . d, up to rounding, which only the searches use
+// (the certificates scan every vertex).
+template <int NV>
+__device__ __forceinline__ SPt g_support_sym(const G32* pb, const Shape3& sh, G32 l, G32 d)
+{
+    constexpr int H = NV / 2;
+    const float c2 = 2.0f * g_dot(l, d);
+    int ib = 0, ia = 0;
+    float best = g_dot(pb[0], d), least = g_dot(vA(sh, 0), d);
+    if (c2 - best > best) { best = c2 - best; ib = H; }
+    if (-least < least) { least = -least; ia = H; }
+#pragma unroll
+    for (int k = 1; k < H; ++k) {
+        const float t = g_dot(pb[k], d), tp = c2 - t;
+        const float u = g_dot(vA(sh, k), d);
+        if (t > best) { best = t; ib = k; }
+        if (tp > best) { best = tp; ib = k + H; }
+        if (u < least) { least = u; ia = k; }
+        if (-u < least) { least = -u; ia = k + H; }
+    }
+    return { g_sub(pb[ib], vA(sh, ia)), ib, ia };
+}
+
+// the support query of the searches
+template <int NV>
+__device__ __forceinline__ SPt g_support_q(int nv, const G32* pb, const Shape3& sh, G32 l, G32 d)
+{
+    if constexpr (NV >= 16)
+        if (sh.sym) return g_support_sym<NV>(pb, sh, l, d);
+    return g_support<NV>(nv, pb, sh, d);
+}
+
 __device__ __forceinline__ int g_closest_seg(G32 a, G32 b, G32& out)
 {
     const G32 ab = g_sub(b, a), ap = g_neg(a);
@@ -402,7 +436,17 @@ __device__ __forceinline__ void gjk32_setup(const Shape3& sh, float dx, float dy
                     (v.z + w * tz) + (x * ty - y * tx) };
     };
     l = rot(a0, a1, a2, a3, G32{ dx, dy, dz });
-    if constexpr (NV >= 16) {
+    if (NV >= 16 && sh.sym) {
+        // rot is odd in v, exactly: the partner k + nv / 2 of vertex k is
+        // l - rot(v_k), the same FP32 value as rot(-v_k) + l
+        constexpr int H = NV / 2;
+#pragma unroll
+        for (int k = 0; k < H; ++k) {
+            const G32 rr = rot(r0, r1, r2, r3, vA(sh, k));
+            pb[k] = G32{ rr.x + l.x, rr.y + l.y, rr.z + l.z };
+            pb[k + H] = G32{ l.x - rr.x, l.y - rr.y, l.z - rr.z };
+        }
+    } else if constexpr (NV >= 16) {
 #pragma unroll 4
         for (int i = 0; i < NV; ++i) {
             const G32 rr = rot(r0, r1, r2, r3, vA(sh, i));
@@ -432,14 +476,14 @@ __device__ __forceinline__ int gjk32_run(int nv, const G32* pb, const Shape3& sh
     if (d.x == 0.f && d.y == 0.f && d.z == 0.f) d.x = -1.0f;
     SPt sp[4];
     int n = 1;
-    sp[0] = g_support<NV>(nv, pb, sh, d);
+    sp[0] = g_support_q<NV>(nv, pb, sh, l, d);
     G32 v = sp[0].p;
     bool tried = false;   // a separating direction failed its certificate
 #pragma unroll 1
     for (int it = 0; it < kGjkMaxIt; ++it) {
         const float vv = g_dot(v, v);
         if (vv == 0.f) return GJK32_UNC_DEGENERATE;
-        const SPt w = g_support<NV>(nv, pb, sh, g_neg(v));
+        const SPt w = g_support_q<NV>(nv, pb, sh, l, g_neg(v));
         const float vw = g_dot(v, w.p);
         if (vw > 0.f) {
             // v separates in FP32.  Certify it; if the gap is within the

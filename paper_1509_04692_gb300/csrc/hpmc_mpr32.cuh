@@ -59,7 +59,7 @@ __device__ __forceinline__ int mpr32_cert(const Shape3& sh, float dx, float dy, 
                 break;
             }
         }
-        const SPt p = g_support<NV>(nv, pb, sh, n);
+        const SPt p = g_support_q<NV>(nv, pb, sh, l, n);
         if (g_dot(p.p, n) <= 0.f) {
             res = 2;
             break;

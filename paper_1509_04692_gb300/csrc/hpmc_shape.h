@@ -96,6 +96,40 @@ inline int build_shapes(int dim, const double* verts, uint32_t nv, Shape2& s2, S
         s.rc2 = rc2;
         s.frc2 = (float)rc2;
         s.mpr = shape_inradius(3, verts, nv) > 1e-3 * Rc ? 1 : 0;
+        // central symmetry (every vertex's negation is a vertex too): the FP32
+        // copies the filter scans are reordered into pairs k, k + nv / 2; the
+        // filter's certificates do not depend on the order, and the FP64
+        // contract keeps the given one
+        if (nv >= 2 && nv % 2 == 0) {
+            bool ok = true;
+            uint32_t h = 0;
+            int used[kMaxV3] = {};
+            int rep[kMaxV3 / 2], par[kMaxV3 / 2];
+            for (uint32_t i = 0; i < nv && ok; ++i) {
+                if (used[i]) continue;
+                int j = -1;
+                for (uint32_t k = i + 1; k < nv; ++k)
+                    if (!used[k] && s.v[k][0] == -s.v[i][0] && s.v[k][1] == -s.v[i][1] && s.v[k][2] == -s.v[i][2]) {
+                        j = (int)k;
+                        break;
+                    }
+                if (j < 0) ok = false;
+                else {
+                    used[i] = used[j] = 1;
+                    rep[h] = (int)i;
+                    par[h] = j;
+                    h += 1;
+                }
+            }
+            if (ok && 2 * h == nv) {
+                s.sym = 1;
+                for (uint32_t k = 0; k < h; ++k)
+                    for (int a = 0; a < 3; ++a) {
+                        s.fv[k][a] = (float)s.v[rep[k]][a];
+                        s.fv[k + h][a] = (float)s.v[par[k]][a];
+                    }
+            }
+        }
         // a box centred on the origin and aligned with the local axes: every
         // vertex is (+-h0, +-h1, +-h2) and all 8 sign patterns occur
         if (nv == 8) {

@@ -99,9 +99,10 @@ struct Shape3 {
     int round;               // 1: hard sphere (nv = 0), overlap iff |D|^2 <= rc2
     int box;                 // 1: the 8 vertices are (+-h0, +-h1, +-h2), a box centred on the origin
     int mpr;                 // 1: the local origin is interior (the FP32 filter searches by portal refinement)
+    int sym;                 // 1: centrally symmetric; fv is then ordered so that fv[k + nv / 2] = -fv[k]
     float bh[3];             // its half extents (FP32)
-    double v[kMaxV3][3];
-    float fv[kMaxV3][3];
+    double v[kMaxV3][3];     // the contract's vertices, in the given order
+    float fv[kMaxV3][3];     // FP32 copies for the filter (same order unless sym)
     double rc2;
     float frc2;
 };
