@@ -39,8 +39,8 @@ __device__ __forceinline__ int mpr32_cert(const Shape3& sh, float dx, float dy, 
     G32 l;
     G32 pb[NV ? NV : kMaxV3];
     gjk32_setup<NV>(sh, dx, dy, dz, qA, qB, l, pb);
-    // the centre line first: well-separated pairs are certified at once
-    if (cert_separated<NV>(nv, pb, sh, l, e_pb, e_va, tau)) return GJK32_SEPARATED;
+    // (the first iteration's query along -l tests the centre line: a miss
+    // there is certified along l like GJK's first step)
     const G32 v0 = l;
     // a move of the portal below this is no progress (lengths scale with 2R)
     const float tol = 1e-6f * sqrtf(sh.frc2);
