@@ -111,7 +111,8 @@ int hpmc_create(const double* box, int dim, uint32_t N, const double* verts, uin
                 const double* pos, const double* orient, uint64_t seed, double w_min,
                 hpmc_t* out);
 
-/* Release every device and host resource of the handle (synchronises it). */
+/* Release every device and host resource of the handle (synchronises it).
+ * Resource management: no counterpart in the paper. */
 int hpmc_destroy(hpmc_t h);
 
 /*
@@ -174,7 +175,8 @@ int hpmc_set_group_size(hpmc_t h, int lanes_per_cell, int warps_per_block);
 int hpmc_sweep(hpmc_t h, uint32_t n, void* stream);
 int hpmc_sweep_graph(hpmc_t h, uint32_t n, void* stream);
 
-/* Wait for the handle's last stream; returns a recorded device error. */
+/* Wait for the handle's last stream; returns a recorded device error.
+ * Host synchronisation: no counterpart in the paper. */
 int hpmc_sync(hpmc_t h);
 
 /*
@@ -235,8 +237,9 @@ int hpmc_run_host(hpmc_t h, const double* pos, const double* orient, uint32_t n,
                   double* pos_out, double* orient_out, hpmc_counters_t* out, void* stream);
 
 /*
- * hpmc_autotune -- time each (lanes per cell, warps per block) choice on
- * n_trial sweeps from a saved copy of the state, restore the state and
+ * hpmc_autotune -- the launch-parameter autotuner of Sec. 2.5.3 (the fastest
+ * group size and block size by timing).  Times each (lanes per cell, warps
+ * per block) choice on n_trial sweeps from a saved copy of the state, restore the state and
  * sweep counters, and keep the fastest choice.  The trajectory does not
  * depend on the choice.  *best_lanes / *best_warps receive it.  A choice
  * whose sweeps cannot be launched is skipped; a failing CUDA call restores
@@ -245,7 +248,8 @@ int hpmc_run_host(hpmc_t h, const double* pos, const double* orient, uint32_t n,
 int hpmc_autotune(hpmc_t h, uint32_t n_trial, int* best_lanes, int* best_warps);
 
 /*
- * hpmc_profile_sweeps -- run n sweeps on `stream` with CUDA events recorded
+ * hpmc_profile_sweeps -- the time per sweep that Sec. 3's benchmarks report,
+ * split by phase: run n sweeps on `stream` with CUDA events recorded
  * around the rebuild (shift + cell list) and around the 2^d set kernels of
  * every sweep; synchronise and return the mean milliseconds per sweep of
  * each phase.  The set kernels' mean duration is *ms_sets / 2^d.
@@ -257,7 +261,8 @@ int hpmc_profile_sweeps(hpmc_t h, uint32_t n, void* stream, double* ms_rebuild, 
  * work item of every warp of the last set kernel, clock64() stamps at its
  * phase boundaries (*n_points per warp; see HPMC_STAMP in the kernel source).
  * Copies up to max_warps warps' stamps into out[max_warps * *n_points].
- * Returns HPMC_ERR_NOT_READY in ordinary builds.  Synchronous.
+ * Returns HPMC_ERR_NOT_READY in ordinary builds.  Synchronous.  A profiling
+ * aid: no counterpart in the paper.
  */
 int hpmc_trace_read(hpmc_t h, uint64_t* out, uint32_t max_warps, uint32_t* n_points);
 
@@ -281,11 +286,13 @@ int hpmc_box_move(hpmc_t h, int32_t r, double beta_P, double dV_max, int* accept
  * allocation the library makes from now on (n = 0: the next one) fails as
  * if the device were out of memory; the call that made it returns
  * HPMC_ERR_OOM and releases what it had allocated.  n < 0 disables it.
- * Host-side only: nothing runs on or faults the device.
+ * Host-side only: nothing runs on or faults the device.  A test hook with
+ * no counterpart in the paper.
  */
 int hpmc_debug_fail_alloc(int32_t n);
 
-/* hpmc_get_box -- the current box lengths of replica r (box[3]; 0 beyond dim). */
+/* hpmc_get_box -- the current box lengths of replica r (box[3]; 0 beyond
+ * dim), which hpmc_box_move changes (the NPT ensemble of Sec. 1). */
 int hpmc_get_box(hpmc_t h, int32_t r, double* box);
 
 /*
@@ -367,15 +374,18 @@ int hpmc_pressure(const uint64_t* hist, uint32_t nbins, uint64_t n_samples, doub
                   double volume, int dim, int deg, double sigma, hpmc_pressure_t* out);
 
 /*
- * hpmc_pair_test -- evaluate the overlap test on n independent pairs on the
- * GPU, for validation.  A sits at the origin with orientation qA, B at Delta
+ * hpmc_pair_test -- evaluate the overlap test of Sec. 2.3 (the separating
+ * axis test in 2D, GJK in 3D, and the single-precision check of its mixed
+ * precision mode) on n independent pairs on the GPU, for validation.  A sits at the origin with orientation qA, B at Delta
  * (minimum image already applied) with orientation qB; host arrays
  * D[n*dim], qA[n*(2|4)], qB[n*(2|4)] in FP64.  out64[n] receives the FP64
  * contract's verdict (1 overlap, 0 separated); out32[n] the FP32 filter's
  * verdict from the FP32-cast inputs (1 overlap, 0 separated, >= 2
  * uncertain: the sweep would re-decide in FP64; in 3D the value says why:
  * 2 converged apart within the error bound, 3 enclosed but the origin within
- * the bound of a face, 4 degenerate simplex, 5 iteration cap).  Shape and dim as in
+ * the bound of a face, 4 degenerate simplex, 5 iteration cap).  3D boxes take
+ * the separating-axis certificate (2 = uncertain), polyhedra with an
+ * interior origin the portal refinement before the GJK.  Shape and dim as in
  * hpmc_batch_create.  Synchronous; allocates and frees its own device
  * buffers.
  */
@@ -407,22 +417,28 @@ int hpmc_pair_test_warp3d(const double* verts, uint32_t nv, uint32_t n, const do
 int hpmc_pair_test_box64(const double* verts, uint32_t nv, uint32_t n, const double* D, const double* qA,
                          const double* qB, int32_t* out);
 
-/* Geometry of replica r: cells per axis, cell width, circumradius. */
+/* Geometry of replica r: cells per axis, cell width, circumradius (the cell
+ * list of Sec. 2.2.1: cells at least the circumdiameter wide). */
 int hpmc_geometry(hpmc_t h, int32_t r, int32_t* nc, double* w, double* R);
 
 /* Number of kernel launches one sweep enqueues, the select-table kernel of
- * the latency regime included (for launch accounting). */
+ * the latency regime included (for launch accounting; no counterpart in the
+ * paper). */
 int hpmc_launches_per_sweep(hpmc_t h, uint32_t* n);
 
-/* FP32 filter margins of replica r (in-cell, cull, overlap), for reporting. */
+/* FP32 filter margins of replica r (in-cell, cull, overlap), for reporting:
+ * the certified bounds of the single-precision checks of the mixed
+ * precision mode (Sec. 2.3). */
 int hpmc_filter_margins(hpmc_t h, int32_t r, double* e_in, double* e_cull, double* e_overlap);
 
+/* Name of an error code (a static string; unknown codes get a generic name).
+ * Error reporting: no counterpart in the paper. */
 const char* hpmc_strerror(int code);
 
 /*
  * hpmc_measure_fma_peak -- measured peak of the pipe the set kernels' ALU
  * work runs on (the roofline denominator of their arithmetic; the paper
- * states no machine peak).  Times `iters` iterations of 8 independent fused
+ * states no machine peak: no counterpart in the paper).  Times `iters` iterations of 8 independent fused
  * multiply-adds per thread in 2048 resident threads on every SM, FP64 when
  * fp64 != 0 else FP32, with CUDA events on a private stream, `reps` times
  * after one short warm-up launch; *flops_per_s receives the best rate (2
