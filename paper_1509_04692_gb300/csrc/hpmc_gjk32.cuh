@@ -130,10 +130,13 @@ struct G32 {
 };
 __device__ __forceinline__ G32 g_sub(G32 a, G32 b) { return { a.x - b.x, a.y - b.y, a.z - b.z }; }
 __device__ __forceinline__ G32 g_neg(G32 a) { return { -a.x, -a.y, -a.z }; }
-__device__ __forceinline__ float g_dot(G32 a, G32 b) { return (a.x * b.x + a.y * b.y) + a.z * b.z; }
+// Products and sums in fused multiply-adds: each result is rounded at most
+// as often as with separate operations, so the certificates' bounds, which
+// count one rounding per operation, cover them.
+__device__ __forceinline__ float g_dot(G32 a, G32 b) { return __fmaf_rn(a.z, b.z, __fmaf_rn(a.y, b.y, a.x * b.x)); }
 __device__ __forceinline__ G32 g_cross(G32 a, G32 b)
 {
-    return { a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x };
+    return { __fmaf_rn(a.y, b.z, -(a.z * b.y)), __fmaf_rn(a.z, b.x, -(a.x * b.z)), __fmaf_rn(a.x, b.y, -(a.y * b.x)) };
 }
 __device__ __forceinline__ G32 g_axpy(G32 a, float t, G32 b) { return { a.x + t * b.x, a.y + t * b.y, a.z + t * b.z }; }
 
@@ -428,12 +431,14 @@ __device__ __forceinline__ void gjk32_setup(const Shape3& sh, float dx, float dy
     const float r1 = ((a0 * b1 + a1 * b0) + a2 * b3) - a3 * b2;
     const float r2 = ((a0 * b2 - a1 * b3) + a2 * b0) + a3 * b1;
     const float r3 = ((a0 * b3 + a1 * b2) - a2 * b1) + a3 * b0;
+    // (fused multiply-adds: no more roundings than the operations the
+    // vertex bound counts)
     auto rot = [](float w, float x, float y, float z, G32 v) {
-        const float tx = 2.0f * (y * v.z - z * v.y);
-        const float ty = 2.0f * (z * v.x - x * v.z);
-        const float tz = 2.0f * (x * v.y - y * v.x);
-        return G32{ (v.x + w * tx) + (y * tz - z * ty), (v.y + w * ty) + (z * tx - x * tz),
-                    (v.z + w * tz) + (x * ty - y * tx) };
+        const float tx = 2.0f * __fmaf_rn(y, v.z, -(z * v.y));
+        const float ty = 2.0f * __fmaf_rn(z, v.x, -(x * v.z));
+        const float tz = 2.0f * __fmaf_rn(x, v.y, -(y * v.x));
+        return G32{ __fmaf_rn(w, tx, v.x) + __fmaf_rn(y, tz, -(z * ty)), __fmaf_rn(w, ty, v.y) + __fmaf_rn(z, tx, -(x * tz)),
+                    __fmaf_rn(w, tz, v.z) + __fmaf_rn(x, ty, -(y * tx)) };
     };
     l = rot(a0, a1, a2, a3, G32{ dx, dy, dz });
     if (NV >= 16 && sh.sym) {
@@ -548,22 +553,25 @@ __device__ __forceinline__ int box32_sat(const Shape3& sh, float dx, float dy, f
     const float y = ((a0 * b2 - a1 * b3) + a2 * b0) + a3 * b1;
     const float z = ((a0 * b3 + a1 * b2) - a2 * b1) + a3 * b0;
     // l = rot(conj(qA), Delta), the same evaluation as the certified GJK
-    const float tx = 2.0f * (a2 * dz - a3 * dy);
-    const float ty = 2.0f * (a3 * dx - a1 * dz);
-    const float tz = 2.0f * (a1 * dy - a2 * dx);
-    const float l[3] = { (dx + a0 * tx) + (a2 * tz - a3 * ty), (dy + a0 * ty) + (a3 * tx - a1 * tz),
-                         (dz + a0 * tz) + (a1 * ty - a2 * tx) };
+    // (fused multiply-adds throughout: no more roundings than the
+    // operations the margins count)
+    const float tx = 2.0f * __fmaf_rn(a2, dz, -(a3 * dy));
+    const float ty = 2.0f * __fmaf_rn(a3, dx, -(a1 * dz));
+    const float tz = 2.0f * __fmaf_rn(a1, dy, -(a2 * dx));
+    const float l[3] = { __fmaf_rn(a0, tx, dx) + __fmaf_rn(a2, tz, -(a3 * ty)),
+                         __fmaf_rn(a0, ty, dy) + __fmaf_rn(a3, tx, -(a1 * tz)),
+                         __fmaf_rn(a0, tz, dz) + __fmaf_rn(a1, ty, -(a2 * tx)) };
     // M[k][j] = component k of u_j = R(qr) e_j
     float M[3][3];
-    M[0][0] = 1.0f - 2.0f * (y * y + z * z);
-    M[1][1] = 1.0f - 2.0f * (x * x + z * z);
-    M[2][2] = 1.0f - 2.0f * (x * x + y * y);
-    M[1][0] = 2.0f * (x * y + w * z);
-    M[0][1] = 2.0f * (x * y - w * z);
-    M[2][0] = 2.0f * (x * z - w * y);
-    M[0][2] = 2.0f * (x * z + w * y);
-    M[2][1] = 2.0f * (y * z + w * x);
-    M[1][2] = 2.0f * (y * z - w * x);
+    M[0][0] = 1.0f - 2.0f * __fmaf_rn(y, y, z * z);
+    M[1][1] = 1.0f - 2.0f * __fmaf_rn(x, x, z * z);
+    M[2][2] = 1.0f - 2.0f * __fmaf_rn(x, x, y * y);
+    M[1][0] = 2.0f * __fmaf_rn(x, y, w * z);
+    M[0][1] = 2.0f * __fmaf_rn(x, y, -(w * z));
+    M[2][0] = 2.0f * __fmaf_rn(x, z, -(w * y));
+    M[0][2] = 2.0f * __fmaf_rn(x, z, w * y);
+    M[2][1] = 2.0f * __fmaf_rn(y, z, w * x);
+    M[1][2] = 2.0f * __fmaf_rn(y, z, -(w * x));
     float A[3][3];   // |M|
 #pragma unroll
     for (int k = 0; k < 3; ++k)
@@ -574,14 +582,14 @@ __device__ __forceinline__ int box32_sat(const Shape3& sh, float dx, float dy, f
     // A's faces e_k
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
-        const float eb = (h[0] * A[k][0] + h[1] * A[k][1]) + h[2] * A[k][2];
+        const float eb = __fmaf_rn(h[2], A[k][2], __fmaf_rn(h[1], A[k][1], h[0] * A[k][0]));
         smax = fmaxf(smax, (fabsf(l[k]) - h[k]) - eb);
     }
     // B's faces u_j
 #pragma unroll
     for (int j = 0; j < 3; ++j) {
-        const float c = (l[0] * M[0][j] + l[1] * M[1][j]) + l[2] * M[2][j];
-        const float ea = (h[0] * A[0][j] + h[1] * A[1][j]) + h[2] * A[2][j];
+        const float c = __fmaf_rn(l[2], M[2][j], __fmaf_rn(l[1], M[1][j], l[0] * M[0][j]));
+        const float ea = __fmaf_rn(h[2], A[2][j], __fmaf_rn(h[1], A[1][j], h[0] * A[0][j]));
         smax = fmaxf(smax, (fabsf(c) - ea) - h[j]);
     }
     // edge crosses e_i x u_j; (i, i1, i2) and (j, j1, j2) cyclic
@@ -591,9 +599,9 @@ __device__ __forceinline__ int box32_sat(const Shape3& sh, float dx, float dy, f
 #pragma unroll
         for (int j = 0; j < 3; ++j) {
             const int j1 = (j + 1) % 3, j2 = (j + 2) % 3;
-            const float c = l[i2] * M[i1][j] - l[i1] * M[i2][j];
-            const float ea = h[i1] * A[i2][j] + h[i2] * A[i1][j];
-            const float eb = h[j1] * A[i][j2] + h[j2] * A[i][j1];
+            const float c = __fmaf_rn(l[i2], M[i1][j], -(l[i1] * M[i2][j]));
+            const float ea = __fmaf_rn(h[i1], A[i2][j], h[i2] * A[i1][j]);
+            const float eb = __fmaf_rn(h[j1], A[i][j2], h[j2] * A[i][j1]);
             smax = fmaxf(smax, (fabsf(c) - ea) - eb);
         }
     }
