@@ -417,7 +417,9 @@ def run_ours(args):
 
     # ---- roofline of the dominant kernel (the set kernel), CUDA events live
     roofline = set_kernel_roofline(b, stream, 8, p32)
-    roofline["kernel"] = "k_set2d (checkerboard set), 2^24-pentagon system"
+    roofline["kernel"] = ("k_set2d_direct<5> (checkerboard set, one lane per active cell)" if lanes == 0 else
+                          f"k_set2d<{lanes}, 1, 5> (checkerboard set, {lanes} lanes per cell)") + \
+        ", 2^24-pentagon system"
     roofline["peak_source"] = "FP32 fused multiply-add rate measured in this run (hpmc_measure_fma_peak)"
     roofline["traffic_note"] = ("DRAM bytes of this kernel come from a separate ncu capture of a 2^22-particle "
                                 "instance (kept with the profiles), not from this run")
