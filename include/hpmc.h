@@ -146,11 +146,10 @@ int hpmc_set_precision(hpmc_t h, int mode);
 
 /*
  * hpmc_set_group_size -- lanes per active cell in the set kernel (1, 2, 4, 8,
- * 16 or 32; or 0: the 2D direct kernel of the FP32-filtered form, one lane
- * per cell reading its neighbours without shared-memory staging and
- * skipping the stencil layers a trial cannot reach -- INVALID_ARG in 3D or
- * in the plain FP64 form, and a later switch to FP64 makes the next sweep
- * return INVALID_ARG until another size is set) and warps per block (1..16,
+ * 16 or 32; or 0: the 2D direct kernel, one lane per cell reading its
+ * neighbours without shared-memory staging; the FP32-filtered form also
+ * skips the stencil layers a trial cannot reach -- INVALID_ARG in 3D) and
+ * warps per block (1..16,
  * at most the kernel's launch bound: 8 warps for 8+ lanes per cell in 2D and
  * for the direct kernel, 6 for fewer, 8 in 3D; INVALID_ARG beyond it).  The
  * checkerboard schedule of Sec. 2.5.2 is the same for every choice, so the

@@ -396,7 +396,7 @@ SetKernel pick_kernel(const hpmc_batch* h)
     const bool f32 = h->precision == HPMC_FP32_FILTERED;
     if (h->dim == 2) {
         const bool fixed = h->nv == 5;
-        if (h->G == 0) return f32 ? set2d_direct_kernel(fixed) : SetKernel{ nullptr, 0 };
+        if (h->G == 0) return set2d_direct_kernel(fixed, f32);
         return f32 ? set2d_f32_kernel(h->G, fixed) : set2d_f64_kernel(h->G, fixed);
     }
     if (h->G == 0) return SetKernel{ nullptr, 0 };

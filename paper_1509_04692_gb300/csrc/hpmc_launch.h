@@ -20,8 +20,8 @@ SetKernel set2d_f64_kernel(int G, bool fixed_nv);
 SetKernel set3d_f32_kernel(int G, int nv);
 SetKernel set3d_f64_kernel(int G, int nv);
 SetKernel set3d_f32_nv20(int G);
-// 2D direct kernel (one lane per cell, no staging), FP32-filtered form
-SetKernel set2d_direct_kernel(bool fixed_nv);
+// 2D direct kernel (one lane per cell, no staging), FP32-filtered or plain FP64 form
+SetKernel set2d_direct_kernel(bool fixed_nv, bool f32);
 SetKernel set3d_f64_nv20(int G);
 
 // select table of the latency-regime set kernels (selects.cu): bytes of one

@@ -28,6 +28,12 @@
 // rare FP32 verdicts the certified margins cannot decide, exactly as in the
 // other set kernels; it needs no select table, so no table kernel competes
 // with the cell-list rebuild for the FP64 pipe.
+//
+// The plain FP64 form (F32 = false) keeps the structure with the contract's
+// own arithmetic: the FP64 trial at the proposal, every stencil cell (the
+// reach test is certified for the FP32 trial only), the FP64 circumsphere
+// cull on positions read through L1 and the FP64 separating-axis test in the
+// drain.
 #pragma once
 #include "hpmc_sweep2d.cuh"
 
@@ -105,7 +111,7 @@ __device__ __noinline__ bool direct_overlap64(const Shape2& sh, const Rep& rp, c
 // each a certified FP32 separating-axis test (the FP64 contract when the
 // FP32 verdict is not certified); a pair whose owner already overlaps is
 // skipped.  Adds the tests run and the FP64 re-checks to chk, rechk.
-template <int NV>
+template <int NV, bool F32>
 __device__ __forceinline__ void direct_drain_round(Direct2Warp& ws, int lane, int base, int np, const Shape2& sh,
                                                    const Rep& rp, const Bufs& B, unsigned& chk, unsigned& rechk)
 {
@@ -114,14 +120,23 @@ __device__ __forceinline__ void direct_drain_round(Direct2Warp& ws, int lane, in
         const int g2 = ws.qg[p];
         if (!((ws.ovmask >> g2) & 1u)) {
             chk += 1;
-            const float2 d2 = ws.qd[p], zb = ws.qz[p], za = ws.tz[g2];
-            const int v = sat32<NV>(sh, rp.sat_e, d2.x, d2.y, za.x, za.y, zb.x, zb.y);
-            bool pov = v == 1;
-            if (v == 2) {
-                rechk += 1;
-                const uint32_t w[6] = { ws.wd[0][g2], ws.wd[1][g2], ws.wd[2][g2],
-                                        ws.wd[3][g2], ws.wd[4][g2], ws.wd[5][g2] };
-                pov = direct_overlap64<NV>(sh, rp, B, w, ws.ea[g2], ws.qe[p]);
+            bool pov;
+            if constexpr (F32) {
+                const float2 d2 = ws.qd[p], zb = ws.qz[p], za = ws.tz[g2];
+                const int v = sat32<NV>(sh, rp.sat_e, d2.x, d2.y, za.x, za.y, zb.x, zb.y);
+                pov = v == 1;
+                if (v == 2) {
+                    rechk += 1;
+                    const uint32_t w[6] = { ws.wd[0][g2], ws.wd[1][g2], ws.wd[2][g2],
+                                            ws.wd[3][g2], ws.wd[4][g2], ws.wd[5][g2] };
+                    pov = direct_overlap64<NV>(sh, rp, B, w, ws.ea[g2], ws.qe[p]);
+                }
+            } else {
+                // FP64 form: the contract's test on the owner's trial (ws.acc)
+                const uint32_t gB = ws.qe[p];
+                const double Dx = min_image(B.px[gB] - ws.acc[0][g2], rp.L[0], rp.halfL[0]);
+                const double Dy = min_image(B.py[gB] - ws.acc[1][g2], rp.L[1], rp.halfL[1]);
+                pov = overlap2d64<NV>(sh, Dx, Dy, ws.acc[2][g2], ws.acc[3][g2], B.q0[gB], B.q1[gB]);
             }
             if (pov) atomicOr(&ws.ovmask, 1u << g2);
         }
@@ -131,16 +146,16 @@ __device__ __forceinline__ void direct_drain_round(Direct2Warp& ws, int lane, in
 
 // the same round out of line, for a queue about to overflow inside the cull
 // loop (rare): the loop then carries no separating-axis registers
-template <int NV>
+template <int NV, bool F32>
 __device__ __noinline__ uint2 direct_drain_round_out(Direct2Warp& ws, int lane, int base, int np, const Shape2& sh,
                                                      const Rep& rp, const Bufs& B)
 {
     unsigned chk = 0, rechk = 0;
-    direct_drain_round<NV>(ws, lane, base, np, sh, rp, B, chk, rechk);
+    direct_drain_round<NV, F32>(ws, lane, base, np, sh, rp, B, chk, rechk);
     return make_uint2(chk, rechk);
 }
 
-template <int NV>
+template <int NV, bool F32>
 __global__ void __launch_bounds__(256, 2)
 k_set2d_direct(Dev dv, Shape2 sh, int nxt, int sigma, const uint32_t* __restrict__ item_base)
 {
@@ -211,8 +226,25 @@ k_set2d_direct(Dev dv, Shape2 sh, int nxt, int sigma, const uint32_t* __restrict
             int status = 0;                                // 0 idle, 1 in the cell, 2 left it
             uint32_t eA = 0;
             float4 tr = make_float4(0.f, 0.f, 0.f, 0.f);
-            cp_async_wait_all();                           // the last accept's operands
-            if (live_cell) {
+            if constexpr (F32) cp_async_wait_all();        // the last accept's operands
+            if (!F32 && live_cell) {
+                // FP64 form: the contract's trial itself, kept in ws.acc for the
+                // cull, the separating-axis tests and the accept
+                c_moves += 1;
+                const uint4 b0 = move_block(seed, sweep, (uint32_t)sigma, cell_local, k, 0);
+                const uint4 b1 = move_block(seed, sweep, (uint32_t)sigma, cell_local, k, 1);
+                eA = cb + __umulhi(b0.x, n_c);
+                const Trial2 t2 = propose2d(rp, B.px[eA], B.py[eA], B.q0[eA], B.q1[eA], b0.y, b0.z, b0.w, b1.x, b1.y,
+                                            b1.z);
+                ws.acc[0][lane] = t2.x;
+                ws.acc[1][lane] = t2.y;
+                ws.acc[2][lane] = t2.c;
+                ws.acc[3][lane] = t2.s;
+                status = (cell_axis(t2.x, dv.shift[3 * r], rp.L[0], rp.inv_w[0], rp.nc[0]) == ix &&
+                          cell_axis(t2.y, dv.shift[3 * r + 1], rp.L[1], rp.inv_w[1], rp.nc[1]) == iy) ? 1 : 2;
+                ws.ea[lane] = eA;
+            }
+            if (F32 && live_cell) {
                 c_moves += 1;
                 // Philox words of select k of this cell (Sec. 2.5: one stream per trial move)
                 const uint4 b0 = move_block(seed, sweep, (uint32_t)sigma, cell_local, k, 0);
@@ -263,8 +295,10 @@ k_set2d_direct(Dev dv, Shape2 sh, int nxt, int sigma, const uint32_t* __restrict
             // ---- the stencil cells within reach of the trial, and their candidates
             uint32_t mask = 0u, Tn = 0u;
             if (status == 1) {
-                const bool need_l = !(tr.x > rp.reach_lo[0]), need_r = !(tr.x < rp.reach_hi[0]);
-                const bool need_b = !(tr.y > rp.reach_lo[1]), need_t = !(tr.y < rp.reach_hi[1]);
+                // (FP64 form: every stencil cell; the reach test is certified
+                // for the FP32 trial only)
+                const bool need_l = !F32 || !(tr.x > rp.reach_lo[0]), need_r = !F32 || !(tr.x < rp.reach_hi[0]);
+                const bool need_b = !F32 || !(tr.y > rp.reach_lo[1]), need_t = !F32 || !(tr.y < rp.reach_hi[1]);
 #pragma unroll
                 for (int q = 0; q < 9; ++q) {
                     const int ox = q % 3 - 1, oy = q / 3 - 1;
@@ -289,6 +323,16 @@ k_set2d_direct(Dev dv, Shape2 sh, int nxt, int sigma, const uint32_t* __restrict
             uint32_t ec = 0, eend = 0;
             float oxc = 0.f, oyc = 0.f;                    // FP32 offset of the cursor's cell
             float4 fc = make_float4(0.f, 0.f, 0.f, 0.f);
+            double xc = 0.0, yc = 0.0;                     // FP64 form: the next candidate's position
+            const double tx64 = F32 ? 0.0 : ws.acc[0][lane], ty64 = F32 ? 0.0 : ws.acc[1][lane];
+            auto fetch = [&]() {
+                if constexpr (F32) {
+                    fc = B.f4a[ec];
+                } else {
+                    xc = B.px[ec];
+                    yc = B.py[ec];
+                }
+            };
             // the cell the cursor enters next: its range and offset
             auto enter = [&]() {
                 const int kq = __ffs(m_left) - 1;
@@ -302,7 +346,7 @@ k_set2d_direct(Dev dv, Shape2 sh, int nxt, int sigma, const uint32_t* __restrict
             };
             if (Tn) {
                 enter();
-                fc = B.f4a[ec];
+                fetch();
             }
 #pragma unroll 1
             for (uint32_t i = 0; i < trips; ++i) {
@@ -310,14 +354,26 @@ k_set2d_direct(Dev dv, Shape2 sh, int nxt, int sigma, const uint32_t* __restrict
                 const uint32_t e = ec;
                 const float offx = oxc, offy = oyc;
                 const float4 f = fc;
+                const double xe = xc, ye = yc;
                 if (live && i + 1 < Tn) {                  // advance and prefetch
                     ec += 1u;
                     if (ec == eend) enter();
-                    fc = B.f4a[ec];
+                    fetch();
                 }
                 bool keep = false;
                 float dlx = 0.f, dly = 0.f;
-                if (live && e != eA) {
+                if (!F32 && live && e != eA) {
+                    // FP64 form: the contract's circumsphere cull
+                    const double Dx = min_image(xe - tx64, rp.L[0], rp.halfL[0]);
+                    const double Dy = min_image(ye - ty64, rp.L[1], rp.halfL[1]);
+                    keep = (Dx * Dx + Dy * Dy) <= sh.rc2;
+                    if (NV == 0 && sh.round && keep) {     // disks: a kept pair is the overlap
+                        keep = false;
+                        c_chk += 1;
+                        ov = true;
+                    }
+                }
+                if (F32 && live && e != eA) {
                     dlx = __fsub_rn(__fadd_rn(f.x, offx), tr.x);
                     dly = __fsub_rn(__fadd_rn(f.y, offy), tr.y);
                     const float q32 = __fmaf_rn(dlx, dlx, __fmul_rn(dly, dly));
@@ -340,15 +396,17 @@ k_set2d_direct(Dev dv, Shape2 sh, int nxt, int sigma, const uint32_t* __restrict
                 const unsigned bal = __ballot_sync(FULL, keep);
                 if (keep) {
                     const int p = qn + __popc(bal & lt_mask);
-                    ws.qd[p] = make_float2(dlx, dly);
-                    ws.qz[p] = make_float2(f.z, f.w);
+                    if (F32) {
+                        ws.qd[p] = make_float2(dlx, dly);
+                        ws.qz[p] = make_float2(f.z, f.w);
+                    }
                     ws.qe[p] = e;
                     ws.qg[p] = (uint8_t)lane;
                 }
                 qn += __popc(bal);
                 if (qn > W::QCAP - 32) {                   // room for one more trip's survivors
                     __syncwarp();
-                    const uint2 cr = direct_drain_round_out<NV>(ws, lane, qn - 32, 32, sh, rp, B);
+                    const uint2 cr = direct_drain_round_out<NV, F32>(ws, lane, qn - 32, 32, sh, rp, B);
                     c_chk += cr.x;
                     c_rechk += cr.y;
                     qn -= 32;
@@ -359,7 +417,7 @@ k_set2d_direct(Dev dv, Shape2 sh, int nxt, int sigma, const uint32_t* __restrict
             __syncwarp();
             while (qn > 0) {
                 const int np = min(qn, 32);
-                direct_drain_round<NV>(ws, lane, qn - np, np, sh, rp, B, c_chk, c_rechk);
+                direct_drain_round<NV, F32>(ws, lane, qn - np, np, sh, rp, B, c_chk, c_rechk);
                 qn -= np;
             }
             ov = ov || ((ws.ovmask >> lane) & 1u);
@@ -374,10 +432,18 @@ k_set2d_direct(Dev dv, Shape2 sh, int nxt, int sigma, const uint32_t* __restrict
                     c_rov += 1;
                 } else {
                     c_acc += 1;
-                    cp_async_wait_all();
-                    const Trial2 t2 = propose2d(rp, ws.acc[0][lane], ws.acc[1][lane], ws.acc[2][lane],
-                                                ws.acc[3][lane], ws.wd[0][lane], ws.wd[1][lane], ws.wd[2][lane],
-                                                ws.wd[3][lane], ws.wd[4][lane], ws.wd[5][lane]);
+                    Trial2 t2;
+                    if constexpr (F32) {
+                        cp_async_wait_all();
+                        t2 = propose2d(rp, ws.acc[0][lane], ws.acc[1][lane], ws.acc[2][lane], ws.acc[3][lane],
+                                       ws.wd[0][lane], ws.wd[1][lane], ws.wd[2][lane], ws.wd[3][lane],
+                                       ws.wd[4][lane], ws.wd[5][lane]);
+                    } else {
+                        t2.x = ws.acc[0][lane];                // the trial computed at the proposal
+                        t2.y = ws.acc[1][lane];
+                        t2.c = ws.acc[2][lane];
+                        t2.s = ws.acc[3][lane];
+                    }
                     B.px[eA] = t2.x;
                     B.py[eA] = t2.y;
                     B.q0[eA] = t2.c;

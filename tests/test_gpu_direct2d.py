@@ -3,7 +3,8 @@ active cell, neighbours read through L1, unreachable stencil columns and
 rows skipped) against the CPU oracle, bit for bit: small and ragged grids,
 cells much wider than the circumdiameter (where the skipping acts), many
 selects (beyond the select table), disks, replica batches, volume moves that
-change the grid, and every block shape."""
+change the grid, and every block shape; and the same kernel's plain FP64
+form on the ragged, wide-cell, disk and batch cases."""
 import numpy as np
 import pytest
 
@@ -27,9 +28,9 @@ def _oracle(s, n, sweep0=0, pos=None, ori=None):
     return p, q, [int(x) for x in c[:3]]
 
 
-def _gpu(s, n, warps=4, graph=False):
+def _gpu(s, n, warps=4, graph=False, prec=F32):
     b = hpmc.from_system(s)
-    b.set_precision(F32)
+    b.set_precision(prec)
     b.set_group_size(DIRECT, warps)
     b.sweep(n, graph=graph)
     c = b.counters()
@@ -173,3 +174,52 @@ def test_direct_volume_moves_change_the_grid():
     b.close()
     assert acc_g == acc_o and 0 < sum(acc_o) < len(acc_o) and len(nc_seen) > 1
     assert np.array_equal(gp, p) and np.array_equal(gq, q)
+
+
+# ---- the plain FP64 form of the direct kernel
+
+@pytest.mark.parametrize("warps", [1, 8])
+def test_direct_fp64_rsa1024(warps):
+    s = _rsa()
+    _same(_gpu(s, 20, warps=warps, prec=F64), _oracle(s, 20), f"FP64 warps {warps}")
+
+
+@pytest.mark.parametrize("case", ["small_box", "dilute", "heptagon", "odd_N", "wide_cells"])
+def test_direct_fp64_cases(case):
+    if case == "small_box":
+        s = inputs.pentagon_system(12, 0.30, seed=3, d=0.3, a=0.5)
+    elif case == "dilute":
+        s = inputs.pentagon_system(300, 0.02, seed=5, d=0.4, a=1.0)
+    elif case == "heptagon":
+        base = inputs.pentagon_system(900, 0.35, seed=8)
+        s = inputs.System(name=case, dim=2, verts=inputs.regular_polygon(7, 0.5), L=base.L, pos=base.pos,
+                          orient=base.orient, phi=0.0, seed=9)
+    elif case == "odd_N":
+        s = inputs.pentagon_system(1237, 0.45, seed=10, nselect=3)
+    else:
+        s = inputs.large2d(42, N=40000)
+        s.w_min = 2.6
+    got = _gpu(s, 30, graph=True, prec=F64)
+    _same(got, _oracle(s, 30), f"FP64 {case}")
+    assert got[3]["fp64_rechecks"] == 0
+
+
+def test_direct_fp64_disks_and_batch():
+    s = inputs.disk_system(1024, 0.60, 5, d=0.12, w_min=1.06)
+    o = orc.OracleSystem(2, s.L, 0.5, w_min=s.w_min)
+    o.set_moves(s.d, s.a, s.nselect, s.seed)
+    p, q = s.pos.copy(), s.orient.copy()
+    rc = o.sweep(p, q, 0, 30)
+    _same(_gpu(s, 30, warps=2, prec=F64), (p, q, [int(x) for x in rc[:3]]), "FP64 disks")
+    systems = [inputs.pentagon_system(N, phi, seed, gen_seed=seed)
+               for N, phi, seed in [(300, 0.45, 42), (777, 0.62, 43), (5000, 0.40, 45)]]
+    b = hpmc.from_systems(systems)
+    b.set_precision(F64)
+    b.set_group_size(DIRECT, 4)
+    b.sweep(25, graph=True)
+    for r, sr in enumerate(systems):
+        p, q, sw = b.get_state(r)
+        c = b.counters(r)
+        assert sw == 25
+        _same((p, q, [c["accept"], c["reject_overlap"], c["reject_boundary"]]), _oracle(sr, 25), f"FP64 replica {r}")
+    b.close()
