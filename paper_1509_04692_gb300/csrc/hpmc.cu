@@ -294,6 +294,12 @@ int rep_geometry(const hpmc_batch* h, const HostRep& hr, Rep& rp)
         const double reach = h->Rc * 2.0 * (1.0 + 4.0 * kU64) + g.e_in;
         rp.reach_lo[a] = f32_up(reach);
         rp.reach_hi[a] = f32_down(rp.w[a] - reach);
+        // the FP64 trial coordinate (x' - s, + L, - i w: a few roundings of
+        // magnitude L) in place of the FP32 one: the cell rule's and these
+        // roundings together stay far below 32 u64 L + 4 u64 w
+        const double reach64 = h->Rc * 2.0 * (1.0 + 4.0 * kU64) + 32.0 * kU64 * rp.L[a] + 4.0 * kU64 * rp.w[a];
+        rp.reach64_lo[a] = reach64;
+        rp.reach64_hi[a] = rp.w[a] - reach64;
     }
     // FP32 cell rule of the rebuild: x and s truncated to FP32 (relative
     // error below 2^-23), y32 = x32 - s32 (+ L32), t32 = y32 * inv_w32 (each

@@ -30,10 +30,10 @@
 // with the cell-list rebuild for the FP64 pipe.
 //
 // The plain FP64 form (F32 = false) keeps the structure with the contract's
-// own arithmetic: the FP64 trial at the proposal, every stencil cell (the
-// reach test is certified for the FP32 trial only), the FP64 circumsphere
-// cull on positions read through L1 and the FP64 separating-axis test in the
-// drain.
+// own arithmetic: the FP64 trial at the proposal (whose cell-relative
+// coordinate drives the same skipping, with FP64 rounding bounds), the FP64
+// circumsphere cull on positions read through L1 and the FP64
+// separating-axis test in the drain.
 #pragma once
 #include "hpmc_sweep2d.cuh"
 
@@ -226,6 +226,7 @@ k_set2d_direct(Dev dv, Shape2 sh, int nxt, int sigma, const uint32_t* __restrict
             int status = 0;                                // 0 idle, 1 in the cell, 2 left it
             uint32_t eA = 0;
             float4 tr = make_float4(0.f, 0.f, 0.f, 0.f);
+            double rx64 = 0.0, ry64 = 0.0;                 // FP64 form: the trial's cell-relative position
             if constexpr (F32) cp_async_wait_all();        // the last accept's operands
             if (!F32 && live_cell) {
                 // FP64 form: the contract's trial itself, kept in ws.acc for the
@@ -242,6 +243,8 @@ k_set2d_direct(Dev dv, Shape2 sh, int nxt, int sigma, const uint32_t* __restrict
                 ws.acc[3][lane] = t2.s;
                 status = (cell_axis(t2.x, dv.shift[3 * r], rp.L[0], rp.inv_w[0], rp.nc[0]) == ix &&
                           cell_axis(t2.y, dv.shift[3 * r + 1], rp.L[1], rp.inv_w[1], rp.nc[1]) == iy) ? 1 : 2;
+                rx64 = cell_coord_bits(t2.x, dv.shift[3 * r], rp.L[0]) - (double)ix * rp.w[0];
+                ry64 = cell_coord_bits(t2.y, dv.shift[3 * r + 1], rp.L[1]) - (double)iy * rp.w[1];
                 ws.ea[lane] = eA;
             }
             if (F32 && live_cell) {
@@ -295,10 +298,11 @@ k_set2d_direct(Dev dv, Shape2 sh, int nxt, int sigma, const uint32_t* __restrict
             // ---- the stencil cells within reach of the trial, and their candidates
             uint32_t mask = 0u, Tn = 0u;
             if (status == 1) {
-                // (FP64 form: every stencil cell; the reach test is certified
-                // for the FP32 trial only)
-                const bool need_l = !F32 || !(tr.x > rp.reach_lo[0]), need_r = !F32 || !(tr.x < rp.reach_hi[0]);
-                const bool need_b = !F32 || !(tr.y > rp.reach_lo[1]), need_t = !F32 || !(tr.y < rp.reach_hi[1]);
+                // (the FP64 form tests its FP64 trial coordinate)
+                const bool need_l = F32 ? !(tr.x > rp.reach_lo[0]) : !(rx64 > rp.reach64_lo[0]);
+                const bool need_r = F32 ? !(tr.x < rp.reach_hi[0]) : !(rx64 < rp.reach64_hi[0]);
+                const bool need_b = F32 ? !(tr.y > rp.reach_lo[1]) : !(ry64 > rp.reach64_lo[1]);
+                const bool need_t = F32 ? !(tr.y < rp.reach_hi[1]) : !(ry64 < rp.reach64_hi[1]);
 #pragma unroll
                 for (int q = 0; q < 9; ++q) {
                     const int ox = q % 3 - 1, oy = q / 3 - 1;

@@ -72,6 +72,7 @@ struct Rep {
     float reach_hi[3];       // trial rel' < reach_hi[a]: the upper neighbour layer is beyond the cull
     // FP32 cell rule of the rebuild (certified; see cell_axis_f32)
     float L32[3], inv_w32[3];
+    double reach64_lo[3], reach64_hi[3];  // the same reach for the FP64 trial coordinate (FP64 direct kernel)
     float cell_ey[3];        // bound on |y32 - (x - s)| (the sign test)
     float cell_et[3];        // bound on |t32 - t64| in cells (the boundary test)
     float box_esep;          // 3D boxes: a separating-axis gap above this certifies separation
