@@ -121,3 +121,140 @@ def test_interior_origin(prog):
     # origin on a face (the centroid of vertices 1-3 moved to it): not interior
     t = _tetra()
     assert _run(prog, t - (t[1] + t[2] + t[3]) / 3.0)["mpr"] == "0"
+
+
+# ---- the FP32 box test's error bound, checked numerically
+#
+# The separating-axis test of two boxes (box32_sat) evaluates, in FP32 from
+# the FP32-cast inputs, s(n) = |l.n| - sum_k h_k |n_k| - extent_B(n) on 15
+# axes n; its certificate needs |s(n) - s*(n)| <= E_sep, s* the same value
+# for the exact boxes along the same n, and |s*(n) - s*(n*)| <= E_ov - E_sep
+# for the exact axis n* the FP32 axis stands for.  Here the FP32 arithmetic
+# is emulated in numpy (float32 operations; a fused multiply-add as the
+# float64 sum of the exact float32 product, rounded once more to float32,
+# which is within the same one-rounding bound), the exact values in float64,
+# and the largest errors over many random pairs are compared with E_sep and
+# E_ov as the library derives them (printed relative to 2R by shape_host).
+
+F = np.float32
+
+
+def _fma(a, b, c):
+    return (a.astype(np.float64) * b.astype(np.float64) + c.astype(np.float64)).astype(F)
+
+
+def _box_axes_fp32(h32, d32, qa32, qb32):
+    a0, a1, a2, a3 = qa32[:, 0], -qa32[:, 1], -qa32[:, 2], -qa32[:, 3]
+    b0, b1, b2, b3 = qb32[:, 0], qb32[:, 1], qb32[:, 2], qb32[:, 3]
+    w = ((a0 * b0 - a1 * b1) - a2 * b2) - a3 * b3
+    x = ((a0 * b1 + a1 * b0) + a2 * b3) - a3 * b2
+    y = ((a0 * b2 - a1 * b3) + a2 * b0) + a3 * b1
+    z = ((a0 * b3 + a1 * b2) - a2 * b1) + a3 * b0
+    dx, dy, dz = d32[:, 0], d32[:, 1], d32[:, 2]
+    two = F(2.0)
+    tx = two * _fma(a2, dz, -(a3 * dy))
+    ty = two * _fma(a3, dx, -(a1 * dz))
+    tz = two * _fma(a1, dy, -(a2 * dx))
+    l = [_fma(a0, tx, dx) + _fma(a2, tz, -(a3 * ty)), _fma(a0, ty, dy) + _fma(a3, tx, -(a1 * tz)),
+         _fma(a0, tz, dz) + _fma(a1, ty, -(a2 * tx))]
+    one = F(1.0)
+    M = [[None] * 3 for _ in range(3)]
+    M[0][0] = one - two * _fma(y, y, z * z)
+    M[1][1] = one - two * _fma(x, x, z * z)
+    M[2][2] = one - two * _fma(x, x, y * y)
+    M[1][0] = two * _fma(x, y, w * z)
+    M[0][1] = two * _fma(x, y, -(w * z))
+    M[2][0] = two * _fma(x, z, -(w * y))
+    M[0][2] = two * _fma(x, z, w * y)
+    M[2][1] = two * _fma(y, z, w * x)
+    M[1][2] = two * _fma(y, z, -(w * x))
+    A = [[np.abs(M[k][j]) for j in range(3)] for k in range(3)]
+    h = [F(v) for v in h32]
+    s, axes = [], []
+    for k in range(3):
+        eb = _fma(np.full_like(dx, h[2]), A[k][2], _fma(np.full_like(dx, h[1]), A[k][1], h[0] * A[k][0]))
+        s.append((np.abs(l[k]) - h[k]) - eb)
+        n = np.zeros((len(dx), 3))
+        n[:, k] = 1.0
+        axes.append(("e", k, None, n))
+    for j in range(3):
+        c = _fma(l[2], M[2][j], _fma(l[1], M[1][j], l[0] * M[0][j]))
+        ea = _fma(np.full_like(dx, h[2]), A[2][j], _fma(np.full_like(dx, h[1]), A[1][j], h[0] * A[0][j]))
+        s.append((np.abs(c) - ea) - h[j])
+        axes.append(("u", None, j, np.stack([M[0][j], M[1][j], M[2][j]], 1).astype(np.float64)))
+    for i in range(3):
+        i1, i2 = (i + 1) % 3, (i + 2) % 3
+        for j in range(3):
+            j1, j2 = (j + 1) % 3, (j + 2) % 3
+            c = _fma(l[i2], M[i1][j], -(l[i1] * M[i2][j]))
+            ea = _fma(np.full_like(dx, h[i1]), A[i2][j], h[i2] * A[i1][j])
+            eb = _fma(np.full_like(dx, h[j1]), A[i][j2], h[j2] * A[i][j1])
+            s.append((np.abs(c) - ea) - eb)
+            n = np.zeros((len(dx), 3))
+            n[:, i1] = -M[i2][j]
+            n[:, i2] = M[i1][j]
+            axes.append(("x", i, j, n))
+    return np.stack(s, 1).astype(np.float64), axes
+
+
+def _rot64(q):
+    w, x, y, z = q[:, 0], q[:, 1], q[:, 2], q[:, 3]
+    R = np.empty((len(q), 3, 3))
+    R[:, 0, 0] = 1 - 2 * (y * y + z * z)
+    R[:, 1, 1] = 1 - 2 * (x * x + z * z)
+    R[:, 2, 2] = 1 - 2 * (x * x + y * y)
+    R[:, 1, 0] = 2 * (x * y + w * z)
+    R[:, 0, 1] = 2 * (x * y - w * z)
+    R[:, 2, 0] = 2 * (x * z - w * y)
+    R[:, 0, 2] = 2 * (x * z + w * y)
+    R[:, 2, 1] = 2 * (y * z + w * x)
+    R[:, 1, 2] = 2 * (y * z - w * x)
+    return R
+
+
+def _s_exact(h, l, U, n):
+    # |l.n| - sum_k h_k |n_k| - sum_m h_m |n.u_m| for the exact boxes
+    c = np.abs(np.einsum("pi,pi->p", l, n))
+    ea = (np.abs(n) * h).sum(1)
+    eb = sum(h[m] * np.abs(np.einsum("pi,pi->p", n, U[:, :, m])) for m in range(3))
+    return c - ea - eb
+
+
+@pytest.mark.parametrize("hh", [(0.5, 0.5, 0.5), (0.7, 0.35, 0.2)])
+def test_box_test_errors_within_its_margins(prog, hh):
+    h = np.array(hh)
+    R = float(np.linalg.norm(h))
+    r = _run(prog, _cuboid(*hh))
+    e_sep = (float(r["sep32"]) - 4e-6 * 1.0001) / 2            # E_sep / 2R
+    e_ov = (float(r["ov32"]) - 1e-9 * 1.0001) / 2              # E_ov / 2R
+    rng = np.random.default_rng(11)
+    n = 200000
+    qa = rng.normal(size=(n, 4))
+    qa /= np.linalg.norm(qa, axis=1)[:, None]
+    qb = rng.normal(size=(n, 4))
+    qb /= np.linalg.norm(qb, axis=1)[:, None]
+    d = rng.normal(size=(n, 3))
+    d *= (2 * R * rng.uniform(0, 1, n) ** (1 / 3) / np.linalg.norm(d, axis=1))[:, None]
+    s32, axes = _box_axes_fp32(h.astype(F), d.astype(F), qa.astype(F), qb.astype(F))
+    # exact: l* = R(qA)^T D, B's axes u*_m = columns of R(qA)^T R(qB)
+    RA, RB = _rot64(qa), _rot64(qb)
+    l = np.einsum("pki,pk->pi", RA, d)
+    U = np.einsum("pki,pkj->pij", RA, RB)
+    err_sep, err_axis = 0.0, 0.0
+    for a, (kind, i, j, nv) in enumerate(axes):
+        se = _s_exact(h, l, U, nv)
+        err_sep = max(err_sep, float(np.max(np.abs(s32[:, a] - se))))
+        if kind == "e":
+            nstar = nv
+        elif kind == "u":
+            nstar = U[:, :, j]
+        else:
+            e = np.zeros(3)
+            e[i] = 1.0
+            nstar = np.cross(np.broadcast_to(e, U[:, :, j].shape), U[:, :, j])
+        err_axis = max(err_axis, float(np.max(np.abs(se - _s_exact(h, l, U, nstar)))))
+    assert err_sep / (2 * R) < e_sep, (err_sep / (2 * R), e_sep)
+    assert err_axis / (2 * R) < e_ov - e_sep, (err_axis / (2 * R), e_ov - e_sep)
+    # the bounds are not vacuous: the worst errors seen are within two
+    # orders of magnitude of them
+    assert err_sep / (2 * R) > e_sep / 300
