@@ -1,11 +1,12 @@
-// Host-side check of the polyhedron classification the 3D kernels rely on
-// (test helper, built by tests/test_shape_host.py): reads "nv" and nv lines
-// of "x y z" from stdin, runs build_shapes, and prints one line of
-// key=value pairs: the return code, the box / central-symmetry / interior-
-// origin flags, the box half extents, whether the FP32 copies are the
-// vertices' casts in some order (and, for symmetric shapes, in pairs k,
+// Host-side check of the shape constants the kernels rely on (test helper,
+// built by tests/test_shape_host.py).  Reads "dim nv" and nv vertices of dim
+// coordinates from stdin, runs build_shapes, and prints one line of
+// key=value pairs.  3D: the return code, the box / central-symmetry /
+// interior-origin flags, the box half extents, whether the FP32 copies are
+// the vertices' casts in some order (and, for symmetric shapes, in pairs k,
 // k + nv/2 of opposite sign), and the box test's FP32 and FP64 margins
-// relative to the circumdiameter.
+// relative to the circumdiameter.  2D: the FP32 separating-axis margin for
+// inputs that are FP32 casts of the FP64 ones.
 #include <vector_types.h>
 
 #include <cstdio>
@@ -16,18 +17,32 @@
 
 int main()
 {
+    int dim = 0;
     unsigned nv = 0;
-    if (std::scanf("%u", &nv) != 1) return 2;
-    std::vector<double> v(3 * nv);
-    for (unsigned i = 0; i < 3 * nv; ++i)
+    if (std::scanf("%d %u", &dim, &nv) != 2 || (dim != 2 && dim != 3)) return 2;
+    std::vector<double> v((size_t)dim * nv);
+    for (size_t i = 0; i < v.size(); ++i)
         if (std::scanf("%lf", &v[i]) != 1) return 2;
     hpmc::Shape2 s2{};
     hpmc::Shape3 s3{};
     double Rc = 0.0, rc2 = 0.0;
-    const int rc = hpmc::build_shapes(3, v.data(), nv, s2, s3, Rc, rc2);
+    const int rc = hpmc::build_shapes(dim, v.data(), nv, s2, s3, Rc, rc2);
     std::printf("rc=%d", rc);
     if (rc) {
         std::printf("\n");
+        return 0;
+    }
+    if (dim == 2) {
+        hpmc::Margins g{};
+        g.e_dlt = hpmc::kU32 * 2.0 * Rc * 1.01;
+        g.e_ori = hpmc::kU32 * 1.01;
+        double vm = 0.0, nm = 0.0, am = 0.0;
+        for (int k = 0; k < s2.nv; ++k) {
+            vm = std::fmax(vm, std::fmax(std::fabs(s2.vx[k]), std::fabs(s2.vy[k])));
+            nm = std::fmax(nm, std::fmax(std::fabs(s2.nx[k]), std::fabs(s2.ny[k])));
+            am = std::fmax(am, std::fmax(std::fabs(s2.alo[k]), std::fabs(s2.ahi[k])));
+        }
+        std::printf(" Rc=%.17g E=%.9g\n", Rc, hpmc::sat2_margin(g, Rc, vm, nm, am));
         return 0;
     }
     // the FP32 copies: a permutation of the casts

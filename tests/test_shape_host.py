@@ -45,9 +45,9 @@ def prog(tmp_path_factory):
     return exe
 
 
-def _run(exe, v):
-    v = np.asarray(v, dtype=np.float64).reshape(-1, 3)
-    txt = f"{len(v)}\n" + "\n".join(" ".join(repr(float(x)) for x in row) for row in v) + "\n"
+def _run(exe, v, dim=3):
+    v = np.asarray(v, dtype=np.float64).reshape(-1, dim)
+    txt = f"{dim} {len(v)}\n" + "\n".join(" ".join(repr(float(x)) for x in row) for row in v) + "\n"
     out = subprocess.run([exe], input=txt, capture_output=True, text=True, check=True).stdout.split()
     res = {}
     for kv in out:
@@ -258,3 +258,71 @@ def test_box_test_errors_within_its_margins(prog, hh):
     # the bounds are not vacuous: the worst errors seen are within two
     # orders of magnitude of them
     assert err_sep / (2 * R) > e_sep / 300
+
+
+# ---- the FP32 separating-axis test of polygons, checked the same way
+#
+# sat32 evaluates, in FP32 from FP32 casts, each axis' gap max(lo - a_hi,
+# a_lo - hi) of the two halves (A's edge normals with B in A's frame, then
+# B's with A in B's frame); its certificate needs |gap32 - gap64| <= E / 2,
+# gap64 the FP64 contract's value (sat2_margin returns twice the sum of the
+# FP32 and FP64 error bounds).
+
+
+def _sat_gaps(dtype, fma, V, D, cA, sA, cB, sB):
+    """Every axis gap of both halves (pairs x 2 nv), with the FP32 filter's
+    operations (fma given) or the FP64 contract's (fma None)."""
+    nv = len(V)
+    vx, vy = V[:, 0].astype(np.float64), V[:, 1].astype(np.float64)
+    nx = np.roll(vy, -1) - vy
+    ny = vx - np.roll(vx, -1)
+    t = nx[:, None] * vx[None, :] + ny[:, None] * vy[None, :]
+    alo, ahi = t.min(1), t.max(1)
+    c = lambda a: np.asarray(a, dtype=dtype)                       # noqa: E731
+    fvx, fvy, fnx, fny, falo, fahi = map(c, (vx, vy, nx, ny, alo, ahi))
+    dx, dy = c(D[:, 0]), c(D[:, 1])
+    cA, sA, cB, sB = map(c, (cA, sA, cB, sB))
+    if fma:
+        cr = fma(cA, cB, sA * sB)
+        sr = fma(cA, sB, -(sA * cB))
+        lx, ly = fma(cA, dx, sA * dy), fma(cA, dy, -(sA * dx))
+        mx, my = fma(cB, dx, sB * dy), fma(cB, dy, -(sB * dx))
+    else:
+        cr, sr = cA * cB + sA * sB, cA * sB - sA * cB
+        lx, ly = cA * dx + sA * dy, cA * dy - sA * dx
+        mx, my = cB * dx + sB * dy, cB * dy - sB * dx
+    gaps = []
+    for (r_c, r_s, ox, oy) in ((cr, sr, lx, ly), (cr, -sr, -mx, -my)):
+        if fma:
+            px = [fma(r_c, np.full_like(dx, fvx[i]), fma(-r_s, np.full_like(dx, fvy[i]), ox)) for i in range(nv)]
+            py = [fma(r_s, np.full_like(dx, fvx[i]), fma(r_c, np.full_like(dx, fvy[i]), oy)) for i in range(nv)]
+        else:
+            px = [(r_c * fvx[i] - r_s * fvy[i]) + ox for i in range(nv)]
+            py = [(r_s * fvx[i] + r_c * fvy[i]) + oy for i in range(nv)]
+        for k in range(nv):
+            if fma:
+                tk = [fma(np.full_like(dx, fnx[k]), px[i], fny[k] * py[i]) for i in range(nv)]
+            else:
+                tk = [fnx[k] * px[i] + fny[k] * py[i] for i in range(nv)]
+            lo, hi = np.min(tk, axis=0), np.max(tk, axis=0)
+            gaps.append(np.maximum(lo - fahi[k], falo[k] - hi).astype(np.float64))
+    return np.stack(gaps, 1)
+
+
+@pytest.mark.parametrize("nv", [5, 3, 7])
+def test_polygon_test_errors_within_its_margin(prog, nv):
+    V = inputs.regular_polygon(nv, 0.5)
+    r = _run(prog, V, dim=2)
+    E = float(r["E"])
+    R = float(r["Rc"])
+    rng = np.random.default_rng(nv)
+    n = 200000
+    ang = rng.uniform(0, 2 * np.pi, n)
+    D = np.stack([np.cos(ang), np.sin(ang)], 1) * (2 * R * np.sqrt(rng.uniform(0, 1, n)))[:, None]
+    tA, tB = rng.uniform(0, 2 * np.pi, n), rng.uniform(0, 2 * np.pi, n)
+    cA, sA, cB, sB = np.cos(tA), np.sin(tA), np.cos(tB), np.sin(tB)
+    g32 = _sat_gaps(F, _fma, V, D, cA, sA, cB, sB)
+    g64 = _sat_gaps(np.float64, None, V, D, cA, sA, cB, sB)
+    err = float(np.max(np.abs(g32 - g64)))
+    assert err < E / 2, (err, E / 2)
+    assert err > E / 2 / 300
