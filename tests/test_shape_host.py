@@ -326,3 +326,16 @@ def test_polygon_test_errors_within_its_margin(prog, nv):
     err = float(np.max(np.abs(g32 - g64)))
     assert err < E / 2, (err, E / 2)
     assert err > E / 2 / 300
+
+
+def test_polygon_validation(prog):
+    # counter-clockwise convex polygons are accepted; clockwise, non-convex
+    # and degenerate (collinear) vertex lists are refused
+    pent = np.asarray(inputs.regular_polygon(5, 0.5))
+    assert _run(prog, pent, dim=2)["rc"] == "0"
+    assert _run(prog, pent[::-1], dim=2)["rc"] != "0"                 # clockwise
+    dart = np.array([[0.0, -0.5], [0.5, 0.5], [0.0, 0.1], [-0.5, 0.5]])
+    assert _run(prog, dart, dim=2)["rc"] != "0"                        # a reflex vertex
+    line = np.array([[-0.5, -0.5], [0.0, -0.5], [0.5, -0.5], [0.0, 0.5]])
+    assert _run(prog, line, dim=2)["rc"] != "0"                        # three collinear vertices
+    assert _run(prog, np.array([[0.0, 0.0], [1.0, 0.0]]), dim=2)["rc"] != "0"    # too few
